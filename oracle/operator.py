@@ -1,0 +1,150 @@
+"""The second-order 7-point operator of Eq. 4, built from ghost-cell rules.
+
+Oracle module (test infrastructure only; see ``oracle/__init__``).
+
+Arrays are C-ordered ``[n_z][n_y][n_x]`` (x fastest), cell-centred. x and y are
+uniform (§2.1 requires a constant spacing in the two transformed directions);
+z may be non-uniform (footnote to Eq. 5), given by its n_z + 1 face
+coordinates.
+
+Readings (the paper gives the uniform stencil only):
+
+* "Staggered" BCs (Table 1 caption, end of §2.1): the boundary sits on a cell
+  face. Neumann: ghost Φ_{−1} = Φ_0 (zero flux). Dirichlet: ghost
+  Φ_{−1} = −Φ_0 mirrored across the face (zero value on the face). Periodic:
+  the ghost is the cell on the other end. ``"ND"`` is Neumann at the low end,
+  Dirichlet at the high end.
+* Stretched z: finite-volume form ``(flux_{k+1/2} − flux_{k−1/2}) / Δz^f_k``
+  with ``flux_{k+1/2} = (Φ_{k+1} − Φ_k) / Δz^c_k``; Δz^f_k is the width of
+  cell k and Δz^c_k the distance between the centres of cells k and k+1. A
+  Dirichlet ghost sits a distance Δz^f of the boundary cell away (its mirror
+  image); a periodic ghost sits (Δz^f_0 + Δz^f_{n−1})/2 away. On a uniform grid
+  this is exactly the z row of Eq. 4.
+
+``operator_1d`` and ``apply`` are two separate codings of these rules (a matrix
+assembled row by row, and a padded-array stencil); tests check they agree.
+"""
+
+import numpy as np
+import scipy.sparse as sp
+
+from .transforms import BCS
+
+
+def uniform_faces(n, h):
+    """Face coordinates 0, h, …, n·h of a uniform axis."""
+    return np.arange(n + 1, dtype=np.float64) * h
+
+
+def metrics(faces):
+    """(Δz^f, Δz^c): cell widths (n) and centre-to-centre distances (n−1)."""
+    faces = np.asarray(faces, dtype=np.float64)
+    dzf = np.diff(faces)
+    zc = 0.5 * (faces[:-1] + faces[1:])
+    return dzf, np.diff(zc)
+
+
+def _ends(bc):
+    """BC kind at (low, high) end: 'N', 'D' or 'P'."""
+    if bc not in BCS:
+        raise ValueError(f"unknown BC {bc!r}")
+    return {"P": ("P", "P"), "NN": ("N", "N"), "DD": ("D", "D"), "ND": ("N", "D")}[bc]
+
+
+def operator_1d(bc, faces):
+    """Dense n×n matrix of the 1D operator on one axis, assembled row by row."""
+    dzf, dzc = metrics(faces)
+    n = len(dzf)
+    lo, hi = _ends(bc)
+    L = np.zeros((n, n))
+    hper = 0.5 * (dzf[0] + dzf[-1])
+    for k in range(n):
+        w = 1.0 / dzf[k]
+        # flux through the upper face of cell k: (Φ_up − Φ_k)/h_up
+        if k < n - 1:
+            L[k, k + 1] += w / dzc[k]
+            L[k, k] -= w / dzc[k]
+        elif hi == "P":
+            L[k, 0] += w / hper
+            L[k, k] -= w / hper
+        elif hi == "D":            # ghost −Φ_k at distance Δz^f_k
+            L[k, k] -= 2.0 * w / dzf[k]
+        # Neumann: zero flux, nothing added
+        # minus the flux through the lower face: (Φ_k − Φ_down)/h_down
+        if k > 0:
+            L[k, k] -= w / dzc[k - 1]
+            L[k, k - 1] += w / dzc[k - 1]
+        elif lo == "P":
+            L[k, k] -= w / hper
+            L[k, n - 1] += w / hper
+        elif lo == "D":
+            L[k, k] -= 2.0 * w / dzf[k]
+    return L
+
+
+def operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz):
+    """Sparse (CSR) N×N matrix of Eq. 4 on the [n_z][n_y][n_x] grid."""
+    zf = np.asarray(zf, dtype=np.float64)
+    nz = len(zf) - 1
+    Lx = sp.csr_matrix(operator_1d(bcx, uniform_faces(nx, dx)))
+    Ly = sp.csr_matrix(operator_1d(bcy, uniform_faces(ny, dy)))
+    Lz = sp.csr_matrix(operator_1d(bcz, zf))
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    A = sp.kron(Lz, sp.kron(Iy, Ix)) + sp.kron(Iz, sp.kron(Ly, Ix)) + sp.kron(Iz, sp.kron(Iy, Lx))
+    return A.tocsr()
+
+
+def _axis_term(p, axis, faces, bc):
+    """Second-difference term of one axis, from a padded copy (ghost rules above)."""
+    dzf, dzc = metrics(faces)
+    lo, hi = _ends(bc)
+    x = np.moveaxis(p, axis, 0)
+    if lo == "P":
+        glo, ghi = x[-1], x[0]
+        hlo = hhi = 0.5 * (dzf[0] + dzf[-1])
+    else:
+        glo = x[0] if lo == "N" else -x[0]
+        ghi = x[-1] if hi == "N" else -x[-1]
+        hlo, hhi = dzf[0], dzf[-1]
+    ext = np.concatenate([glo[None], x, ghi[None]], axis=0)
+    h = np.concatenate([[hlo], dzc, [hhi]])
+    shape = (-1,) + (1,) * (x.ndim - 1)
+    flux = (ext[1:] - ext[:-1]) / h.reshape(shape)
+    term = (flux[1:] - flux[:-1]) / dzf.reshape(shape)
+    return np.moveaxis(term, 0, axis)
+
+
+def apply(p, dx, dy, zf, bcx, bcy, bcz):
+    """A·p for a [n_z][n_y][n_x] FP64 array (stencil form of Eq. 4)."""
+    p = np.asarray(p, dtype=np.float64)
+    nz, ny, nx = p.shape
+    return (_axis_term(p, 2, uniform_faces(nx, dx), bcx)
+            + _axis_term(p, 1, uniform_faces(ny, dy), bcy)
+            + _axis_term(p, 0, np.asarray(zf, dtype=np.float64), bcz))
+
+
+def is_singular(bcx, bcy, bcz):
+    """True when the constant is in the null space: every axis P or NN."""
+    return all(b in ("P", "NN") for b in (bcx, bcy, bcz))
+
+
+def cell_volumes(nx, ny, dx, dy, zf):
+    """Cell volumes Δx·Δy·Δz^f_k broadcast to [n_z][n_y][n_x]."""
+    dzf, _ = metrics(zf)
+    return np.broadcast_to((dx * dy * dzf)[:, None, None], (len(dzf), ny, nx))
+
+
+def compatible_part(f, dx, dy, zf, bcx, bcy, bcz):
+    """f with its volume-weighted mean removed when the operator is singular."""
+    if not is_singular(bcx, bcy, bcz):
+        return np.array(f, dtype=np.float64, copy=True)
+    nz, ny, nx = f.shape
+    v = cell_volumes(nx, ny, dx, dy, zf)
+    return f - (v * f).sum() / v.sum()
+
+
+def relative_residual(p, f, dx, dy, zf, bcx, bcy, bcz):
+    """‖f_c − A p‖∞ / ‖f_c‖∞ with f_c the compatible part of f."""
+    fc = compatible_part(f, dx, dy, zf, bcx, bcy, bcz)
+    r = fc - apply(p, dx, dy, zf, bcx, bcy, bcz)
+    return np.abs(r).max() / np.abs(fc).max()

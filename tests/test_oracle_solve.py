@@ -1,0 +1,166 @@
+"""Pins for the oracle's solve (no GPU).
+
+Independent references used:
+* dense / sparse LU of the assembled operator (``oracle.direct``) — no transform;
+* the dense matrix of a tridiagonal or cyclic system (numpy.linalg.solve);
+* closed form for a single eigenmode on a uniform grid (Eq. 5 with Table 1 λ);
+* second-order convergence toward analytic solutions (§2: second order in space);
+* the stencil apply vs the sparse matrix (two codings of the ghost rules).
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import transforms as T
+from oracle import operator as O
+from oracle import solve as S
+from oracle import direct as D
+from oracle import tridiag as TD
+from paper_1802_10323_gb300 import synth
+
+ALL = list(itertools.product(T.BCS, repeat=3))
+
+
+def _stretched(n, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 1.5, n))])
+
+
+@pytest.mark.parametrize("bcs", ALL, ids=["-".join(b) for b in ALL])
+def test_eigen_solve_equals_dense_lu(bcs):
+    zf = _stretched(6, seed=1)
+    f = np.random.default_rng(2).uniform(-1, 1, (6, 4, 8))
+    p = S.solve(f, 0.3, 0.7, zf, *bcs)
+    q = D.solve_direct(f, 0.3, 0.7, zf, *bcs, dense=True)
+    assert np.abs(p - q).max() <= 1e-12 * np.abs(q).max()
+    assert O.relative_residual(p, f, 0.3, 0.7, zf, *bcs) < 1e-12
+
+
+@pytest.mark.parametrize("bcs", [("P", "P", "NN"), ("DD", "ND", "P"), ("NN", "NN", "NN")])
+def test_stencil_equals_sparse_matrix(bcs):
+    zf = _stretched(5, seed=3)
+    x = np.random.default_rng(4).standard_normal((5, 6, 4))
+    A = O.operator_3d(4, 6, 0.2, 0.9, zf, *bcs)
+    assert np.abs(A @ x.ravel() - O.apply(x, 0.2, 0.9, zf, *bcs).ravel()).max() < 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("bcz", T.BCS)
+@pytest.mark.parametrize("n", [2, 4, 7, 10])
+def test_z_system_is_the_operator(bcz, n):
+    zf = _stretched(n, seed=n)
+    a, b, c = S.z_system(zf, bcz)
+    M = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    if bcz == "P":
+        M[0, n - 1] += a[0]
+        M[n - 1, 0] += c[n - 1]
+    assert np.allclose(M, O.operator_1d(bcz, zf), rtol=0, atol=1e-12 * np.abs(M).max())
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17])
+def test_thomas_vs_dense(n):
+    rng = np.random.default_rng(n)
+    a, c = rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    b = -(a + c) - rng.uniform(0.01, 1, n)
+    d = rng.standard_normal((n, 3))
+    M = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    assert np.allclose(TD.thomas(a, b, c, d), np.linalg.solve(M, d), atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 3, 16])
+def test_cyclic_vs_dense(n):
+    rng = np.random.default_rng(n)
+    a, c = rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    b = -(a + c) - rng.uniform(0.01, 1, n)
+    d = rng.standard_normal((n, 2))
+    M = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    M[0, n - 1] += a[0]
+    M[n - 1, 0] += c[n - 1]
+    assert np.allclose(TD.thomas_cyclic(a, b, c, d), np.linalg.solve(M, d), atol=1e-12)
+
+
+@pytest.mark.parametrize("bcs", [("P", "NN", "DD"), ("ND", "P", "NN"), ("DD", "DD", "ND"), ("P", "P", "P")])
+def test_single_mode_closed_form(bcs):
+    """f = product of eigenvectors ⇒ Φ = f / (λx/Δx² + λy/Δy² + λz/Δz²)."""
+    nx, ny, nz, dx, dy, dz = 8, 6, 10, 0.25, 0.5, 0.1
+    qx, qy, qz = 3, 1, 2
+    if bcs == ("P", "P", "P"):
+        qx = 5
+    ex = T.backward_matrix(bcs[0], nx)[:, qx]
+    ey = T.backward_matrix(bcs[1], ny)[:, qy]
+    ez = T.backward_matrix(bcs[2], nz)[:, qz]
+    f = ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    lam = (T.eigenvalues(bcs[0], nx)[qx] / dx ** 2 + T.eigenvalues(bcs[1], ny)[qy] / dy ** 2
+           + T.eigenvalues(bcs[2], nz)[qz] / dz ** 2)
+    p = S.solve(f, dx, dy, O.uniform_faces(nz, dz), *bcs)
+    assert np.abs(p - f / lam).max() < 1e-13 * np.abs(f / lam).max()
+
+
+@pytest.mark.parametrize("bcs", [("P", "NN", "DD"), ("ND", "DD", "NN"), ("NN", "P", "ND"), ("P", "P", "NN")])
+def test_second_order_convergence(bcs):
+    errs, hs = [], []
+    for n in (16, 32, 64):
+        zf = synth.tanh_faces(n, 1.0, 1.5)
+        p_ex, f = synth.manufactured(n, n, 1.0, 2.0, zf, bcs)
+        p = S.solve(f, 1.0 / n, 2.0 / n, zf, *bcs)
+        if O.is_singular(*bcs):
+            v = O.cell_volumes(n, n, 1.0 / n, 2.0 / n, zf)
+            p_ex = p_ex - (v * p_ex).sum() / v.sum()
+        errs.append(np.abs(p - p_ex).max())
+        hs.append(1.0 / n)
+    orders = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log(2.0)
+    assert orders.min() >= 1.9, orders
+
+
+@pytest.mark.parametrize("bcs", [("P", "P", "NN"), ("NN", "NN", "NN"), ("P", "NN", "P"), ("P", "P", "P")])
+def test_singular_zero_mean_and_compatible_part(bcs):
+    zf = synth.tanh_faces(8, 1.0, 1.5) if bcs[2] != "P" else O.uniform_faces(8, 0.125)
+    f = np.random.default_rng(7).uniform(-1, 1, (8, 6, 4)) + 0.3   # has a mean
+    p = S.solve(f, 0.25, 0.2, zf, *bcs)
+    v = O.cell_volumes(4, 6, 0.25, 0.2, zf)
+    assert abs((v * p).sum()) < 1e-13 * np.abs(p).max() * v.sum()
+    fc = O.compatible_part(f, 0.25, 0.2, zf, *bcs)
+    assert abs((v * fc).sum()) < 1e-13 * v.sum()
+    assert O.relative_residual(p, f, 0.25, 0.2, zf, *bcs) < 1e-12
+
+
+def test_small_channel_32_cubed_vs_sparse_lu():
+    """32³, P/P/NN, uniform unit cube, U[−1,1] mean-removed (the small FP64 case)."""
+    n = 32
+    f = synth.uniform_noise((n, n, n), seed=0)
+    zf = O.uniform_faces(n, 1.0 / n)
+    p = S.solve(f, 1.0 / n, 1.0 / n, zf, "P", "P", "NN")
+    q = D.solve_direct(f, 1.0 / n, 1.0 / n, zf, "P", "P", "NN")
+    assert np.abs(p - q).max() <= 1e-12 * np.abs(q).max()
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_tiny_grids(n):
+    for bcs in [("P", "P", "P"), ("DD", "ND", "NN"), ("NN", "NN", "P")]:
+        zf = _stretched(n, seed=9)
+        f = np.random.default_rng(n).standard_normal((n, n, n))
+        p = S.solve(f, 0.5, 0.5, zf, *bcs)
+        q = D.solve_direct(f, 0.5, 0.5, zf, *bcs, dense=True)
+        assert np.abs(p - q).max() <= 1e-12 * max(np.abs(q).max(), 1e-300)
+
+
+def test_golden_nonuniform_operator():
+    """Hand-worked 1D operator rows on faces 0, 1, 3, 6 (tests/golden)."""
+    import os
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(__file__), "golden", "operator_faces_0_1_3_6.txt")
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        bc, *vals = line.split()
+        expect = np.array([float(Fraction(v)) for v in vals]).reshape(3, 3)
+        got = O.operator_1d(bc, np.array([0.0, 1.0, 3.0, 6.0]))
+        assert np.abs(got - expect).max() < 1e-15, bc
+        a, b, c = S.z_system(np.array([0.0, 1.0, 3.0, 6.0]), bc)
+        M = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+        if bc == "P":
+            M[0, 2] += a[0]
+            M[2, 0] += c[2]
+        assert np.abs(M - expect).max() < 1e-15, bc
