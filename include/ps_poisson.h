@@ -1,0 +1,173 @@
+/*
+ * ps_poisson.h — C ABI of the GB300 eigenfunction-expansion Poisson solver.
+ *
+ * The operation (Costa 2018, §2.1, Eq. 4): solve the second-order 7-point
+ * finite-difference Poisson equation  A·Φ = f  on a cell-centred grid of
+ * n_x × n_y × n_z cells, uniform in x and y, possibly stretched in z (footnote
+ * to Eq. 5), with a homogeneous staggered boundary-condition pair per axis
+ * (Table 1). The method: forward real-to-real transform along x, then y
+ * (Table 2), one tridiagonal solve along z per wavenumber pair (Eq. 5), and the
+ * inverse transforms (the three steps that close §2.1).
+ *
+ * Layout of every field: C order [n_z][n_y][n_x], x contiguous, one value per
+ * cell centre. All field pointers passed to ps_solve* are DEVICE pointers owned
+ * by the caller; plans own their tables. Every call returns a ps_status; no
+ * exception or abort crosses this boundary. ps_last_error() gives a static
+ * description of the last failure on a plan (or of the last failed create).
+ *
+ * Singular problems (every axis periodic or Neumann–Neumann, so constants are
+ * in the null space): the solve returns the Φ that satisfies A·Φ = f_c, with
+ * f_c = f minus its volume-weighted mean, and whose volume-weighted mean is 0.
+ *
+ * Streams are passed as `void*` holding a cudaStream_t (NULL = legacy default
+ * stream). Solves only enqueue work on that stream: no host synchronisation,
+ * no allocation. Results, including the ps_info record, are valid after the
+ * stream has been synchronised.
+ */
+#ifndef PS_POISSON_H
+#define PS_POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PS_OK = 0,
+  PS_INVALID_ARG = 1,        /* null pointer, bad spacing, inconsistent sizes   */
+  PS_UNSUPPORTED_SIZE = 2,   /* n odd, n < 2, n > 1024, or n/2 not 2^a·3^b     */
+  PS_CUDA_ERROR = 3,         /* a CUDA runtime call failed (see ps_last_error)  */
+  PS_OUT_OF_MEMORY = 4,      /* cudaMalloc of plan tables failed                */
+  PS_NOT_CONVERGED = 5,      /* refinement did not reach rtol in max_iter       */
+  PS_TIMEOUT = 6             /* a bounded device wait gave up (batched solve)   */
+} ps_status;
+
+/* Per-axis boundary-condition pair, Table 1 (staggered: the boundary is a
+ * cell face). NEUMANN_DIRICHLET is Neumann at the low end, Dirichlet at the
+ * high end. Forward transforms per Table 2: DFT (half-complex layout),
+ * DCT-II, DST-II, DCT-IV; backward: 1/n IDFT, 1/(2n) DCT-III, 1/(2n) DST-III,
+ * 1/(2n) DCT-IV. */
+typedef enum {
+  PS_BC_PERIODIC = 0,
+  PS_BC_NEUMANN_NEUMANN = 1,
+  PS_BC_DIRICHLET_DIRICHLET = 2,
+  PS_BC_NEUMANN_DIRICHLET = 3
+} ps_bc;
+
+/* Arithmetic of the solve.
+ *   PS_FP64         all of the path in FP64 arithmetic (fields double).
+ *   PS_FP32         all of the path in FP32 arithmetic (fields float).
+ *   PS_FP32_REFINE  FP64 fields; FP32 bulk transforms and tridiagonal solves,
+ *                   iterative refinement whose residual r = f − A·Φ is formed
+ *                   in double-float (pairs of FP32) from the FP64 fields, until
+ *                   ‖r‖∞ ≤ rtol·‖f_c‖∞ or max_iter corrections. */
+typedef enum { PS_FP64 = 0, PS_FP32 = 1, PS_FP32_REFINE = 2 } ps_precision;
+
+/* Device-side record written by every solve (caller allocates it in device
+ * memory; read it after synchronising the stream). */
+typedef struct {
+  int status;             /* ps_status of the device work (OK, NOT_CONVERGED, TIMEOUT) */
+  int iterations;         /* refinement corrections applied (0 for FP64 / FP32)        */
+  double rel_residual;    /* ‖f_c − A·Φ‖∞ / ‖f_c‖∞ measured on the device (refine);   */
+                          /* −1 when not measured (FP64 / FP32 modes)                  */
+  double r_norm;          /* ‖f_c − A·Φ‖∞ (refine), else −1                            */
+  double f_norm;          /* ‖f_c‖∞ (refine), else −1                                  */
+} ps_info;
+
+typedef struct ps_plan ps_plan;
+typedef struct ps_batch ps_batch;
+
+/* Create a plan (§2.1; Table 1 eigenvalues λ_q = −4 sin²θ_q / Δ² and the
+ * Table 2 twiddles are computed here in FP64, cast once for FP32 paths; the
+ * z coefficients follow the finite-volume form of Eq. 4 on the faces zf).
+ *   nx, ny, nz   cells per axis; each even, 2 ≤ n ≤ 1024, n/2 = 2^a·3^b.
+ *   dx, dy       uniform spacings (> 0).
+ *   zf           host array of nz+1 increasing face coordinates, or NULL for a
+ *                uniform z of spacing dz (> 0). Copied; the caller keeps it.
+ *   bcx,bcy,bcz  boundary pairs (Table 1).
+ *   prec         arithmetic (see ps_precision).
+ *   rtol         refinement target on ‖r‖∞/‖f_c‖∞ (PS_FP32_REFINE only).
+ *   max_iter     maximum refinement corrections (PS_FP32_REFINE only, ≥ 0).
+ * Allocates the plan's device tables on the current device. On failure *out is
+ * NULL and the status says why. */
+ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, double dy,
+                         const double* zf, double dz, ps_bc bcx, ps_bc bcy, ps_bc bcz,
+                         ps_precision prec, double rtol, int max_iter);
+
+/* Bytes of device workspace a solve on this plan needs (caller allocates it,
+ * 256-byte aligned, and may reuse it across solves on the same stream). */
+ps_status ps_workspace_bytes(const ps_plan* plan, size_t* bytes);
+
+/* Solve A·p = f (Eq. 4) for FP64 fields (plans with PS_FP64 or
+ * PS_FP32_REFINE). f, p: device arrays of nx·ny·nz doubles; p == f (in place)
+ * is allowed for PS_FP64 only. ws: workspace of ps_workspace_bytes. stream:
+ * cudaStream_t as void*. info: device ps_info (may be NULL). */
+ps_status ps_solve(ps_plan* plan, const double* f, double* p, void* ws, void* stream,
+                   ps_info* info);
+
+/* Same for FP32 fields (plans with PS_FP32). p == f allowed. */
+ps_status ps_solve_f32(ps_plan* plan, const float* f, float* p, void* ws, void* stream,
+                       ps_info* info);
+
+/* Apply the transpose of the solve map, Aᵀ-solve (for reverse-mode
+ * differentiation). With A = W⁻¹S, W = diag(Δz^f_k), S symmetric, the
+ * transpose is p = W · solve(W⁻¹ g); singular problems use the transposed
+ * projector accordingly. Same arguments and rules as ps_solve (FP64 fields,
+ * PS_FP64 or PS_FP32_REFINE plans). */
+ps_status ps_solve_transpose(ps_plan* plan, const double* g, double* p, void* ws, void* stream,
+                             ps_info* info);
+
+/* FP32-field variant of ps_solve_transpose (PS_FP32 plans). */
+ps_status ps_solve_transpose_f32(ps_plan* plan, const float* g, float* p, void* ws, void* stream,
+                                 ps_info* info);
+
+/* Host-buffer convenience: copies f_host (pageable or pinned, nx·ny·nz
+ * doubles) to the caller's device buffer f_dev, solves into p_dev, copies p_dev
+ * back to p_host and the ps_info to info_host (may be NULL), then synchronises
+ * the stream. Device buffers and workspace are the caller's. */
+ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, double* f_dev,
+                        double* p_dev, void* ws, void* stream, ps_info* info_host);
+
+/* Destroy a plan and free its device tables (NULL is accepted). */
+ps_status ps_plan_destroy(ps_plan* plan);
+
+/* Static, NUL-terminated description of the last failure on this plan (or,
+ * for plan == NULL, of the last failed ps_plan_create / ps_batch_create). */
+const char* ps_last_error(const ps_plan* plan);
+
+/* ---- Batched solve: many independent grids, one persistent launch ----------
+ * Each grid is an independent problem of §2.1 with its own sizes, spacings,
+ * z faces and BC pairs. */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy;
+  const double* zf;   /* host, nz+1 faces, or NULL for uniform dz */
+  double dz;
+  ps_bc bcx, bcy, bcz;
+} ps_grid_desc;
+
+/* Create a batch of `count` grids (1 ≤ count ≤ 4096); precision PS_FP64 or
+ * PS_FP32_REFINE. Tables for every grid are built as in ps_plan_create. */
+ps_status ps_batch_create(ps_batch** out, int count, const ps_grid_desc* descs,
+                          ps_precision prec, double rtol, int max_iter);
+
+/* Workspace bytes for one batched solve. */
+ps_status ps_batch_workspace_bytes(const ps_batch* batch, size_t* bytes);
+
+/* Solve every grid: f_dev[g], p_dev[g] are DEVICE arrays of DEVICE pointers
+ * (count entries each) to the grids' FP64 fields. infos: device array of
+ * `count` ps_info (may be NULL). One persistent kernel walks a task queue of
+ * (grid, stage, tile); its inter-task waits are bounded and report
+ * PS_TIMEOUT in the grid's ps_info instead of hanging. Capturable in a CUDA
+ * graph (no host synchronisation, no allocation). */
+ps_status ps_batch_solve(ps_batch* batch, double* const* f_dev, double* const* p_dev, void* ws,
+                         void* stream, ps_info* infos);
+
+ps_status ps_batch_destroy(ps_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_POISSON_H */

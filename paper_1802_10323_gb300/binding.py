@@ -1,0 +1,173 @@
+"""ctypes binding of the C ABI in ``include/ps_poisson.h`` (argument marshalling only).
+
+Every solve step runs in the CUDA library ``libps_poisson.so``; this module only
+passes pointers, sizes and the current CUDA stream. Importing it raises if the
+library has not been built (there is no fallback of any kind). Build it with
+``python -m paper_1802_10323_gb300.build`` or ``__graft_entry__.build()``.
+
+The functions ``ps_*`` mirror the C calls one to one; ``Plan`` wraps a plan
+with torch-tensor conveniences (device pointers from ``data_ptr()``, the
+workspace as a uint8 tensor, the stream from ``torch.cuda.current_stream()``).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libps_poisson.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                      "(python -m paper_1802_10323_gb300.build)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+PS_OK, PS_INVALID_ARG, PS_UNSUPPORTED_SIZE, PS_CUDA_ERROR = 0, 1, 2, 3
+PS_OUT_OF_MEMORY, PS_NOT_CONVERGED, PS_TIMEOUT = 4, 5, 6
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "CUDA_ERROR",
+                4: "OUT_OF_MEMORY", 5: "NOT_CONVERGED", 6: "TIMEOUT"}
+BC = {"P": 0, "NN": 1, "DD": 2, "ND": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
+
+
+class PsInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("r_norm", ctypes.c_double),
+                ("f_norm", ctypes.c_double)]
+
+
+class PsGridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("zf", ctypes.POINTER(ctypes.c_double)), ("dz", ctypes.c_double),
+                ("bcx", ctypes.c_int), ("bcy", ctypes.c_int), ("bcz", ctypes.c_int)]
+
+
+_vp, _i, _d, _st = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int
+_SIGS = {
+    "ps_plan_create": [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _vp, _d, _i, _i, _i, _i, _d, _i],
+    "ps_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+    "ps_solve": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "ps_solve_f32": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "ps_solve_transpose": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "ps_solve_transpose_f32": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "ps_solve_host": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "ps_plan_destroy": [_vp],
+    "ps_batch_create": [ctypes.POINTER(_vp), _i, ctypes.POINTER(PsGridDesc), _i, _d, _i],
+    "ps_batch_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+    "ps_batch_solve": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "ps_batch_destroy": [_vp],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _st
+_lib.ps_last_error.argtypes = [_vp]
+_lib.ps_last_error.restype = ctypes.c_char_p
+
+EXPORTS = sorted(list(_SIGS) + ["ps_last_error"])
+
+
+def __getattr__(name):
+    if name in _SIGS or name == "ps_last_error":
+        return getattr(_lib, name)
+    raise AttributeError(name)
+
+
+class PoissonError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != PS_OK:
+        msg = _lib.ps_last_error(handle)
+        raise PoissonError(status, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def info_tensor(device="cuda"):
+    """A device buffer for one ps_info (32 bytes)."""
+    import torch
+    return torch.zeros(4, dtype=torch.float64, device=device)
+
+
+def read_info(t):
+    """Decode a ps_info device buffer (after the stream is synchronised)."""
+    raw = t.detach().cpu().numpy().tobytes()
+    return PsInfo.from_buffer_copy(raw[: ctypes.sizeof(PsInfo)])
+
+
+class Plan:
+    """A solver plan for one grid (see ps_plan_create)."""
+
+    def __init__(self, nx, ny, nz, dx, dy, zf=None, dz=None, bcs=("P", "P", "NN"),
+                 precision="fp64", rtol=1e-10, max_iter=5):
+        self.shape = (nz, ny, nx)
+        self.precision = precision
+        self.bcs = tuple(bcs)
+        self._zf = None if zf is None else np.ascontiguousarray(zf, dtype=np.float64)
+        h = _vp()
+        zp = None if self._zf is None else self._zf.ctypes.data_as(_vp)
+        _check(_lib.ps_plan_create(ctypes.byref(h), nx, ny, nz, float(dx), float(dy), zp,
+                                   float(dz or 0.0), BC[bcs[0]], BC[bcs[1]], BC[bcs[2]],
+                                   PRECISION[precision], float(rtol), int(max_iter)))
+        self.handle = h
+        n = ctypes.c_size_t()
+        _check(_lib.ps_workspace_bytes(h, ctypes.byref(n)), h)
+        self.workspace_bytes = n.value
+        self._ws = None
+
+    def workspace(self, device="cuda"):
+        import torch
+        if self._ws is None or self._ws.device != torch.device(device):
+            self._ws = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
+        return self._ws
+
+    def _call(self, fn, f, out, info, stream):
+        import torch
+        if out is None:
+            out = torch.empty_like(f)
+        ws = self.workspace(f.device)
+        ip = _vp(info.data_ptr()) if info is not None else None
+        _check(fn(self.handle, _vp(f.data_ptr()), _vp(out.data_ptr()), _vp(ws.data_ptr()),
+                  _stream_ptr(stream), ip), self.handle)
+        return out
+
+    def solve(self, f, out=None, info=None, stream=None):
+        """Φ with A·Φ = f; f a contiguous CUDA tensor [nz, ny, nx] (float64, or float32 for fp32)."""
+        assert f.is_cuda and f.is_contiguous() and tuple(f.shape) == self.shape
+        fn = _lib.ps_solve_f32 if self.precision == "fp32" else _lib.ps_solve
+        return self._call(fn, f, out, info, stream)
+
+    def solve_transpose(self, g, out=None, info=None, stream=None):
+        assert g.is_cuda and g.is_contiguous() and tuple(g.shape) == self.shape
+        fn = _lib.ps_solve_transpose_f32 if self.precision == "fp32" else _lib.ps_solve_transpose
+        return self._call(fn, g, out, info, stream)
+
+    def solve_host(self, f_host, p_host, f_dev, p_dev, stream=None):
+        """End-to-end solve from host memory (copies inside the call); returns PsInfo."""
+        ws = self.workspace(f_dev.device)
+        info = PsInfo()
+        _check(_lib.ps_solve_host(self.handle, _vp(f_host.data_ptr()), _vp(p_host.data_ptr()),
+                                  _vp(f_dev.data_ptr()), _vp(p_dev.data_ptr()), _vp(ws.data_ptr()),
+                                  _stream_ptr(stream), ctypes.cast(ctypes.byref(info), _vp)), self.handle)
+        return info
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ps_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

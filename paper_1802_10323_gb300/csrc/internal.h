@@ -1,0 +1,96 @@
+// internal.h — declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/ps_poisson.h"
+#include "common.cuh"
+
+namespace ps {
+
+enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3 };
+constexpr int kMaxN = 1024;
+constexpr int kMaxStages = 12;
+
+// Arguments of one batch of line transforms (x or y).
+template <class T>
+struct XformArgs {
+  const void* in;
+  void* out;
+  int n, m;          // line length and half length
+  int axis;          // 0 = x (contiguous rows), 1 = y (strided by nx)
+  int nx, ny, nz;
+  int nlines;        // x: nz*ny rows
+  int L;             // lines per CTA (set by the launcher)
+  int bc;
+  int nstages;
+  int radix[kMaxStages];
+  const cplx<T>* tw;        // e^{−2πi t/(8n)}, t = 0 … 8n−1
+  const T* plane_scale;     // per-z factor on load (fwd) / store (bwd), or null
+  int accumulate;           // store: out = out + v
+  const int* skip;          // if non-null and *skip != 0 the kernel returns at once
+};
+
+template <class T, class TI, class TO, bool FWD>
+cudaError_t launch_xform(XformArgs<T> a, cudaStream_t st);
+
+// z tridiagonal solves of Eq. 5, one per (q_x, q_y) column.
+template <class T>
+struct ZArgs {
+  T* data;                  // [nz][ny][nx], spectral in x and y; overwritten with Φ̂
+  T* scr_c;                 // scratch, nx*ny*nz (eliminated upper diagonal)
+  T* scr_u;                 // scratch for the periodic (Sherman–Morrison) column, or null
+  int nx, ny, nz;
+  const T* lamx;            // λ_qx/Δx², nx
+  const T* lamy;            // λ_qy/Δy², ny
+  const T* za;              // a_k (sub-diagonal; a_0 = wrap coupling when periodic)
+  const T* zb;              // b_k (diagonal incl. Dirichlet ghost terms)
+  const T* zc;              // c_k (super-diagonal; c_{n−1} = wrap coupling when periodic)
+  const T* dzf;             // cell widths (weights of the singular column)
+  int periodic;
+  int singular;             // column (0,0) is singular: handled by the fix-up kernel
+  const int* skip;
+};
+
+template <class T>
+cudaError_t launch_zsolve(ZArgs<T> a, cudaStream_t st);
+
+// Residual r = f − A·p (double-float), written as FP32, with reductions.
+struct ResidArgs {
+  const double* p;
+  const double* f;
+  float* r;                 // FP32 residual out (may be null: norms only)
+  int nx, ny, nz;
+  int bcx, bcy, bcz;        // ends: see residual.cu
+  df idx2, idy2;            // 1/Δx², 1/Δy²
+  const float2* zlo;        // coefficient of (Φ_{k−1} − Φ_k), ghost rules folded in
+  const float2* zhi;        // coefficient of (Φ_{k+1} − Φ_k)
+  const float* wz;          // Δz^f_k (weights of the mean, singular problems)
+  const float* mu;          // double-float volume-weighted mean of f (singular), subtracted from f
+  int singular;
+  int* red;                 // per-call reduction words (see residual.cu)
+  float* partial;           // per-block double-float weighted sums (2 floats per block) ×2
+  int nblocks;
+  const int* skip;
+};
+
+cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
+
+// Control block at the start of the workspace.
+struct Ctrl {
+  int converged;            // set when ‖r‖ ≤ rtol·‖f_c‖ (refinement done)
+  int iterations;
+  int status;
+  int pad0;
+  int red[8];               // reduction words of the current residual pass
+  double rel, rnorm, fnorm;
+  float mu[2];              // double-float weighted mean of f, set by the first finalize
+};
+
+cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
+                            int singular, double rtol, int iteration, int last, ps_info* info,
+                            cudaStream_t st);
+cudaError_t launch_info_plain(ps_info* info, cudaStream_t st);
+
+}  // namespace ps

@@ -1,0 +1,534 @@
+// plan.cu — plans, tables and the C-ABI entry points of ps_poisson.h.
+//
+// Tables are computed on the host in FP64 (Table 1 eigenvalues through the
+// sin² form, Table 2 twiddles, the z coefficients of Eq. 4 on the faces) and
+// cast once for the FP32 kernels. Solves only enqueue kernels on the caller's
+// stream.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ps;
+
+namespace {
+
+thread_local char g_create_err[256] = "";
+
+// cos and sin of 2π t / N for N divisible by 8, reduced to [0, π/4] so that
+// multiples of N/8 come out exact.
+void cis(long t, long N, double* c, double* s) {
+  t %= N;
+  if (t < 0) t += N;
+  const long q = t / (N / 4), r = t % (N / 4);
+  const bool flip = 2 * r > N / 4;
+  const long rr = flip ? (N / 4 - r) : r;
+  const double ang = 2.0 * M_PI * (double)rr / (double)N;
+  double c0 = cos(ang), s0 = sin(ang);
+  if (flip) {
+    double tmp = c0;
+    c0 = s0;
+    s0 = tmp;
+  }
+  // rotate by q quarter turns
+  double cc = c0, ss = s0;
+  for (long i = 0; i < q; ++i) {
+    double t2 = cc;
+    cc = -ss;
+    ss = t2;
+  }
+  *c = cc;
+  *s = ss;
+}
+
+struct AxisTab {
+  int n = 0, m = 0, bc = 0, nstages = 0;
+  int radix[kMaxStages] = {0};
+  cplx<double>* tw64 = nullptr;
+  cplx<float>* tw32 = nullptr;
+  double* lam64 = nullptr;
+  float* lam32 = nullptr;
+};
+
+bool size_ok(int n) {
+  if (n < 2 || n > kMaxN || (n & 1)) return false;
+  int m = n / 2;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+int make_radix(int m, int* radix) {
+  int ns = 0;
+  while (m % 4 == 0) { radix[ns++] = 4; m /= 4; }
+  while (m % 2 == 0) { radix[ns++] = 2; m /= 2; }
+  while (m % 3 == 0) { radix[ns++] = 3; m /= 3; }
+  return ns;
+}
+
+// θ_q of Table 1 as a multiple of π/(4n): θ_q = π·j/(4n).
+long theta_j(int bc, int n, int q) {
+  switch (bc) {
+    case BC_P: return 4L * ((q + 1) / 2);  // ⌈q/2⌉·π/n; Nyquist q = n−1 gives π/2
+    case BC_NN: return 2L * q;
+    case BC_DD: return 2L * (q + 1);
+    default: return 2L * q + 1;            // ND
+  }
+}
+
+std::vector<double> eig_scaled(int bc, int n, double h) {
+  std::vector<double> lam(n);
+  for (int q = 0; q < n; ++q) {
+    double c, s;
+    cis(theta_j(bc, n, q), 8L * n, &c, &s);  // sin(π j / 4n) = sin(2π j / 8n)
+    lam[q] = -4.0 * s * s / (h * h);
+  }
+  return lam;
+}
+
+void split_df(double d, float2* out) {
+  float h = (float)d;
+  float l = (float)(d - (double)h);
+  out->x = h;
+  out->y = l;
+}
+
+}  // namespace
+
+struct ps_plan {
+  int nx, ny, nz;
+  double dx, dy;
+  int bcx, bcy, bcz;
+  ps_precision prec;
+  double rtol;
+  int max_iter;
+  int singular, periodic_z;
+  size_t N;
+  AxisTab ax, ay;
+  // z tables
+  double *za64, *zb64, *zc64, *dzf64, *idzf64;
+  float *za32, *zb32, *zc32, *dzf32, *idzf32;
+  float2 *zlo, *zhi;
+  double wsum;  // Σ Δz^f (the per-plane weights of the singular mean, times nx·ny)
+  df idx2, idy2;
+  void* dev;    // one allocation for all of the above
+  int resid_blocks;
+  char err[256];
+};
+
+namespace {
+
+ps_status fail(ps_plan* p, ps_status st, const char* msg) {
+  if (p) snprintf(p->err, sizeof(p->err), "%s", msg);
+  else snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+  return st;
+}
+
+ps_status cuda_fail(ps_plan* p, cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  return fail(p, e == cudaErrorMemoryAllocation ? PS_OUT_OF_MEMORY : PS_CUDA_ERROR, buf);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct WsLayout {
+  size_t ctrl, partial, info, w, scr_c, scr_u, total;
+};
+
+WsLayout ws_layout(const ps_plan* p) {
+  WsLayout L{};
+  size_t off = 0;
+  L.ctrl = off;
+  off += align256(sizeof(Ctrl));
+  L.partial = off;
+  off += align256((size_t)p->resid_blocks * 4 * sizeof(float));
+  L.info = off;
+  off += align256(sizeof(ps_info));
+  const size_t tz = (p->prec == PS_FP64) ? sizeof(double) : sizeof(float);
+  L.w = off;
+  if (p->prec == PS_FP32_REFINE) off += align256(p->N * sizeof(float));
+  L.scr_c = off;
+  off += align256(p->N * tz);
+  L.scr_u = off;
+  if (p->periodic_z) off += align256(p->N * tz);
+  L.total = off;
+  return L;
+}
+
+template <class T>
+XformArgs<T> xargs(const ps_plan* p, int axis, const void* in, void* out, const T* scale,
+                   int accumulate, const int* skip) {
+  XformArgs<T> a{};
+  const AxisTab& t = axis == 0 ? p->ax : p->ay;
+  a.in = in;
+  a.out = out;
+  a.n = t.n;
+  a.m = t.m;
+  a.axis = axis;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.nlines = (axis == 0) ? p->ny * p->nz : p->nx * p->nz;
+  a.bc = t.bc;
+  a.nstages = t.nstages;
+  for (int i = 0; i < kMaxStages; ++i) a.radix[i] = t.radix[i];
+  if constexpr (sizeof(T) == 8) a.tw = reinterpret_cast<const cplx<T>*>(t.tw64);
+  else a.tw = reinterpret_cast<const cplx<T>*>(t.tw32);
+  a.plane_scale = scale;
+  a.accumulate = accumulate;
+  a.skip = skip;
+  return a;
+}
+
+template <class T>
+ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int* skip) {
+  ZArgs<T> a{};
+  char* w = static_cast<char*>(ws);
+  a.data = data;
+  a.scr_c = reinterpret_cast<T*>(w + L.scr_c);
+  a.scr_u = p->periodic_z ? reinterpret_cast<T*>(w + L.scr_u) : nullptr;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  if constexpr (sizeof(T) == 8) {
+    a.lamx = p->ax.lam64; a.lamy = p->ay.lam64;
+    a.za = p->za64; a.zb = p->zb64; a.zc = p->zc64; a.dzf = p->dzf64;
+  } else {
+    a.lamx = p->ax.lam32; a.lamy = p->ay.lam32;
+    a.za = p->za32; a.zb = p->zb32; a.zc = p->zc32; a.dzf = p->dzf32;
+  }
+  a.periodic = p->periodic_z;
+  a.singular = p->singular;
+  a.skip = skip;
+  return a;
+}
+
+// The plain five-pass solve in one precision, in place on `p` after the first pass.
+template <class T>
+ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, ps_info* info,
+                      bool transpose) {
+  const WsLayout L = ws_layout(pl);
+  const T* sin_ = nullptr;
+  const T* sout = nullptr;
+  if (transpose) {
+    if constexpr (sizeof(T) == 8) { sin_ = pl->idzf64; sout = pl->dzf64; }
+    else { sin_ = pl->idzf32; sout = pl->dzf32; }
+  }
+  cudaError_t e;
+  if ((e = launch_xform<T, T, T, true>(xargs<T>(pl, 0, f, p, sin_, 0, nullptr), st)) != cudaSuccess)
+    return cuda_fail(pl, e, "x forward");
+  if ((e = launch_xform<T, T, T, true>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st)) != cudaSuccess)
+    return cuda_fail(pl, e, "y forward");
+  if ((e = launch_zsolve<T>(zargs<T>(pl, p, ws, L, nullptr), st)) != cudaSuccess)
+    return cuda_fail(pl, e, "z solve");
+  if ((e = launch_xform<T, T, T, false>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st)) != cudaSuccess)
+    return cuda_fail(pl, e, "y backward");
+  if ((e = launch_xform<T, T, T, false>(xargs<T>(pl, 0, p, p, sout, 0, nullptr), st)) != cudaSuccess)
+    return cuda_fail(pl, e, "x backward");
+  if (info && (e = launch_info_plain(info, st)) != cudaSuccess) return cuda_fail(pl, e, "info");
+  return PS_OK;
+}
+
+// FP32 bulk solve with FP64 iterative refinement (residual in double-float).
+ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaStream_t st,
+                       ps_info* info) {
+  const WsLayout L = ws_layout(pl);
+  char* wb = static_cast<char*>(ws);
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(wb + L.ctrl);
+  float* partial = reinterpret_cast<float*>(wb + L.partial);
+  float* w = reinterpret_cast<float*>(wb + L.w);
+  const int* skip = &ctrl->converged;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(pl, e, "reset");
+  auto correction = [&](bool first) -> cudaError_t {
+    cudaError_t r;
+    if (first) r = launch_xform<float, double, float, true>(xargs<float>(pl, 0, f, w, nullptr, 0, skip), st);
+    else r = launch_xform<float, float, float, true>(xargs<float>(pl, 0, w, w, nullptr, 0, skip), st);
+    if (r != cudaSuccess) return r;
+    if ((r = launch_xform<float, float, float, true>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st)) != cudaSuccess) return r;
+    if ((r = launch_zsolve<float>(zargs<float>(pl, w, ws, L, skip), st)) != cudaSuccess) return r;
+    if ((r = launch_xform<float, float, float, false>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st)) != cudaSuccess) return r;
+    return launch_xform<float, float, double, false>(xargs<float>(pl, 0, w, p, nullptr, first ? 0 : 1, skip), st);
+  };
+  ResidArgs ra{};
+  ra.p = p;
+  ra.f = f;
+  ra.nx = pl->nx;
+  ra.ny = pl->ny;
+  ra.nz = pl->nz;
+  ra.bcx = pl->bcx;
+  ra.bcy = pl->bcy;
+  ra.bcz = pl->bcz;
+  ra.idx2 = pl->idx2;
+  ra.idy2 = pl->idy2;
+  ra.zlo = pl->zlo;
+  ra.zhi = pl->zhi;
+  ra.wz = pl->dzf32;
+  ra.mu = ctrl->mu;
+  ra.singular = pl->singular;
+  ra.red = ctrl->red;
+  ra.partial = partial;
+  ra.nblocks = pl->resid_blocks;
+  ra.skip = skip;
+  const double wsum_total = pl->wsum * pl->nx * pl->ny;
+  if ((e = correction(true)) != cudaSuccess) return cuda_fail(pl, e, "initial solve");
+  for (int it = 1; it <= pl->max_iter; ++it) {
+    ra.r = w;
+    if ((e = launch_residual(ra, st)) != cudaSuccess) return cuda_fail(pl, e, "residual");
+    if ((e = launch_finalize(ctrl, partial, pl->resid_blocks, wsum_total, pl->singular, pl->rtol,
+                             it - 1, 0, info, st)) != cudaSuccess)
+      return cuda_fail(pl, e, "finalize");
+    if ((e = correction(false)) != cudaSuccess) return cuda_fail(pl, e, "correction");
+  }
+  ra.r = nullptr;
+  if ((e = launch_residual(ra, st)) != cudaSuccess) return cuda_fail(pl, e, "residual");
+  if ((e = launch_finalize(ctrl, partial, pl->resid_blocks, wsum_total, pl->singular, pl->rtol,
+                           pl->max_iter, 1, info, st)) != cudaSuccess)
+    return cuda_fail(pl, e, "finalize");
+  return PS_OK;
+}
+
+ps_status check_solve_args(ps_plan* p, const void* f, const void* out, const void* ws) {
+  if (!p) return fail(nullptr, PS_INVALID_ARG, "null plan");
+  if (!f || !out) return fail(p, PS_INVALID_ARG, "null field pointer");
+  if (!ws) return fail(p, PS_INVALID_ARG, "null workspace");
+  if (((uintptr_t)ws) & 255) return fail(p, PS_INVALID_ARG, "workspace must be 256-byte aligned");
+  return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, double dy,
+                         const double* zf, double dz, ps_bc bcx, ps_bc bcy, ps_bc bcz,
+                         ps_precision prec, double rtol, int max_iter) {
+  if (!out) return fail(nullptr, PS_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if ((unsigned)bcx > 3u || (unsigned)bcy > 3u || (unsigned)bcz > 3u)
+    return fail(nullptr, PS_INVALID_ARG, "unknown boundary condition");
+  if ((unsigned)prec > 2u) return fail(nullptr, PS_INVALID_ARG, "unknown precision");
+  if (!(dx > 0) || !(dy > 0)) return fail(nullptr, PS_INVALID_ARG, "dx and dy must be > 0");
+  if (!zf && !(dz > 0)) return fail(nullptr, PS_INVALID_ARG, "dz must be > 0 when zf is NULL");
+  if (!size_ok(nx) || !size_ok(ny))
+    return fail(nullptr, PS_UNSUPPORTED_SIZE, "nx, ny must be even, 2..1024, with n/2 = 2^a 3^b");
+  if (nz < 2 || nz > 8192) return fail(nullptr, PS_UNSUPPORTED_SIZE, "nz must be in 2..8192");
+  if (prec == PS_FP32_REFINE && (max_iter < 0 || !(rtol > 0)))
+    return fail(nullptr, PS_INVALID_ARG, "refinement needs rtol > 0 and max_iter >= 0");
+  std::vector<double> faces(nz + 1);
+  for (int k = 0; k <= nz; ++k) faces[k] = zf ? zf[k] : k * dz;
+  for (int k = 0; k < nz; ++k)
+    if (!(faces[k + 1] > faces[k])) return fail(nullptr, PS_INVALID_ARG, "z faces must increase");
+
+  ps_plan* p = new (std::nothrow) ps_plan();
+  if (!p) return fail(nullptr, PS_OUT_OF_MEMORY, "host allocation failed");
+  p->nx = nx; p->ny = ny; p->nz = nz; p->dx = dx; p->dy = dy;
+  p->bcx = bcx; p->bcy = bcy; p->bcz = bcz;
+  p->prec = prec; p->rtol = rtol; p->max_iter = max_iter;
+  p->N = (size_t)nx * ny * nz;
+  p->periodic_z = (bcz == PS_BC_PERIODIC);
+  auto pn = [](int b) { return b == PS_BC_PERIODIC || b == PS_BC_NEUMANN_NEUMANN; };
+  p->singular = pn(bcx) && pn(bcy) && pn(bcz);
+  {
+    size_t nb = (p->N + 255) / 256;
+    p->resid_blocks = (int)(nb < 152 * 8 ? nb : 152 * 8);
+  }
+
+  // ---- z metric (finite-volume form of Eq. 4 on the faces) ----
+  std::vector<double> dzf(nz), dzc(nz > 1 ? nz - 1 : 0), za(nz, 0.0), zb(nz, 0.0), zc(nz, 0.0);
+  std::vector<float2> zlo(nz), zhi(nz);
+  for (int k = 0; k < nz; ++k) dzf[k] = faces[k + 1] - faces[k];
+  for (int k = 0; k + 1 < nz; ++k) dzc[k] = 0.5 * (faces[k + 2] - faces[k]);
+  std::vector<double> lo(nz, 0.0), hi(nz, 0.0);  // residual coefficients
+  for (int k = 1; k < nz; ++k) za[k] = lo[k] = 1.0 / (dzf[k] * dzc[k - 1]);
+  for (int k = 0; k + 1 < nz; ++k) zc[k] = hi[k] = 1.0 / (dzf[k] * dzc[k]);
+  for (int k = 0; k < nz; ++k) zb[k] = -(za[k] + zc[k]);
+  if (bcz == PS_BC_PERIODIC) {
+    const double hp = 0.5 * (dzf[0] + dzf[nz - 1]);
+    za[0] = lo[0] = 1.0 / (dzf[0] * hp);
+    zc[nz - 1] = hi[nz - 1] = 1.0 / (dzf[nz - 1] * hp);
+    zb[0] -= za[0];
+    zb[nz - 1] -= zc[nz - 1];
+  } else {
+    if (bcz == PS_BC_DIRICHLET_DIRICHLET) {
+      zb[0] -= 2.0 / (dzf[0] * dzf[0]);
+      lo[0] = 1.0 / (dzf[0] * dzf[0]);
+    }
+    if (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_NEUMANN_DIRICHLET) {
+      zb[nz - 1] -= 2.0 / (dzf[nz - 1] * dzf[nz - 1]);
+      hi[nz - 1] = 1.0 / (dzf[nz - 1] * dzf[nz - 1]);
+    }
+  }
+  double wsum = 0.0;
+  for (int k = 0; k < nz; ++k) {
+    split_df(lo[k], &zlo[k]);
+    split_df(hi[k], &zhi[k]);
+    wsum += dzf[k];
+  }
+  p->wsum = wsum;
+  {
+    float2 t;
+    split_df(1.0 / (dx * dx), &t);
+    p->idx2 = df{t.x, t.y};
+    split_df(1.0 / (dy * dy), &t);
+    p->idy2 = df{t.x, t.y};
+  }
+
+  // ---- axis tables ----
+  AxisTab* axes[2] = {&p->ax, &p->ay};
+  const int ns[2] = {nx, ny};
+  const int bcs[2] = {bcx, bcy};
+  const double hs[2] = {dx, dy};
+  size_t bytes = 0;
+  for (int a = 0; a < 2; ++a) {
+    const int n = ns[a];
+    bytes += align256(8 * n * sizeof(cplx<double>)) + align256(8 * n * sizeof(cplx<float>));
+    bytes += align256(n * sizeof(double)) + align256(n * sizeof(float));
+  }
+  bytes += 5 * align256(nz * sizeof(double)) + 5 * align256(nz * sizeof(float)) +
+           2 * align256(nz * sizeof(float2));
+  char* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, bytes);
+  if (e != cudaSuccess) {
+    delete p;
+    char buf[200];
+    snprintf(buf, sizeof(buf), "cudaMalloc of plan tables: %s", cudaGetErrorString(e));
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? PS_OUT_OF_MEMORY : PS_CUDA_ERROR, buf);
+  }
+  p->dev = dev;
+  size_t off = 0;
+  auto take = [&](size_t nbytes) { char* q = dev + off; off += align256(nbytes); return q; };
+  std::vector<char> host(bytes, 0);
+  auto hput = [&](void* devp, const void* src, size_t nbytes) {
+    memcpy(host.data() + (static_cast<char*>(devp) - dev), src, nbytes);
+  };
+  for (int a = 0; a < 2; ++a) {
+    AxisTab& t = *axes[a];
+    const int n = ns[a];
+    t.n = n;
+    t.m = n / 2;
+    t.bc = bcs[a];
+    t.nstages = make_radix(t.m, t.radix);
+    t.tw64 = reinterpret_cast<cplx<double>*>(take(8 * n * sizeof(cplx<double>)));
+    t.tw32 = reinterpret_cast<cplx<float>*>(take(8 * n * sizeof(cplx<float>)));
+    t.lam64 = reinterpret_cast<double*>(take(n * sizeof(double)));
+    t.lam32 = reinterpret_cast<float*>(take(n * sizeof(float)));
+    std::vector<cplx<double>> tw64(8 * n);
+    std::vector<cplx<float>> tw32(8 * n);
+    for (int i = 0; i < 8 * n; ++i) {
+      double c, s;
+      cis(i, 8L * n, &c, &s);
+      tw64[i] = {c, -s};  // e^{−2πi t/(8n)}
+      tw32[i] = {(float)c, (float)-s};
+    }
+    std::vector<double> lam = eig_scaled(t.bc, n, hs[a]);
+    std::vector<float> lam32(lam.begin(), lam.end());
+    hput(t.tw64, tw64.data(), tw64.size() * sizeof(tw64[0]));
+    hput(t.tw32, tw32.data(), tw32.size() * sizeof(tw32[0]));
+    hput(t.lam64, lam.data(), n * sizeof(double));
+    hput(t.lam32, lam32.data(), n * sizeof(float));
+  }
+  double** d64[5] = {&p->za64, &p->zb64, &p->zc64, &p->dzf64, &p->idzf64};
+  float** d32[5] = {&p->za32, &p->zb32, &p->zc32, &p->dzf32, &p->idzf32};
+  std::vector<double> idzf(nz);
+  for (int k = 0; k < nz; ++k) idzf[k] = 1.0 / dzf[k];
+  const std::vector<double>* srcs[5] = {&za, &zb, &zc, &dzf, &idzf};
+  for (int i = 0; i < 5; ++i) {
+    *d64[i] = reinterpret_cast<double*>(take(nz * sizeof(double)));
+    *d32[i] = reinterpret_cast<float*>(take(nz * sizeof(float)));
+    std::vector<float> f32(srcs[i]->begin(), srcs[i]->end());
+    hput(*d64[i], srcs[i]->data(), nz * sizeof(double));
+    hput(*d32[i], f32.data(), nz * sizeof(float));
+  }
+  p->zlo = reinterpret_cast<float2*>(take(nz * sizeof(float2)));
+  p->zhi = reinterpret_cast<float2*>(take(nz * sizeof(float2)));
+  hput(p->zlo, zlo.data(), nz * sizeof(float2));
+  hput(p->zhi, zhi.data(), nz * sizeof(float2));
+  e = cudaMemcpy(dev, host.data(), bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    delete p;
+    return fail(nullptr, PS_CUDA_ERROR, "copy of plan tables failed");
+  }
+  p->err[0] = 0;
+  *out = p;
+  return PS_OK;
+}
+
+ps_status ps_workspace_bytes(const ps_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(nullptr, PS_INVALID_ARG, "null argument");
+  *bytes = ws_layout(plan).total;
+  return PS_OK;
+}
+
+ps_status ps_solve(ps_plan* plan, const double* f, double* p, void* ws, void* stream, ps_info* info) {
+  ps_status s = check_solve_args(plan, f, p, ws);
+  if (s != PS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->prec == PS_FP64) return solve_plain<double>(plan, f, p, ws, st, info, false);
+  if (plan->prec == PS_FP32_REFINE) {
+    if (f == p) return fail(plan, PS_INVALID_ARG, "in-place solve is not allowed with refinement");
+    return solve_refine(plan, f, p, ws, st, info);
+  }
+  return fail(plan, PS_INVALID_ARG, "FP32 plans take float fields: use ps_solve_f32");
+}
+
+ps_status ps_solve_f32(ps_plan* plan, const float* f, float* p, void* ws, void* stream, ps_info* info) {
+  ps_status s = check_solve_args(plan, f, p, ws);
+  if (s != PS_OK) return s;
+  if (plan->prec != PS_FP32) return fail(plan, PS_INVALID_ARG, "ps_solve_f32 needs a PS_FP32 plan");
+  return solve_plain<float>(plan, f, p, ws, static_cast<cudaStream_t>(stream), info, false);
+}
+
+ps_status ps_solve_transpose(ps_plan* plan, const double* g, double* p, void* ws, void* stream,
+                             ps_info* info) {
+  ps_status s = check_solve_args(plan, g, p, ws);
+  if (s != PS_OK) return s;
+  if (plan->prec == PS_FP64)
+    return solve_plain<double>(plan, g, p, ws, static_cast<cudaStream_t>(stream), info, true);
+  return fail(plan, PS_INVALID_ARG, "ps_solve_transpose needs a PS_FP64 plan");
+}
+
+ps_status ps_solve_transpose_f32(ps_plan* plan, const float* g, float* p, void* ws, void* stream,
+                                 ps_info* info) {
+  ps_status s = check_solve_args(plan, g, p, ws);
+  if (s != PS_OK) return s;
+  if (plan->prec != PS_FP32) return fail(plan, PS_INVALID_ARG, "needs a PS_FP32 plan");
+  return solve_plain<float>(plan, g, p, ws, static_cast<cudaStream_t>(stream), info, true);
+}
+
+ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, double* f_dev,
+                        double* p_dev, void* ws, void* stream, ps_info* info_host) {
+  ps_status s = check_solve_args(plan, f_dev, p_dev, ws);
+  if (s != PS_OK) return s;
+  if (!f_host || !p_host) return fail(plan, PS_INVALID_ARG, "null host pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = plan->N * sizeof(double);
+  ps_info* info_dev = reinterpret_cast<ps_info*>(static_cast<char*>(ws) + ws_layout(plan).info);
+  cudaError_t e = cudaMemcpyAsync(f_dev, f_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "host to device copy");
+  s = ps_solve(plan, f_dev, p_dev, ws, stream, info_dev);
+  if (s != PS_OK) return s;
+  if ((e = cudaMemcpyAsync(p_host, p_dev, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(plan, e, "device to host copy");
+  if (info_host && (e = cudaMemcpyAsync(info_host, info_dev, sizeof(ps_info), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(plan, e, "info copy");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(plan, e, "stream synchronize");
+  return PS_OK;
+}
+
+ps_status ps_plan_destroy(ps_plan* plan) {
+  if (!plan) return PS_OK;
+  if (plan->dev) cudaFree(plan->dev);
+  delete plan;
+  return PS_OK;
+}
+
+const char* ps_last_error(const ps_plan* plan) { return plan ? plan->err : g_create_err; }
+
+}  // extern "C"

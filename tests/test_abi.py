@@ -1,0 +1,75 @@
+"""The C-ABI library loads, exports every symbol its header declares, and
+rejects invalid plans on the host (no GPU needed for any of this)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            src = open(os.path.join(inc, fn)).read()
+            names |= set(re.findall(r"^(?:ps_status|const char\*)\s+(ps_\w+)\s*\(", src, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_1802_10323_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_1802_10323_gb300 import binding as b
+    return b
+
+
+def test_every_declared_symbol_is_exported(binding):
+    declared = _declared()
+    assert len(declared) >= 12
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(binding.EXPORTS)
+
+
+@pytest.mark.parametrize("n,status", [(0, 2), (3, 2), (7, 2), (2048, 2), (10, 2), (14, 2)])
+def test_unsupported_sizes_rejected(binding, n, status):
+    h = ctypes.c_void_p()
+    st = binding.ps_plan_create(ctypes.byref(h), n, 8, 8, 1.0, 1.0, None, 1.0, 0, 0, 1, 0, 1e-10, 3)
+    assert st == status
+    assert not h.value
+    assert b"n/2" in binding.ps_last_error(None) or b"nx" in binding.ps_last_error(None)
+
+
+@pytest.mark.parametrize("kw", [dict(dx=0.0), dict(dz=-1.0), dict(bcx=7), dict(prec=9),
+                                dict(prec=2, rtol=0.0), dict(prec=2, max_iter=-1)])
+def test_invalid_arguments_rejected(binding, kw):
+    a = dict(nx=8, ny=8, nz=8, dx=1.0, dy=1.0, dz=1.0, bcx=0, bcy=0, bcz=1, prec=0, rtol=1e-10, max_iter=3)
+    a.update(kw)
+    h = ctypes.c_void_p()
+    st = binding.ps_plan_create(ctypes.byref(h), a["nx"], a["ny"], a["nz"], a["dx"], a["dy"], None,
+                                a["dz"], a["bcx"], a["bcy"], a["bcz"], a["prec"], a["rtol"], a["max_iter"])
+    assert st == binding.PS_INVALID_ARG
+    assert not h.value
+
+
+def test_non_increasing_faces_rejected(binding):
+    zf = (ctypes.c_double * 5)(0.0, 1.0, 1.0, 2.0, 3.0)
+    h = ctypes.c_void_p()
+    st = binding.ps_plan_create(ctypes.byref(h), 8, 8, 4, 1.0, 1.0, ctypes.cast(zf, ctypes.c_void_p),
+                                0.0, 0, 0, 1, 0, 1e-10, 3)
+    assert st == binding.PS_INVALID_ARG
+
+
+def test_null_arguments(binding):
+    assert binding.ps_plan_create(None, 8, 8, 8, 1.0, 1.0, None, 1.0, 0, 0, 1, 0, 1e-10, 3) == binding.PS_INVALID_ARG
+    assert binding.ps_solve(None, None, None, None, None, None) == binding.PS_INVALID_ARG
+    assert binding.ps_plan_destroy(None) == binding.PS_OK
+    n = ctypes.c_size_t()
+    assert binding.ps_workspace_bytes(None, ctypes.byref(n)) == binding.PS_INVALID_ARG
