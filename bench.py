@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput of the eigenfunction-expansion Poisson solve on the channel workload.
+
+Workload (one step = one complete solve): 1024 × 1024 × 1024 cells on a
+6 × 3 × 1 box, periodic x and y, Neumann–Neumann z on a tanh grid (α = 1.5);
+right-hand side f = discrete divergence of a seeded Gaussian staggered
+velocity field (w = 0 on the walls). The timed path is the FP32 bulk solve
+with FP64 iterative refinement to a relative residual of 1e-10 (checked on
+the device every step); the plain FP64 GPU solve of the same input is timed
+beside it. Inputs are resident in HBM (8.6 GB per field, far above the
+126 MB L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (torchrun; weak scaling, no
+collective on the data path). ``--impl reference`` times the FP64 CPU oracle
+(test infrastructure) on a bounded sample of the same workload.
+
+Printed: one JSON line on rank 0.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solve Mpts/s at 1024^3 (FP32+refine vs FP64) and % of HBM roofline"
+GRID = dict(nx=1024, ny=1024, nz=1024, lx=6.0, ly=3.0, lz=1.0, alpha=1.5, seed=3)
+BCS = ("P", "P", "NN")
+RTOL = 1e-10
+MAX_ITER = 4
+
+# Algorithmic bytes per grid point of each kernel kind (compulsory reads + writes
+# of the fields it must touch; scratch traffic is not counted).
+BYTES_PER_POINT = {
+    "refine": {"x_fwd_f64in": 8 + 4, "x_fwd": 4 + 4, "y_fwd": 4 + 4, "z_solve": 4 + 4,
+               "y_bwd": 4 + 4, "x_bwd_f64store": 4 + 8, "x_bwd_f64acc": 4 + 8 + 8,
+               "residual": 8 + 8 + 4, "residual_check": 8 + 8},
+    "fp64": {"x_fwd": 16, "y_fwd": 16, "z_solve": 16, "y_bwd": 16, "x_bwd": 16},
+}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1802_10323_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, n_points):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent["dram_bytes_per_point"] * n_points
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_input(n, seed, device):
+    """Channel right-hand side on the device (seeded Philox), FP64, and the z faces."""
+    from paper_1802_10323_gb300 import synth
+    zf = synth.tanh_faces(n[2], GRID["lz"], GRID["alpha"])
+    dx, dy = GRID["lx"] / n[0], GRID["ly"] / n[1]
+    u, v, w = synth.staggered_velocity_torch(n[0], n[1], n[2], seed, device=device)
+    f = synth.divergence_rhs_torch(u, v, w, dx, dy, zf)
+    del u, v, w
+    return f.contiguous(), zf, dx, dy
+
+
+def cpu_oracle_rate(nz_sample=None, target_s=15.0):
+    """Mpts/s of the FP64 oracle solve on a 1024 × 1024 × nz_sample slab of the workload."""
+    import numpy as np
+    from oracle import solve as S
+    from paper_1802_10323_gb300 import synth
+
+    def run(nzs):
+        zf = synth.tanh_faces(nzs, GRID["lz"], GRID["alpha"])
+        dx, dy = GRID["lx"] / GRID["nx"], GRID["ly"] / GRID["ny"]
+        u, v, w = synth.staggered_velocity(GRID["nx"], GRID["ny"], nzs, GRID["seed"])
+        f = synth.divergence_rhs(u, v, w, dx, dy, zf)
+        del u, v, w
+        t0 = time.perf_counter()
+        S.solve(f, dx, dy, zf, *BCS)
+        return time.perf_counter() - t0
+
+    if nz_sample is None:
+        t8 = run(8)
+        nz_sample = int(min(256, max(8, 8 * target_s / max(t8, 1e-3))) // 8 * 8)
+    t = run(nz_sample)
+    pts = GRID["nx"] * GRID["ny"] * nz_sample
+    cores = len(os.sched_getaffinity(0))
+    try:
+        blas = np.__config__.CONFIG["Build Dependencies"]["blas"]["name"]
+    except Exception:
+        blas = "unknown"
+    return {"value": pts / t / 1e6, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 oracle solve (dense Table 2 matmuls + Thomas) of a "
+                      f"1024x1024x{nz_sample} slab of the channel workload "
+                      f"(same x/y sizes, BCs, tanh z), {t:.1f} s; BLAS={blas}, "
+                      f"threads={cores}"}
+
+
+def bench_reference(args):
+    """The FP64 CPU oracle, as it stands, on a bounded slab of the workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    nzs = 16
+    for _ in range(args.warmup):
+        cpu_oracle_rate(nz_sample=nzs)
+    runs = [cpu_oracle_rate(nz_sample=nzs) for _ in range(args.steps)]
+    v = statistics.median(r["value"] for r in runs)
+    cpu = dict(runs[0])
+    cpu["value"] = v
+    pts = GRID["nx"] * GRID["ny"] * nzs
+    line = {"metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": pts / v / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"channel 1024x1024x{nzs} slab (bounded CPU sample of the 1024^3 "
+                                   "workload), P/P/NN, tanh z 1.5", "parallelism": "none (host cores)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_ours(args):
+    import torch
+    from paper_1802_10323_gb300 import binding as lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = (args.n, args.n, args.n)
+    N = n[0] * n[1] * n[2]
+    f, zf, dx, dy = make_input(n, GRID["seed"], dev)
+    plan = lib.Plan(n[0], n[1], n[2], dx, dy, zf=zf, bcs=BCS, precision="fp32_refine",
+                    rtol=RTOL, max_iter=MAX_ITER)
+    p = torch.empty_like(f)
+    info = lib.info_tensor(dev)
+    ws = plan.workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.solve(f, p, info=info)
+    torch.cuda.synchronize()
+    inf = lib.read_info(info)
+    if inf.status != 0:
+        raise SystemExit(f"refined solve did not converge: status {inf.status}, rel {inf.rel_residual}")
+
+    # ---- timed region: K refined solves ----
+    plan.profile(True)
+    clk = Clocks(local)
+    time.sleep(0.4)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.solve(f, p, info=info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms)
+    prof = plan.profile_read()
+    plan.profile(False)
+    inf = lib.read_info(info)
+    value = world * N / (ms_max * 1e-3) / 1e6
+
+    # dominant kernel and its roofline
+    bpp = BYTES_PER_POINT["refine"]
+    dom, dom_ms = None, -1.0
+    for k, (launches, active, tot, act_ms) in prof.items():
+        if k in bpp and act_ms > dom_ms:
+            dom, dom_ms = k, act_ms
+    launches, active, tot, act_ms = prof[dom]
+    avg_ms = act_ms / max(active, 1)
+    bytes_launch = bpp[dom] * N
+    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+    peak, peak_src = peaks()
+    gpu_launches = sum(v[0] for v in prof.values()) + prof.get("residual", (0,))[0] \
+        + prof.get("residual_check", (0,))[0]
+    kernels = {k: {"launches": v[0], "active": v[1], "active_ms_per_step": v[3] / args.steps,
+                   "share": v[3] / max(sum(x[3] for x in prof.values()), 1e-9)}
+               for k, v in prof.items() if v[0]}
+
+    # ---- plain FP64 GPU solve of the same input (the comparison) ----
+    plan64 = lib.Plan(n[0], n[1], n[2], dx, dy, zf=zf, bcs=BCS, precision="fp64")
+    p64 = torch.empty_like(f)
+    plan64.solve(f, p64)
+    torch.cuda.synchronize()
+    k64 = max(1, args.fp64_steps)
+    plan64.profile(True)
+    e0.record(stream)
+    for _ in range(k64):
+        plan64.solve(f, p64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(e0.elapsed_time(e1) / k64)
+    prof64 = plan64.profile_read()
+    diff = (p - p64).abs().max().item() / p64.abs().max().item()
+    del p64
+    plan64.close()
+
+    # ---- end to end through the public host-buffer call ----
+    e2e = None
+    if not args.no_e2e:
+        fh = f.cpu().pin_memory()
+        ph = torch.empty_like(fh).pin_memory()
+        plan.solve_host(fh, ph, f, p)  # warm
+        barrier()
+        t0 = time.perf_counter()
+        k_e2e = max(1, min(args.steps, 3))
+        for _ in range(k_e2e):
+            ie = plan.solve_host(fh, ph, f, p)
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e)
+        e2e = {"value": world * N / t_e2e / 1e6, "unit": "Mpts/s",
+               "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8 + 32,
+               "ms_per_step": t_e2e * 1e3, "status": ie.status}
+        del fh, ph
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bulk) + double-float residual", "data": "synthetic",
+            "config": {"workload": f"channel {n[0]}x{n[1]}x{n[2]}, 6x3x1 box, P/P/NN, tanh z alpha=1.5, "
+                                   "f = div(Gaussian staggered velocity), seed 3",
+                       "grid": list(n), "precision": "fp32_refine", "rtol": RTOL, "max_iter": MAX_ITER,
+                       "l2": "no flush: every field (8.6 GB at 1024^3) exceeds the 126 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "refine": {"iterations": inf.iterations, "rel_residual": inf.rel_residual,
+                       "status": inf.status},
+            "fp64_solve": {"value": world * N / (ms64 * 1e-3) / 1e6, "unit": "Mpts/s",
+                           "ms_per_step": ms64, "max_rel_diff_vs_refined": diff,
+                           "kernels": {k: v[3] / k64 for k, v in prof64.items() if v[0]}},
+            "speedup_vs_fp64": ms64 / ms_max,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "algorithmic_bytes_per_launch": bytes_launch,
+                         "avg_launch_ms": avg_ms, "traffic": recorded_traffic(dom, N)},
+            "kernels": kernels,
+            "gpu_launches": int(gpu_launches),
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024, help="cells per axis (default: the 1024^3 workload)")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -136,6 +136,31 @@ ps_status ps_plan_destroy(ps_plan* plan);
  * for plan == NULL, of the last failed ps_plan_create / ps_batch_create). */
 const char* ps_last_error(const ps_plan* plan);
 
+/* ---- Per-kernel timing (optional) --------------------------------------------
+ * When enabled on a plan, every kernel launch of its solves is bracketed by a
+ * pair of CUDA events recorded on the solve's stream (no host synchronisation
+ * is added to the solve). ps_profile_read synchronises those events, sums the
+ * durations per kernel kind and clears the record. A launch whose duration is
+ * below a quarter of the longest launch of its kind in the window counts as
+ * "skipped" (refinement kernels return at once after convergence). */
+typedef struct {
+  char name[24];          /* kernel kind: x_fwd, x_fwd_f64in, y_fwd, z_solve, z_singular,
+                             y_bwd, x_bwd, x_bwd_f64store, x_bwd_f64acc, residual,
+                             residual_check, control */
+  int launches;           /* all launches in the window                         */
+  int active_launches;    /* launches that did work (see above)                 */
+  double total_ms;        /* summed duration of all launches                    */
+  double active_ms;       /* summed duration of the active launches             */
+} ps_kernel_stat;
+
+/* Turn event bracketing on (1) or off (0); up to 4096 launches are recorded
+ * per window, later ones are dropped and counted in the next read's totals as
+ * missing. */
+ps_status ps_profile_enable(ps_plan* plan, int enable);
+
+/* Fill up to `max` entries (one per kernel kind), set *count, clear the window. */
+ps_status ps_profile_read(ps_plan* plan, ps_kernel_stat* stats, int max, int* count);
+
 /* ---- Batched solve: many independent grids, one persistent launch ----------
  * Each grid is an independent problem of §2.1 with its own sizes, spacings,
  * z faces and BC pairs. */

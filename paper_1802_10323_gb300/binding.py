@@ -44,6 +44,12 @@ class PsGridDesc(ctypes.Structure):
                 ("bcx", ctypes.c_int), ("bcy", ctypes.c_int), ("bcz", ctypes.c_int)]
 
 
+class PsKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int),
+                ("active_launches", ctypes.c_int), ("total_ms", ctypes.c_double),
+                ("active_ms", ctypes.c_double)]
+
+
 _vp, _i, _d, _st = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int
 _SIGS = {
     "ps_plan_create": [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _vp, _d, _i, _i, _i, _i, _d, _i],
@@ -54,6 +60,8 @@ _SIGS = {
     "ps_solve_transpose_f32": [_vp, _vp, _vp, _vp, _vp, _vp],
     "ps_solve_host": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "ps_plan_destroy": [_vp],
+    "ps_profile_enable": [_vp, _i],
+    "ps_profile_read": [_vp, ctypes.POINTER(PsKernelStat), _i, ctypes.POINTER(_i)],
     "ps_batch_create": [ctypes.POINTER(_vp), _i, ctypes.POINTER(PsGridDesc), _i, _d, _i],
     "ps_batch_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "ps_batch_solve": [_vp, _vp, _vp, _vp, _vp, _vp],
@@ -160,6 +168,17 @@ class Plan:
                                   _vp(f_dev.data_ptr()), _vp(p_dev.data_ptr()), _vp(ws.data_ptr()),
                                   _stream_ptr(stream), ctypes.cast(ctypes.byref(info), _vp)), self.handle)
         return info
+
+    def profile(self, enable=True):
+        _check(_lib.ps_profile_enable(self.handle, 1 if enable else 0), self.handle)
+
+    def profile_read(self):
+        """Per-kernel-kind timing since the last read: {name: (launches, active, total_ms, active_ms)}."""
+        arr = (PsKernelStat * 16)()
+        n = ctypes.c_int()
+        _check(_lib.ps_profile_read(self.handle, arr, 16, ctypes.byref(n)), self.handle)
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].active_launches, arr[i].total_ms,
+                                       arr[i].active_ms) for i in range(n.value)}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -55,6 +55,8 @@ struct ZArgs {
 
 template <class T>
 cudaError_t launch_zsolve(ZArgs<T> a, cudaStream_t st);
+template <class T>
+cudaError_t launch_zsingular(ZArgs<T> a, cudaStream_t st);
 
 // Residual r = f − A·p (double-float), written as FP32, with reductions.
 struct ResidArgs {

@@ -99,7 +99,25 @@ void split_df(double d, float2* out) {
 
 }  // namespace
 
+// Kernel kinds for the optional timing; each kind moves a fixed number of bytes
+// per grid point (the FP32 refinement path has separate kinds for its FP64-input
+// x pass, its storing and accumulating x passes and its check-only residual).
+enum Kind { K_XF = 0, K_XF64IN, K_YF, K_Z, K_ZS, K_YB, K_XB, K_XB64ST, K_XB64ACC, K_RES, K_CHK,
+            K_CTL, K_NKINDS };
+static const char* kKindName[K_NKINDS] = {"x_fwd", "x_fwd_f64in", "y_fwd", "z_solve",
+                                          "z_singular", "y_bwd", "x_bwd", "x_bwd_f64store",
+                                          "x_bwd_f64acc", "residual", "residual_check", "control"};
+constexpr int kProfMax = 4096;
+
+struct Prof {
+  int on = 0;
+  int n = 0;
+  std::vector<cudaEvent_t> ev;  // 2 per recorded launch
+  std::vector<int> kind;
+};
+
 struct ps_plan {
+  Prof prof;
   int nx, ny, nz;
   double dx, dy;
   int bcx, bcy, bcz;
@@ -208,6 +226,21 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
   return a;
 }
 
+// Launch `fn` on `st`, bracketed by profiling events when enabled on the plan.
+template <class F>
+cudaError_t run(ps_plan* pl, int kind, cudaStream_t st, F&& fn) {
+  Prof& pr = pl->prof;
+  const bool rec = pr.on && pr.n < kProfMax;
+  if (rec) cudaEventRecord(pr.ev[2 * pr.n], st);
+  cudaError_t e = fn();
+  if (rec) {
+    cudaEventRecord(pr.ev[2 * pr.n + 1], st);
+    pr.kind[pr.n] = kind;
+    ++pr.n;
+  }
+  return e;
+}
+
 // The plain five-pass solve in one precision, in place on `p` after the first pass.
 template <class T>
 ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, ps_info* info,
@@ -220,17 +253,21 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
     else { sin_ = pl->idzf32; sout = pl->dzf32; }
   }
   cudaError_t e;
-  if ((e = launch_xform<T, T, T, true>(xargs<T>(pl, 0, f, p, sin_, 0, nullptr), st)) != cudaSuccess)
+  if ((e = run(pl, K_XF, st, [&] { return launch_xform<T, T, T, true>(xargs<T>(pl, 0, f, p, sin_, 0, nullptr), st); })) != cudaSuccess)
     return cuda_fail(pl, e, "x forward");
-  if ((e = launch_xform<T, T, T, true>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st)) != cudaSuccess)
+  if ((e = run(pl, K_YF, st, [&] { return launch_xform<T, T, T, true>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st); })) != cudaSuccess)
     return cuda_fail(pl, e, "y forward");
-  if ((e = launch_zsolve<T>(zargs<T>(pl, p, ws, L, nullptr), st)) != cudaSuccess)
+  const ZArgs<T> za = zargs<T>(pl, p, ws, L, nullptr);
+  if ((e = run(pl, K_Z, st, [&] { return launch_zsolve<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z solve");
-  if ((e = launch_xform<T, T, T, false>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st)) != cudaSuccess)
+  if (pl->singular && (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
+    return cuda_fail(pl, e, "z singular column");
+  if ((e = run(pl, K_YB, st, [&] { return launch_xform<T, T, T, false>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st); })) != cudaSuccess)
     return cuda_fail(pl, e, "y backward");
-  if ((e = launch_xform<T, T, T, false>(xargs<T>(pl, 0, p, p, sout, 0, nullptr), st)) != cudaSuccess)
+  if ((e = run(pl, K_XB, st, [&] { return launch_xform<T, T, T, false>(xargs<T>(pl, 0, p, p, sout, 0, nullptr), st); })) != cudaSuccess)
     return cuda_fail(pl, e, "x backward");
-  if (info && (e = launch_info_plain(info, st)) != cudaSuccess) return cuda_fail(pl, e, "info");
+  if (info && (e = run(pl, K_CTL, st, [&] { return launch_info_plain(info, st); })) != cudaSuccess)
+    return cuda_fail(pl, e, "info");
   return PS_OK;
 }
 
@@ -245,15 +282,19 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   const int* skip = &ctrl->converged;
   cudaError_t e;
   if ((e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(pl, e, "reset");
+  const ZArgs<float> zw = zargs<float>(pl, w, ws, L, skip);
   auto correction = [&](bool first) -> cudaError_t {
     cudaError_t r;
-    if (first) r = launch_xform<float, double, float, true>(xargs<float>(pl, 0, f, w, nullptr, 0, skip), st);
-    else r = launch_xform<float, float, float, true>(xargs<float>(pl, 0, w, w, nullptr, 0, skip), st);
+    if (first)
+      r = run(pl, K_XF64IN, st, [&] { return launch_xform<float, double, float, true>(xargs<float>(pl, 0, f, w, nullptr, 0, skip), st); });
+    else
+      r = run(pl, K_XF, st, [&] { return launch_xform<float, float, float, true>(xargs<float>(pl, 0, w, w, nullptr, 0, skip), st); });
     if (r != cudaSuccess) return r;
-    if ((r = launch_xform<float, float, float, true>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st)) != cudaSuccess) return r;
-    if ((r = launch_zsolve<float>(zargs<float>(pl, w, ws, L, skip), st)) != cudaSuccess) return r;
-    if ((r = launch_xform<float, float, float, false>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st)) != cudaSuccess) return r;
-    return launch_xform<float, float, double, false>(xargs<float>(pl, 0, w, p, nullptr, first ? 0 : 1, skip), st);
+    if ((r = run(pl, K_YF, st, [&] { return launch_xform<float, float, float, true>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st); })) != cudaSuccess) return r;
+    if ((r = run(pl, K_Z, st, [&] { return launch_zsolve<float>(zw, st); })) != cudaSuccess) return r;
+    if (pl->singular && (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
+    if ((r = run(pl, K_YB, st, [&] { return launch_xform<float, float, float, false>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st); })) != cudaSuccess) return r;
+    return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] { return launch_xform<float, float, double, false>(xargs<float>(pl, 0, w, p, nullptr, first ? 0 : 1, skip), st); });
   };
   ResidArgs ra{};
   ra.p = p;
@@ -277,19 +318,18 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   ra.skip = skip;
   const double wsum_total = pl->wsum * pl->nx * pl->ny;
   if ((e = correction(true)) != cudaSuccess) return cuda_fail(pl, e, "initial solve");
-  for (int it = 1; it <= pl->max_iter; ++it) {
-    ra.r = w;
-    if ((e = launch_residual(ra, st)) != cudaSuccess) return cuda_fail(pl, e, "residual");
-    if ((e = launch_finalize(ctrl, partial, pl->resid_blocks, wsum_total, pl->singular, pl->rtol,
-                             it - 1, 0, info, st)) != cudaSuccess)
+  for (int it = 0; it <= pl->max_iter; ++it) {
+    const bool last = (it == pl->max_iter);
+    ra.r = last ? nullptr : w;
+    if ((e = run(pl, last ? K_CHK : K_RES, st, [&] { return launch_residual(ra, st); })) != cudaSuccess)
+      return cuda_fail(pl, e, "residual");
+    if ((e = run(pl, K_CTL, st, [&] {
+           return launch_finalize(ctrl, partial, pl->resid_blocks, wsum_total, pl->singular,
+                                  pl->rtol, it, last ? 1 : 0, info, st);
+         })) != cudaSuccess)
       return cuda_fail(pl, e, "finalize");
-    if ((e = correction(false)) != cudaSuccess) return cuda_fail(pl, e, "correction");
+    if (!last && (e = correction(false)) != cudaSuccess) return cuda_fail(pl, e, "correction");
   }
-  ra.r = nullptr;
-  if ((e = launch_residual(ra, st)) != cudaSuccess) return cuda_fail(pl, e, "residual");
-  if ((e = launch_finalize(ctrl, partial, pl->resid_blocks, wsum_total, pl->singular, pl->rtol,
-                           pl->max_iter, 1, info, st)) != cudaSuccess)
-    return cuda_fail(pl, e, "finalize");
   return PS_OK;
 }
 
@@ -522,8 +562,57 @@ ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, dou
   return PS_OK;
 }
 
+ps_status ps_profile_enable(ps_plan* plan, int enable) {
+  if (!plan) return fail(nullptr, PS_INVALID_ARG, "null plan");
+  Prof& pr = plan->prof;
+  if (enable && pr.ev.empty()) {
+    pr.ev.resize(2 * kProfMax);
+    pr.kind.resize(kProfMax);
+    for (auto& ev : pr.ev) {
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(plan, e, "cudaEventCreate");
+    }
+  }
+  pr.on = enable ? 1 : 0;
+  pr.n = 0;
+  return PS_OK;
+}
+
+ps_status ps_profile_read(ps_plan* plan, ps_kernel_stat* stats, int max, int* count) {
+  if (!plan || !stats || !count) return fail(nullptr, PS_INVALID_ARG, "null argument");
+  Prof& pr = plan->prof;
+  std::vector<float> ms(pr.n, 0.f);
+  float kmax[K_NKINDS] = {0};
+  for (int i = 0; i < pr.n; ++i) {
+    cudaError_t e = cudaEventSynchronize(pr.ev[2 * i + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], pr.ev[2 * i], pr.ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "event timing");
+    if (ms[i] > kmax[pr.kind[i]]) kmax[pr.kind[i]] = ms[i];
+  }
+  int c = 0;
+  for (int k = 0; k < K_NKINDS && c < max; ++k) {
+    ps_kernel_stat& st = stats[c];
+    memset(&st, 0, sizeof(st));
+    snprintf(st.name, sizeof(st.name), "%s", kKindName[k]);
+    for (int i = 0; i < pr.n; ++i) {
+      if (pr.kind[i] != k) continue;
+      st.launches++;
+      st.total_ms += ms[i];
+      if (ms[i] >= 0.25f * kmax[k]) {
+        st.active_launches++;
+        st.active_ms += ms[i];
+      }
+    }
+    ++c;
+  }
+  *count = c;
+  pr.n = 0;
+  return PS_OK;
+}
+
 ps_status ps_plan_destroy(ps_plan* plan) {
   if (!plan) return PS_OK;
+  for (auto& ev : plan->prof.ev) cudaEventDestroy(ev);
   if (plan->dev) cudaFree(plan->dev);
   delete plan;
   return PS_OK;

@@ -153,14 +153,22 @@ template <class T>
 cudaError_t launch_zsolve(ZArgs<T> a, cudaStream_t st) {
   const int ncol = a.nx * a.ny;
   zsolve_kernel<T><<<(ncol + 127) / 128, 128, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !a.singular) return e;
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_zsingular(ZArgs<T> a, cudaStream_t st) {
   const size_t smem = 2 * (size_t)a.nz * sizeof(T);
-  zsingular_kernel<T><<<1, 256, smem, st>>>(a);
+  auto k = zsingular_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<1, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_zsolve<double>(ZArgs<double>, cudaStream_t);
 template cudaError_t launch_zsolve<float>(ZArgs<float>, cudaStream_t);
+template cudaError_t launch_zsingular<double>(ZArgs<double>, cudaStream_t);
+template cudaError_t launch_zsingular<float>(ZArgs<float>, cudaStream_t);
 
 }  // namespace ps
