@@ -12,6 +12,7 @@ namespace ps {
 enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3 };
 constexpr int kMaxN = 1024;
 constexpr int kMaxStages = 12;
+extern thread_local char g_launch_diag[256];  // configuration of the last failed launch
 
 // Arguments of one batch of line transforms (x or y).
 template <class T>

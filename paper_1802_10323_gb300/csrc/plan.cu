@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "xform_fast.cuh"
 
 using namespace ps;
 
@@ -148,7 +149,7 @@ ps_status fail(ps_plan* p, ps_status st, const char* msg) {
 
 ps_status cuda_fail(ps_plan* p, cudaError_t e, const char* where) {
   char buf[256];
-  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  snprintf(buf, sizeof(buf), "%s: %s [%s]", where, cudaGetErrorString(e), g_launch_diag);
   return fail(p, e == cudaErrorMemoryAllocation ? PS_OUT_OF_MEMORY : PS_CUDA_ERROR, buf);
 }
 
@@ -226,6 +227,40 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
   return a;
 }
 
+// One pass of line transforms along x (axis 0) or y (axis 1): the register-resident
+// kernel for n ∈ {128, 256, 512, 1024} when the tile fits, else the generic one.
+template <class T, class TI, class TO, bool FWD>
+cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, const T* scale,
+                       int accumulate, const int* skip, cudaStream_t st) {
+  const AxisTab& t = axis == 0 ? p->ax : p->ay;
+  const int lpc_y = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
+  const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) &&
+                       (axis == 0 || p->nx % lpc_y == 0);
+  if (fast_ok) {
+    FastArgs<T> a{};
+    a.in = in;
+    a.out = out;
+    a.axis = axis;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.nz = p->nz;
+    a.bc = t.bc;
+    a.nlines = (axis == 0) ? p->ny * p->nz : p->nx * p->nz;
+    if constexpr (sizeof(T) == 8) a.tw = reinterpret_cast<const cplx<T>*>(t.tw64);
+    else a.tw = reinterpret_cast<const cplx<T>*>(t.tw32);
+    a.plane_scale = scale;
+    a.accumulate = accumulate;
+    a.skip = skip;
+    switch (t.m) {
+      case 64: return launch_xform_fast<T, TI, TO, 64, FWD>(a, st);
+      case 128: return launch_xform_fast<T, TI, TO, 128, FWD>(a, st);
+      case 256: return launch_xform_fast<T, TI, TO, 256, FWD>(a, st);
+      default: return launch_xform_fast<T, TI, TO, 512, FWD>(a, st);
+    }
+  }
+  return launch_xform<T, TI, TO, FWD>(xargs<T>(p, axis, in, out, scale, accumulate, skip), st);
+}
+
 // Launch `fn` on `st`, bracketed by profiling events when enabled on the plan.
 template <class F>
 cudaError_t run(ps_plan* pl, int kind, cudaStream_t st, F&& fn) {
@@ -253,18 +288,18 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
     else { sin_ = pl->idzf32; sout = pl->dzf32; }
   }
   cudaError_t e;
-  if ((e = run(pl, K_XF, st, [&] { return launch_xform<T, T, T, true>(xargs<T>(pl, 0, f, p, sin_, 0, nullptr), st); })) != cudaSuccess)
+  if ((e = run(pl, K_XF, st, [&] { return line_xform<T, T, T, true>(pl, 0, f, p, sin_, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "x forward");
-  if ((e = run(pl, K_YF, st, [&] { return launch_xform<T, T, T, true>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st); })) != cudaSuccess)
+  if ((e = run(pl, K_YF, st, [&] { return line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "y forward");
   const ZArgs<T> za = zargs<T>(pl, p, ws, L, nullptr);
   if ((e = run(pl, K_Z, st, [&] { return launch_zsolve<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z solve");
   if (pl->singular && (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z singular column");
-  if ((e = run(pl, K_YB, st, [&] { return launch_xform<T, T, T, false>(xargs<T>(pl, 1, p, p, nullptr, 0, nullptr), st); })) != cudaSuccess)
+  if ((e = run(pl, K_YB, st, [&] { return line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "y backward");
-  if ((e = run(pl, K_XB, st, [&] { return launch_xform<T, T, T, false>(xargs<T>(pl, 0, p, p, sout, 0, nullptr), st); })) != cudaSuccess)
+  if ((e = run(pl, K_XB, st, [&] { return line_xform<T, T, T, false>(pl, 0, p, p, sout, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "x backward");
   if (info && (e = run(pl, K_CTL, st, [&] { return launch_info_plain(info, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "info");
@@ -286,15 +321,15 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   auto correction = [&](bool first) -> cudaError_t {
     cudaError_t r;
     if (first)
-      r = run(pl, K_XF64IN, st, [&] { return launch_xform<float, double, float, true>(xargs<float>(pl, 0, f, w, nullptr, 0, skip), st); });
+      r = run(pl, K_XF64IN, st, [&] { return line_xform<float, double, float, true>(pl, 0, f, w, nullptr, 0, skip, st); });
     else
-      r = run(pl, K_XF, st, [&] { return launch_xform<float, float, float, true>(xargs<float>(pl, 0, w, w, nullptr, 0, skip), st); });
+      r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, w, w, nullptr, 0, skip, st); });
     if (r != cudaSuccess) return r;
-    if ((r = run(pl, K_YF, st, [&] { return launch_xform<float, float, float, true>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st); })) != cudaSuccess) return r;
+    if ((r = run(pl, K_YF, st, [&] { return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
     if ((r = run(pl, K_Z, st, [&] { return launch_zsolve<float>(zw, st); })) != cudaSuccess) return r;
     if (pl->singular && (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
-    if ((r = run(pl, K_YB, st, [&] { return launch_xform<float, float, float, false>(xargs<float>(pl, 1, w, w, nullptr, 0, skip), st); })) != cudaSuccess) return r;
-    return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] { return launch_xform<float, float, double, false>(xargs<float>(pl, 0, w, p, nullptr, first ? 0 : 1, skip), st); });
+    if ((r = run(pl, K_YB, st, [&] { return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
+    return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] { return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, first ? 0 : 1, skip, st); });
   };
   ResidArgs ra{};
   ra.p = p;

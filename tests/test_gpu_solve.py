@@ -135,3 +135,30 @@ def test_fp64_in_place(lib):
     q = S.solve(f, 0.1, 0.1, zf, "DD", "P", "NN")
     assert _relerr(t.cpu().numpy(), q) <= 1e-12
     plan.close()
+
+
+FAST = [(4, 16, 1024), (4, 1024, 16), (3, 128, 256), (2, 512, 128), (2, 256, 512)]
+
+
+@pytest.mark.parametrize("shape", FAST, ids=[f"{s[0]}x{s[1]}x{s[2]}" for s in FAST])
+@pytest.mark.parametrize("bcxy", [("P", "NN"), ("NN", "DD"), ("DD", "ND"), ("ND", "P")])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_register_resident_transform_sizes(lib, shape, bcxy, precision, tol):
+    """Line lengths 128…1024 along x and y (the register-resident kernels)."""
+    nz, ny, nx = shape
+    bcs = (bcxy[0], bcxy[1], "NN")
+    zf = synth.tanh_faces(nz, 1.0, 1.5)
+    f = np.random.default_rng(nx + 3 * ny).standard_normal(shape)
+    p, _ = _run(lib, f, 1.0 / nx, 2.0 / ny, zf, bcs, precision=precision)
+    q = S.solve(f, 1.0 / nx, 2.0 / ny, zf, *bcs)
+    assert _relerr(p, q) <= tol
+
+
+@pytest.mark.parametrize("bcs", [("P", "P", "NN"), ("DD", "ND", "DD")])
+def test_refine_register_resident_sizes(lib, bcs):
+    nz, ny, nx = 8, 128, 256
+    zf = synth.tanh_faces(nz, 1.0, 1.5)
+    f = np.random.default_rng(11).uniform(-1, 1, (nz, ny, nx))
+    p, info = _run(lib, f, 6.0 / nx, 3.0 / ny, zf, bcs, precision="fp32_refine", rtol=1e-10, max_iter=6)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    assert O.relative_residual(p, f, 6.0 / nx, 3.0 / ny, zf, *bcs) <= 1e-10
