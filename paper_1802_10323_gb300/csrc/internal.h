@@ -58,6 +58,7 @@ template <class T>
 cudaError_t launch_zsolve(ZArgs<T> a, cudaStream_t st);
 template <class T>
 cudaError_t launch_zsingular(ZArgs<T> a, cudaStream_t st);
+cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st);  // FP32, non-periodic
 
 // Residual r = f − A·p (double-float), written as FP32, with reductions.
 struct ResidArgs {
@@ -75,9 +76,11 @@ struct ResidArgs {
   int* red;                 // per-call reduction words (see residual.cu)
   float* partial;           // per-block double-float weighted sums (2 floats per block) ×2
   int nblocks;
+  int zchunk;               // planes per CTA (set by the launcher)
   const int* skip;
 };
 
+int residual_blocks(int nx, int ny, int nz);  // CTAs of one residual pass (partials buffer size)
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
 
 // Control block at the start of the workspace.

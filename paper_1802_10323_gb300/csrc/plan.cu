@@ -293,7 +293,11 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
   if ((e = run(pl, K_YF, st, [&] { return line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "y forward");
   const ZArgs<T> za = zargs<T>(pl, p, ws, L, nullptr);
-  if ((e = run(pl, K_Z, st, [&] { return launch_zsolve<T>(za, st); })) != cudaSuccess)
+  if ((e = run(pl, K_Z, st, [&] {
+         if constexpr (sizeof(T) == 4)
+           if (!pl->periodic_z) return launch_zsolve_ckpt(za, st);
+         return launch_zsolve<T>(za, st);
+       })) != cudaSuccess)
     return cuda_fail(pl, e, "z solve");
   if (pl->singular && (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z singular column");
@@ -326,7 +330,10 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, w, w, nullptr, 0, skip, st); });
     if (r != cudaSuccess) return r;
     if ((r = run(pl, K_YF, st, [&] { return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
-    if ((r = run(pl, K_Z, st, [&] { return launch_zsolve<float>(zw, st); })) != cudaSuccess) return r;
+    if ((r = run(pl, K_Z, st, [&] {
+           return pl->periodic_z ? launch_zsolve<float>(zw, st) : launch_zsolve_ckpt(zw, st);
+         })) != cudaSuccess)
+      return r;
     if (pl->singular && (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
     if ((r = run(pl, K_YB, st, [&] { return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
     return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] { return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, first ? 0 : 1, skip, st); });
@@ -409,10 +416,7 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
   p->periodic_z = (bcz == PS_BC_PERIODIC);
   auto pn = [](int b) { return b == PS_BC_PERIODIC || b == PS_BC_NEUMANN_NEUMANN; };
   p->singular = pn(bcx) && pn(bcy) && pn(bcz);
-  {
-    size_t nb = (p->N + 255) / 256;
-    p->resid_blocks = (int)(nb < 152 * 8 ? nb : 152 * 8);
-  }
+  p->resid_blocks = residual_blocks(nx, ny, nz);
 
   // ---- z metric (finite-volume form of Eq. 4 on the faces) ----
   std::vector<double> dzf(nz), dzc(nz > 1 ? nz - 1 : 0), za(nz, 0.0), zb(nz, 0.0), zc(nz, 0.0);

@@ -87,6 +87,125 @@ __global__ void __launch_bounds__(128) zsolve_kernel(ZArgs<T> a) {
   }
 }
 
+// FP32, non-periodic columns without scratch: the forward sweep keeps the
+// eliminated (c'_k, d'_k) only at the end of every chunk of ZK planes (in shared
+// memory); the backward sweep walks the chunks from the top, re-reads each
+// chunk's right-hand side, recomputes its (c', d') from the checkpoint in
+// registers (the same instructions on the same inputs, so bit-identical to the
+// forward sweep) and back-substitutes. HBM traffic: read f̂ twice (the second
+// read of a chunk usually hits L2), write Φ̂ once; loads of the next chunk are
+// issued before the current chunk is processed.
+template <class T>
+cudaError_t launch_zsolve(ZArgs<T> a, cudaStream_t st);
+
+constexpr int ZK = 16;
+constexpr int ZB = 64;  // columns (threads) per CTA
+constexpr size_t kZCkptMaxSmem = 200 * 1024;
+
+__global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* ck = reinterpret_cast<float2*>(smem_raw);  // [nchunk][ZB]
+  const int ncol = a.nx * a.ny;
+  const int col = blockIdx.x * ZB + threadIdx.x;
+  const bool act = col < ncol && !(a.singular && col == 0);
+  const int colc = col < ncol ? col : ncol - 1;
+  const int i = colc % a.nx, j = colc / a.nx;
+  const float lam = a.lamx[i] + a.lamy[j];
+  const size_t st = (size_t)ncol;
+  const int nz = a.nz;
+  const int nch = (nz + ZK - 1) / ZK;
+  float* __restrict__ d = a.data + colc;
+  const float* __restrict__ za = a.za;
+  const float* __restrict__ zb = a.zb;
+  const float* __restrict__ zc = a.zc;
+
+  float cur[ZK], nxt[ZK];
+#pragma unroll
+  for (int u = 0; u < ZK; ++u) cur[u] = (u < nz) ? d[(size_t)u * st] : 0.f;
+  float cp = 0.f, dp = 0.f;
+  for (int c = 0; c < nch; ++c) {
+    const int k0 = c * ZK;
+    if (c + 1 < nch) {
+#pragma unroll
+      for (int u = 0; u < ZK; ++u) {
+        const int k = k0 + ZK + u;
+        nxt[u] = (k < nz) ? d[(size_t)k * st] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < ZK; ++u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        const float ak = (k > 0) ? za[k] : 0.f;
+        const float ckk = (k < nz - 1) ? zc[k] : 0.f;
+        const float mk = 1.f / (zb[k] + lam - ak * cp);
+        cp = ckk * mk;
+        dp = (cur[u] - ak * dp) * mk;
+      }
+    }
+    ck[c * ZB + threadIdx.x] = make_float2(cp, dp);
+#pragma unroll
+    for (int u = 0; u < ZK; ++u) cur[u] = nxt[u];
+  }
+  // backward: chunks from the top; prefetch the chunk below
+  {
+    const int k0 = (nch - 1) * ZK;
+#pragma unroll
+    for (int u = 0; u < ZK; ++u) {
+      const int k = k0 + u;
+      cur[u] = (k < nz) ? d[(size_t)k * st] : 0.f;
+    }
+  }
+  float x = 0.f;
+  for (int c = nch - 1; c >= 0; --c) {
+    const int k0 = c * ZK;
+    if (c > 0) {
+#pragma unroll
+      for (int u = 0; u < ZK; ++u) nxt[u] = d[(size_t)(k0 - ZK + u) * st];
+    }
+    float2 prev = (c > 0) ? ck[(c - 1) * ZB + threadIdx.x] : make_float2(0.f, 0.f);
+    float cpa[ZK], dpa[ZK];
+    cp = prev.x;
+    dp = prev.y;
+#pragma unroll
+    for (int u = 0; u < ZK; ++u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        const float ak = (k > 0) ? za[k] : 0.f;
+        const float ckk = (k < nz - 1) ? zc[k] : 0.f;
+        const float mk = 1.f / (zb[k] + lam - ak * cp);
+        cp = ckk * mk;
+        dp = (cur[u] - ak * dp) * mk;
+      }
+      cpa[u] = cp;
+      dpa[u] = dp;
+    }
+#pragma unroll
+    for (int u = ZK - 1; u >= 0; --u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        x = dpa[u] - ((k < nz - 1) ? cpa[u] : 0.f) * x;
+        if (act) d[(size_t)k * st] = x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < ZK; ++u) cur[u] = nxt[u];
+  }
+}
+
+cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st) {
+  const int ncol = a.nx * a.ny;
+  const int nch = (a.nz + ZK - 1) / ZK;
+  const size_t smem = (size_t)nch * ZB * sizeof(float2);
+  if (smem > kZCkptMaxSmem) return launch_zsolve<float>(a, st);  // very tall columns: scratch kernel
+  cudaError_t e = cudaFuncSetAttribute(zsolve_ckpt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  zsolve_ckpt_kernel<<<(ncol + ZB - 1) / ZB, ZB, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 // Column (0,0) of a singular problem; one CTA, the column staged in shared memory.
 template <class T>
 __global__ void __launch_bounds__(256) zsingular_kernel(ZArgs<T> a) {
