@@ -31,6 +31,7 @@ struct XformArgs {
   const T* plane_scale;     // per-z factor on load (fwd) / store (bwd), or null
   int accumulate;           // store: out = out + v
   const int* skip;          // if non-null and *skip != 0 the kernel returns at once
+  unsigned long long* amax; // FP64 output: atomicMax of |value| bit patterns, or null
 };
 
 template <class T, class TI, class TO, bool FWD>
@@ -72,6 +73,8 @@ struct ResidArgs {
   const float2* zhi;        // coefficient of (Φ_{k+1} − Φ_k)
   const float* wz;          // Δz^f_k (weights of the mean, singular problems)
   const float* mu;          // double-float volume-weighted mean of f (singular), subtracted from f
+  const unsigned long long* pmax_bits;  // bit pattern of max|Φ| (sets the fixed-point scale)
+  int first;                // first pass of a solve (measures μ_f)
   int singular;
   int* red;                 // per-call reduction words (see residual.cu)
   float* partial;           // per-block double-float weighted sums (2 floats per block) ×2
@@ -92,6 +95,8 @@ struct Ctrl {
   int red[8];               // reduction words of the current residual pass
   double rel, rnorm, fnorm;
   float mu[2];              // double-float weighted mean of f, set by the first finalize
+  double mf;                // the same mean in FP64
+  unsigned long long pmax;  // bit pattern of max|Φ| after the first FP32 solve
 };
 
 cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,

@@ -231,7 +231,8 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
 // kernel for n ∈ {128, 256, 512, 1024} when the tile fits, else the generic one.
 template <class T, class TI, class TO, bool FWD>
 cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, const T* scale,
-                       int accumulate, const int* skip, cudaStream_t st) {
+                       int accumulate, const int* skip, cudaStream_t st,
+                       unsigned long long* amax = nullptr) {
   const AxisTab& t = axis == 0 ? p->ax : p->ay;
   const int lpc_y = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
   const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) &&
@@ -251,6 +252,7 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
     a.plane_scale = scale;
     a.accumulate = accumulate;
     a.skip = skip;
+    a.amax = amax;
     switch (t.m) {
       case 64: return launch_xform_fast<T, TI, TO, 64, FWD>(a, st);
       case 128: return launch_xform_fast<T, TI, TO, 128, FWD>(a, st);
@@ -258,7 +260,9 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
       default: return launch_xform_fast<T, TI, TO, 512, FWD>(a, st);
     }
   }
-  return launch_xform<T, TI, TO, FWD>(xargs<T>(p, axis, in, out, scale, accumulate, skip), st);
+  XformArgs<T> ga = xargs<T>(p, axis, in, out, scale, accumulate, skip);
+  ga.amax = amax;
+  return launch_xform<T, TI, TO, FWD>(ga, st);
 }
 
 // Launch `fn` on `st`, bracketed by profiling events when enabled on the plan.
@@ -336,7 +340,10 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       return r;
     if (pl->singular && (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
     if ((r = run(pl, K_YB, st, [&] { return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
-    return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] { return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, first ? 0 : 1, skip, st); });
+    return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] {
+      return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, first ? 0 : 1, skip, st,
+                                                     first ? &ctrl->pmax : nullptr);
+    });
   };
   ResidArgs ra{};
   ra.p = p;
@@ -353,6 +360,7 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   ra.zhi = pl->zhi;
   ra.wz = pl->dzf32;
   ra.mu = ctrl->mu;
+  ra.pmax_bits = &ctrl->pmax;
   ra.singular = pl->singular;
   ra.red = ctrl->red;
   ra.partial = partial;
@@ -363,6 +371,7 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   for (int it = 0; it <= pl->max_iter; ++it) {
     const bool last = (it == pl->max_iter);
     ra.r = last ? nullptr : w;
+    ra.first = (it == 0);
     if ((e = run(pl, last ? K_CHK : K_RES, st, [&] { return launch_residual(ra, st); })) != cudaSuccess)
       return cuda_fail(pl, e, "residual");
     if ((e = run(pl, K_CTL, st, [&] {

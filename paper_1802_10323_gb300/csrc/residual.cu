@@ -6,11 +6,16 @@
 // with error-free transformations (TwoSum, FMA products). The residual is
 // rounded once to FP32 (the right-hand side of the next FP32 correction solve).
 //
+// Splitting: Φ = ph + pl with ph on a fixed-point grid 2^−s common to the whole
+// field (s from max|Φ|, so |ph|·2^s < 2^20): the stencil sums of ph are exact
+// in FP32, the four products with the double-float coefficients are made exact
+// with FMA, and the small pl part only needs FP32. f is split into hi + lo.
+//
 // Blocking: a CTA of 32 × 8 threads owns a 32 × 8 (x, y) tile and marches along
 // z over a chunk of planes, keeping Φ_{k−1}, Φ_k, Φ_{k+1} of its column in
-// registers; x and y neighbours come from a double-buffered shared plane with
-// one halo column/row per side. Every FP64 value is loaded from HBM and split
-// once (halos aside).
+// registers (the next plane's loads are issued one iteration ahead); x and y
+// neighbours come from a double-buffered shared plane with one halo column/row
+// per side. Every FP64 value is loaded from HBM and split once (halos aside).
 //
 // Ends of each axis (staggered ghost rules of Table 1): periodic wraps; a
 // Neumann end contributes nothing; a Dirichlet end contributes
@@ -33,24 +38,6 @@ constexpr int RTX = 32, RTY = 8;
 __device__ __forceinline__ int end_lo(int bc) { return bc == BC_P ? END_WRAP : (bc == BC_DD ? END_D : END_N); }
 __device__ __forceinline__ int end_hi(int bc) { return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_ND) ? END_D : END_N); }
 
-// (a + b) − 2c as an unevaluated double-float (two TwoSums on the high parts)
-__device__ __forceinline__ df second_diff(df a, df b, df c) {
-  df s1 = two_sum(a.h, b.h);
-  df s2 = two_sum(s1.h, -2.f * c.h);
-  return {s2.h, s1.l + s2.l + (a.l + b.l - 2.f * c.l)};
-}
-// b − c as an unevaluated double-float
-__device__ __forceinline__ df diff(df b, df c) {
-  df s = two_sum(b.h, -c.h);
-  return {s.h, s.l + (b.l - c.l)};
-}
-// s · w (w a double-float coefficient), unevaluated
-__device__ __forceinline__ df mul_coef(df s, df w) {
-  const float p = __fmul_rn(s.h, w.h);
-  float e = __fmaf_rn(s.h, w.h, -p);
-  e = __fmaf_rn(s.l, w.h, __fmaf_rn(s.h, w.l, e));
-  return {p, e};
-}
 // unevaluated double-float sum
 __device__ __forceinline__ df add_u(df a, df b) {
   df s = two_sum(a.h, b.h);
@@ -58,6 +45,28 @@ __device__ __forceinline__ df add_u(df a, df b) {
 }
 
 __device__ __forceinline__ df ld_df(const double* p) { return df_from_f64(__ldg(p)); }
+
+// Φ on a fixed-point grid: ph = rint(Φ·2^s)·2^−s (|Φ·2^s| < 2^20 for every Φ of
+// the field, so sums and differences of a few ph are exact in FP32) and
+// pl = Φ − ph rounded to FP32 (|pl| ≤ 2^−s−1). A·ph is then exact up to the
+// coefficient products, and A·pl only needs FP32.
+struct fxp {
+  float h, l;
+};
+__device__ __forceinline__ fxp to_fxp(double d, float S, float iS) {
+  float h, l;
+  split_f64(d, h, l);
+  const float ph = __fmul_rn(rintf(__fmul_rn(h, S)), iS);
+  return {ph, __fadd_rn(__fsub_rn(h, ph), l)};
+}
+__device__ __forceinline__ fxp ld_fxp(const double* p, float S, float iS) {
+  return to_fxp(__ldg(p), S, iS);
+}
+// exact product of an FP32 value and a double-float coefficient, unevaluated
+__device__ __forceinline__ df prod(float x, df w) {
+  const float p = __fmul_rn(x, w.h);
+  return {p, __fmaf_rn(x, w.l, __fmaf_rn(x, w.h, -p))};
+}
 
 __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
   if (a.skip && *a.skip) return;
@@ -70,60 +79,103 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
   const int xl = end_lo(a.bcx), xh = end_hi(a.bcx);
   const int yl = end_lo(a.bcy), yh = end_hi(a.bcy);
   const int zl = end_lo(a.bcz), zh = end_hi(a.bcz);
-  __shared__ df sp[2][RTY + 2][RTX + 2];
-  // column of this thread (clamped inside the domain)
+  // fixed-point scale from max|Φ| (recorded by the pass that wrote Φ)
+  float S, iS;
+  {
+    const int e = (int)((*a.pmax_bits >> 52) & 0x7FF) - 1023;  // max|Φ| ∈ [2^e, 2^(e+1))
+    int sc = 19 - e;
+    sc = max(-100, min(100, sc));
+    S = __uint_as_float((uint32_t)(sc + 127) << 23);
+    iS = __uint_as_float((uint32_t)(127 - sc) << 23);
+  }
+  __shared__ fxp sp[2][RTY + 2][RTX + 2];
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
   const size_t col = (size_t)jc * nx + ic;
-  // halo columns / rows loaded by edge threads (periodic wrap; the N/D ends are
-  // resolved in the arithmetic, so their halo value is never used)
   const bool hx_lo = (tx == 0), hx_hi = (tx == RTX - 1) || (i == nx - 1);
   const bool hy_lo = (ty == 0), hy_hi = (ty == RTY - 1) || (j == ny - 1);
   const int ixl = (ic > 0) ? ic - 1 : nx - 1, ixh = (ic < nx - 1) ? ic + 1 : 0;
   const int jyl = (jc > 0) ? jc - 1 : ny - 1, jyh = (jc < ny - 1) ? jc + 1 : 0;
   const size_t cxl = (size_t)jc * nx + ixl, cxh = (size_t)jc * nx + ixh;
   const size_t cyl = (size_t)jyl * nx + ic, cyh = (size_t)jyh * nx + ic;
+  const double* __restrict__ P = a.p;
+  const double* __restrict__ F = a.f;
 
   const int km = (k0 > 0) ? k0 - 1 : nz - 1;
-  df pm = ld_df(a.p + (size_t)km * sxy + col);
-  df pc = ld_df(a.p + (size_t)k0 * sxy + col);
+  fxp pm = ld_fxp(P + (size_t)km * sxy + col, S, iS);
+  fxp pc = ld_fxp(P + (size_t)k0 * sxy + col, S, iS);
+  double pn_raw = __ldg(P + (size_t)((k0 + 1 < nz) ? k0 + 1 : 0) * sxy + col);
+  double f_raw = __ldg(F + (size_t)k0 * sxy + col);
+  // halo values of the current plane, loaded one plane ahead like the centre
+  double hxl = 0, hxh = 0, hyl = 0, hyh = 0;
+  {
+    const size_t pl0 = (size_t)k0 * sxy;
+    if (hx_lo) hxl = __ldg(P + pl0 + cxl);
+    if (hx_hi) hxh = __ldg(P + pl0 + cxh);
+    if (hy_lo) hyl = __ldg(P + pl0 + cyl);
+    if (hy_hi) hyh = __ldg(P + pl0 + cyh);
+  }
   float rmax = -INFINITY, rmin = INFINITY, fmax_ = -INFINITY, fmin_ = INFINITY;
-  df wr = {0.f, 0.f}, wf = {0.f, 0.f};
+  float wr = 0.f;
+  df wf = {0.f, 0.f};
+  const bool first = a.singular && a.first;
   const df mu = a.singular ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
 
   for (int k = k0; k < k1; ++k) {
     const int b = k & 1;
     const size_t plane = (size_t)k * sxy;
-    // this plane into shared memory (centre + halos)
-    // (only in-domain threads write: every cell an in-domain thread reads is
-    // written by an in-domain thread, and out-of-domain clamped copies would race)
     if (in) {
       sp[b][ty + 1][tx + 1] = pc;
-      if (hx_lo) sp[b][ty + 1][tx] = ld_df(a.p + plane + cxl);
-      if (hx_hi) sp[b][ty + 1][tx + 2] = ld_df(a.p + plane + cxh);
-      if (hy_lo) sp[b][ty][tx + 1] = ld_df(a.p + plane + cyl);
-      if (hy_hi) sp[b][ty + 2][tx + 1] = ld_df(a.p + plane + cyh);
+      if (hx_lo) sp[b][ty + 1][tx] = to_fxp(hxl, S, iS);
+      if (hx_hi) sp[b][ty + 1][tx + 2] = to_fxp(hxh, S, iS);
+      if (hy_lo) sp[b][ty][tx + 1] = to_fxp(hyl, S, iS);
+      if (hy_hi) sp[b][ty + 2][tx + 1] = to_fxp(hyh, S, iS);
     }
-    // next plane and f while the shared plane settles
-    const int kp = (k + 1 < nz) ? k + 1 : 0;
-    const df pp = ld_df(a.p + (size_t)kp * sxy + col);
-    const df fv = ld_df(a.f + plane + col);
+    // values of this iteration, then prefetch the next plane's raw loads
+    const fxp pp = to_fxp(pn_raw, S, iS);
+    const df fv = df_from_f64(f_raw);
+    if (k + 1 < k1) {
+      const int kn = (k + 2 < nz) ? k + 2 : 0;
+      const size_t pl1 = plane + sxy;
+      pn_raw = __ldg(P + (size_t)kn * sxy + col);
+      f_raw = __ldg(F + pl1 + col);
+      if (hx_lo) hxl = __ldg(P + pl1 + cxl);
+      if (hx_hi) hxh = __ldg(P + pl1 + cxh);
+      if (hy_lo) hyl = __ldg(P + pl1 + cyl);
+      if (hy_hi) hyh = __ldg(P + pl1 + cyh);
+    }
     __syncthreads();
-    df xm = sp[b][ty + 1][tx], xp = sp[b][ty + 1][tx + 2];
-    df ym = sp[b][ty][tx + 1], yp = sp[b][ty + 2][tx + 1];
-    const df nc = {-pc.h, -pc.l};
+    fxp xm = sp[b][ty + 1][tx], xp = sp[b][ty + 1][tx + 2];
+    fxp ym = sp[b][ty][tx + 1], yp = sp[b][ty + 2][tx + 1];
+    const fxp nc = {-pc.h, -pc.l};
     if (i == 0 && xl != END_WRAP) xm = (xl == END_N) ? pc : nc;
     if (i == nx - 1 && xh != END_WRAP) xp = (xh == END_N) ? pc : nc;
     if (j == 0 && yl != END_WRAP) ym = (yl == END_N) ? pc : nc;
     if (j == ny - 1 && yh != END_WRAP) yp = (yh == END_N) ? pc : nc;
-    df zm = pm, zp = pp;
+    fxp zm = pm, zp = pp;
     if (k == 0 && zl != END_WRAP) zm = (zl == END_N) ? pc : nc;
     if (k == nz - 1 && zh != END_WRAP) zp = (zh == END_N) ? pc : nc;
-    const df tx2 = mul_coef(second_diff(xm, xp, pc), a.idx2);
-    const df ty2 = mul_coef(second_diff(ym, yp, pc), a.idy2);
+    // exact high-part stencil sums (fixed-point grid), FP32 low parts
+    const float sx = (xm.h + xp.h) - 2.f * pc.h, sy = (ym.h + yp.h) - 2.f * pc.h;
+    const float dm = zm.h - pc.h, dpz = zp.h - pc.h;
+    const float lx = (xm.l + xp.l) - 2.f * pc.l, ly = (ym.l + yp.l) - 2.f * pc.l;
     const float2 cl = a.zlo[k], ch = a.zhi[k];
-    const df tz = add_u(mul_coef(diff(zm, pc), df{cl.x, cl.y}), mul_coef(diff(zp, pc), df{ch.x, ch.y}));
-    const df ap = add_u(add_u(tx2, ty2), tz);
-    const df r = add_u(add_u(fv, df{-mu.h, -mu.l}), df{-ap.h, -ap.l});
+    const float lo_terms = lx * a.idx2.h + ly * a.idy2.h + cl.x * (zm.l - pc.l) + ch.x * (zp.l - pc.l);
+    const df t1 = prod(sx, a.idx2), t2 = prod(sy, a.idy2);
+    const df t3 = prod(dm, df{cl.x, cl.y}), t4 = prod(dpz, df{ch.x, ch.y});
+    const df s12 = two_sum(t1.h, t2.h);
+    const df s123 = two_sum(s12.h, t3.h);
+    const df s1234 = two_sum(s123.h, t4.h);
+    const float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
+    // r = (f − μ) − A·Φ
+    df r;
+    if (a.singular) {
+      const df d1 = two_sum(fv.h, -mu.h);
+      const df d2 = two_sum(d1.h, -s1234.h);
+      r = {d2.h, ((d1.l + d2.l) + (fv.l - mu.l)) - ap_lo};
+    } else {
+      const df d2 = two_sum(fv.h, -s1234.h);
+      r = {d2.h, (d2.l + fv.l) - ap_lo};
+    }
     const float rf = r.h + r.l;
     if (in) {
       if (a.r) a.r[plane + col] = rf;
@@ -133,9 +185,12 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
       fmax_ = fmaxf(fmax_, ff);
       fmin_ = fminf(fmin_, ff);
       if (a.singular) {
-        const df w = {a.wz[k], 0.f};
-        wr = add_u(wr, mul_coef(r, w));
-        wf = add_u(wf, mul_coef(fv, w));
+        const float w = a.wz[k];
+        wr = fmaf(w, rf, wr);
+        if (first) {  // Σ Δz^f·f in double-float (only the first pass needs μ_f)
+          wf = add_u(wf, prod(fv.h, df{w, 0.f}));
+          wf.l = fmaf(w, fv.l, wf.l);
+        }
       }
     }
     pm = pc;
@@ -144,19 +199,20 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
 
   // block reductions: warp shuffles, then one thread over the warps
   const unsigned full = 0xffffffffu;
+  df wrd = {wr, 0.f};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     rmax = fmaxf(rmax, __shfl_xor_sync(full, rmax, o));
     rmin = fminf(rmin, __shfl_xor_sync(full, rmin, o));
     fmax_ = fmaxf(fmax_, __shfl_xor_sync(full, fmax_, o));
     fmin_ = fminf(fmin_, __shfl_xor_sync(full, fmin_, o));
-    wr = add_u(wr, df{__shfl_xor_sync(full, wr.h, o), __shfl_xor_sync(full, wr.l, o)});
+    wrd = add_u(wrd, df{__shfl_xor_sync(full, wrd.h, o), __shfl_xor_sync(full, wrd.l, o)});
     wf = add_u(wf, df{__shfl_xor_sync(full, wf.h, o), __shfl_xor_sync(full, wf.l, o)});
   }
   __shared__ float red[RTY][8];
   if (tx == 0) {
     red[ty][0] = rmax; red[ty][1] = rmin; red[ty][2] = fmax_; red[ty][3] = fmin_;
-    red[ty][4] = wr.h; red[ty][5] = wr.l; red[ty][6] = wf.h; red[ty][7] = wf.l;
+    red[ty][4] = wrd.h; red[ty][5] = wrd.l; red[ty][6] = wf.h; red[ty][7] = wf.l;
   }
   __syncthreads();
   if (ty == 0 && tx == 0) {
@@ -165,7 +221,7 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
       rmin = fminf(rmin, red[w][1]);
       fmax_ = fmaxf(fmax_, red[w][2]);
       fmin_ = fminf(fmin_, red[w][3]);
-      wr = add_u(wr, df{red[w][4], red[w][5]});
+      wrd = add_u(wrd, df{red[w][4], red[w][5]});
       wf = add_u(wf, df{red[w][6], red[w][7]});
     }
     atomicMax(&a.red[0], f32_key(rmax));
@@ -173,7 +229,7 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
     atomicMax(&a.red[2], f32_key(fmax_));
     atomicMin(&a.red[3], f32_key(fmin_));
     const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    reinterpret_cast<float4*>(a.partial)[bid] = make_float4(wr.h, wr.l, wf.h, wf.l);
+    reinterpret_cast<float4*>(a.partial)[bid] = make_float4(wrd.h, wrd.l, wf.h, wf.l);
   }
 }
 
@@ -233,17 +289,20 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
       s2 += (double)sf[w].h + (double)sf[w].l;
     }
     mr = s1 / wsum_total;
-    mf = s2 / wsum_total;
-    if (iteration == 0) {
+    if (iteration == 0) {  // μ_f is measured once, on the first pass
+      mf = s2 / wsum_total;
+      c->mf = mf;
       const float h = (float)mf;
       c->mu[0] = h;
       c->mu[1] = (float)(mf - (double)h);
+    } else {
+      mf = c->mf;
     }
   }
   const double rmax = key_f32(c->red[0]), rmin = key_f32(c->red[1]);
   const double vfmax = key_f32(c->red[2]), vfmin = key_f32(c->red[3]);
   const double rn = fmax(rmax - mr, mr - rmin);
-  const double fn = fmax(vfmax - mf, mf - vfmin);  // f's sums are of the raw f
+  const double fn = fmax(vfmax - mf, mf - vfmin);
   const double rel = fn > 0 ? rn / fn : (rn > 0 ? INFINITY : 0.0);
   c->rnorm = rn;
   c->fnorm = fn;

@@ -87,9 +87,9 @@ __global__ void __launch_bounds__(128) zsolve_kernel(ZArgs<T> a) {
   }
 }
 
-// FP32, non-periodic columns without scratch: the forward sweep keeps the
-// eliminated (c'_k, d'_k) only at the end of every chunk of ZK planes (in shared
-// memory); the backward sweep walks the chunks from the top, re-reads each
+// FP32, non-periodic columns: the forward sweep keeps the eliminated
+// (c'_k, d'_k) only at the end of every chunk of ZK planes (1/8 of the data
+// volume, in the scratch array); the backward sweep walks the chunks from the top, re-reads each
 // chunk's right-hand side, recomputes its (c', d') from the checkpoint in
 // registers (the same instructions on the same inputs, so bit-identical to the
 // forward sweep) and back-substitutes. HBM traffic: read f̂ twice (the second
@@ -99,14 +99,12 @@ template <class T>
 cudaError_t launch_zsolve(ZArgs<T> a, cudaStream_t st);
 
 constexpr int ZK = 16;
-constexpr int ZB = 64;  // columns (threads) per CTA
-constexpr size_t kZCkptMaxSmem = 200 * 1024;
+constexpr int ZB = 128;  // columns (threads) per CTA
 
 __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
   if (a.skip && *a.skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* ck = reinterpret_cast<float2*>(smem_raw);  // [nchunk][ZB]
   const int ncol = a.nx * a.ny;
+  float2* __restrict__ ck = reinterpret_cast<float2*>(a.scr_c);  // [nchunk][ncol]
   const int col = blockIdx.x * ZB + threadIdx.x;
   const bool act = col < ncol && !(a.singular && col == 0);
   const int colc = col < ncol ? col : ncol - 1;
@@ -139,12 +137,12 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
       if (k < nz) {
         const float ak = (k > 0) ? za[k] : 0.f;
         const float ckk = (k < nz - 1) ? zc[k] : 0.f;
-        const float mk = 1.f / (zb[k] + lam - ak * cp);
+        const float mk = __fdividef(1.f, zb[k] + lam - ak * cp);
         cp = ckk * mk;
         dp = (cur[u] - ak * dp) * mk;
       }
     }
-    ck[c * ZB + threadIdx.x] = make_float2(cp, dp);
+    ck[(size_t)c * ncol + colc] = make_float2(cp, dp);
 #pragma unroll
     for (int u = 0; u < ZK; ++u) cur[u] = nxt[u];
   }
@@ -164,7 +162,7 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
 #pragma unroll
       for (int u = 0; u < ZK; ++u) nxt[u] = d[(size_t)(k0 - ZK + u) * st];
     }
-    float2 prev = (c > 0) ? ck[(c - 1) * ZB + threadIdx.x] : make_float2(0.f, 0.f);
+    float2 prev = (c > 0) ? ck[(size_t)(c - 1) * ncol + colc] : make_float2(0.f, 0.f);
     float cpa[ZK], dpa[ZK];
     cp = prev.x;
     dp = prev.y;
@@ -174,7 +172,7 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
       if (k < nz) {
         const float ak = (k > 0) ? za[k] : 0.f;
         const float ckk = (k < nz - 1) ? zc[k] : 0.f;
-        const float mk = 1.f / (zb[k] + lam - ak * cp);
+        const float mk = __fdividef(1.f, zb[k] + lam - ak * cp);
         cp = ckk * mk;
         dp = (cur[u] - ak * dp) * mk;
       }
@@ -196,13 +194,7 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
 
 cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st) {
   const int ncol = a.nx * a.ny;
-  const int nch = (a.nz + ZK - 1) / ZK;
-  const size_t smem = (size_t)nch * ZB * sizeof(float2);
-  if (smem > kZCkptMaxSmem) return launch_zsolve<float>(a, st);  // very tall columns: scratch kernel
-  cudaError_t e = cudaFuncSetAttribute(zsolve_ckpt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  zsolve_ckpt_kernel<<<(ncol + ZB - 1) / ZB, ZB, smem, st>>>(a);
+  zsolve_ckpt_kernel<<<(ncol + ZB - 1) / ZB, ZB, 0, st>>>(a);
   return cudaGetLastError();
 }
 

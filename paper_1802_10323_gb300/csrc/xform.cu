@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(256) xform_kernel(XformArgs<T> a) {
   __syncthreads();
 
   // ---- 5. store ----------------------------------------------------------------------
+  unsigned long long amax = 0;
   for (int idx = threadIdx.x; idx < L * n; idx += blockDim.x) {
     int l, e, z;
     size_t g;
@@ -334,11 +335,21 @@ __global__ void __launch_bounds__(256) xform_kernel(XformArgs<T> a) {
     }
     T v = rO[l * ldr + e];
     if (!FWD && a.plane_scale) v *= a.plane_scale[z];
+    TO o;
     if (a.accumulate) {
-      if constexpr (sizeof(TO) == 8) out[g] = out[g] + st_cvt<TO, T>::f(v);
-      else out[g] = out[g] + v;
+      if constexpr (sizeof(TO) == 8) o = out[g] + st_cvt<TO, T>::f(v);
+      else o = out[g] + v;
     } else {
-      out[g] = st_cvt<TO, T>::f(v);
+      o = st_cvt<TO, T>::f(v);
+    }
+    out[g] = o;
+    if constexpr (sizeof(TO) == 8)
+      amax = max(amax, (unsigned long long)__double_as_longlong(o) & 0x7FFFFFFFFFFFFFFFull);
+  }
+  if constexpr (sizeof(TO) == 8) {
+    if (a.amax) {
+      for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if ((threadIdx.x & 31) == 0 && amax) atomicMax(a.amax, amax);
     }
   }
 }

@@ -10,7 +10,7 @@ thread_local char g_launch_diag[256] = "";
 using fast::Shape;
 
 template <class T, class TI, class TO, int M, bool FWD>
-__global__ void __launch_bounds__(512) xform_fast_kernel(FastArgs<T> a) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel(FastArgs<T> a) {
   if (a.skip && *a.skip) return;
   constexpr int N = 2 * M;
   constexpr int E = Shape<M>::E, TPL = Shape<M>::TPL;
@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(512) xform_fast_kernel(FastArgs<T> a) {
   const int ngroups = (a.axis == 0) ? (a.nlines + lpc - 1) / lpc : a.nz * (nx / lpc);
   constexpr int VI = 16 / sizeof(TI);  // input elements per 16-byte load
   constexpr int VO = 16 / sizeof(TO);
+  unsigned long long amax = 0;  // max |value| bits of FP64 outputs (when requested)
 
   for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
     __syncthreads();  // tables ready / previous group's store done
@@ -298,6 +299,8 @@ __global__ void __launch_bounds__(512) xform_fast_kernel(FastArgs<T> a) {
         for (int u = 0; u < VO; ++u) {
           const TO val = st_cvt<TO, T>::f(lines[l * LD + e + u] * s);
           ob[u] = a.accumulate ? ob[u] + val : val;
+          if constexpr (sizeof(TO) == 8)
+            amax = max(amax, (unsigned long long)__double_as_longlong(ob[u]) & 0x7FFFFFFFFFFFFFFFull);
         }
         *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(ob);
       }
@@ -315,9 +318,17 @@ __global__ void __launch_bounds__(512) xform_fast_kernel(FastArgs<T> a) {
         for (int u = 0; u < VO; ++u) {
           const TO val = st_cvt<TO, T>::f(lines[(c + u) * LD + e] * s);
           ob[u] = a.accumulate ? ob[u] + val : val;
+          if constexpr (sizeof(TO) == 8)
+            amax = max(amax, (unsigned long long)__double_as_longlong(ob[u]) & 0x7FFFFFFFFFFFFFFFull);
         }
         *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(ob);
       }
+    }
+  }
+  if constexpr (sizeof(TO) == 8) {
+    if (a.amax) {
+      for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if ((threadIdx.x & 31) == 0 && amax) atomicMax(a.amax, amax);
     }
   }
 }

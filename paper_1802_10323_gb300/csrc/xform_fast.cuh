@@ -139,6 +139,7 @@ struct FastArgs {
   const T* plane_scale;
   int accumulate;
   const int* skip;
+  unsigned long long* amax;  // FP64 output: atomicMax of |value| bit patterns, or null
   int lpc;              // lines per CTA
 };
 
