@@ -12,10 +12,11 @@
 // with FMA, and the small pl part only needs FP32. f is split into hi + lo.
 //
 // Blocking: a CTA of 32 × 8 threads owns a 32 × 8 (x, y) tile and marches along
-// z over a chunk of planes, keeping Φ_{k−1}, Φ_k, Φ_{k+1} of its column in
-// registers (the next plane's loads are issued one iteration ahead); x and y
-// neighbours come from a double-buffered shared plane with one halo column/row
-// per side. Every FP64 value is loaded from HBM and split once (halos aside).
+// z over a chunk of planes. Raw FP64 planes of Φ (tile plus one halo cell per
+// side, periodic wrap resolved in the addresses) and of f stream into a
+// six-stage shared-memory ring with cp.async, up to four planes ahead of the one
+// being computed; each Φ value is split once into a three-plane ring of fixed-point
+// pairs from which the 7-point stencil reads all its neighbours.
 //
 // Ends of each axis (staggered ghost rules of Table 1): periodic wraps; a
 // Neumann end contributes nothing; a Dirichlet end contributes
@@ -44,8 +45,6 @@ __device__ __forceinline__ df add_u(df a, df b) {
   return {s.h, s.l + a.l + b.l};
 }
 
-__device__ __forceinline__ df ld_df(const double* p) { return df_from_f64(__ldg(p)); }
-
 // Φ on a fixed-point grid: ph = rint(Φ·2^s)·2^−s (|Φ·2^s| < 2^20 for every Φ of
 // the field, so sums and differences of a few ph are exact in FP32) and
 // pl = Φ − ph rounded to FP32 (|pl| ≤ 2^−s−1). A·ph is then exact up to the
@@ -59,101 +58,132 @@ __device__ __forceinline__ fxp to_fxp(double d, float S, float iS) {
   const float ph = __fmul_rn(rintf(__fmul_rn(h, S)), iS);
   return {ph, __fadd_rn(__fsub_rn(h, ph), l)};
 }
-__device__ __forceinline__ fxp ld_fxp(const double* p, float S, float iS) {
-  return to_fxp(__ldg(p), S, iS);
-}
 // exact product of an FP32 value and a double-float coefficient, unevaluated
 __device__ __forceinline__ df prod(float x, df w) {
   const float p = __fmul_rn(x, w.h);
   return {p, __fmaf_rn(x, w.l, __fmaf_rn(x, w.h, -p))};
 }
 
+// 8-byte asynchronous global→shared copy; a zero source size fills zeros and
+// reads nothing (used for cells outside the domain).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem),
+               "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+constexpr int RW = RTX + 2, RH = RTY + 2;  // tile with one halo cell per side
+constexpr int RECT = RW * RH;               // 340 cells
+constexpr int NSTG = 6;                     // raw planes in flight (ring)
+
 __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
   if (a.skip && *a.skip) return;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t sxy = (size_t)nx * ny;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * RTX + tx, j = blockIdx.y * RTY + ty;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RTX + tx;
+  const int x0 = blockIdx.x * RTX, y0 = blockIdx.y * RTY;
+  const int i = x0 + tx, j = y0 + ty;
   const bool in = (i < nx) && (j < ny);
   const int k0 = blockIdx.z * a.zchunk, k1 = min(nz, k0 + a.zchunk);
   const int xl = end_lo(a.bcx), xh = end_hi(a.bcx);
   const int yl = end_lo(a.bcy), yh = end_hi(a.bcy);
   const int zl = end_lo(a.bcz), zh = end_hi(a.bcz);
-  // fixed-point scale from max|Φ| (recorded by the pass that wrote Φ)
+  const bool perz = (a.bcz == BC_P);
   float S, iS;
   {
     const int e = (int)((*a.pmax_bits >> 52) & 0x7FF) - 1023;  // max|Φ| ∈ [2^e, 2^(e+1))
-    int sc = 19 - e;
-    sc = max(-100, min(100, sc));
+    int sc = max(-100, min(100, 19 - e));
     S = __uint_as_float((uint32_t)(sc + 127) << 23);
     iS = __uint_as_float((uint32_t)(127 - sc) << 23);
   }
-  __shared__ fxp sp[2][RTY + 2][RTX + 2];
-  const int ic = min(i, nx - 1), jc = min(j, ny - 1);
-  const size_t col = (size_t)jc * nx + ic;
-  const bool hx_lo = (tx == 0), hx_hi = (tx == RTX - 1) || (i == nx - 1);
-  const bool hy_lo = (ty == 0), hy_hi = (ty == RTY - 1) || (j == ny - 1);
-  const int ixl = (ic > 0) ? ic - 1 : nx - 1, ixh = (ic < nx - 1) ? ic + 1 : 0;
-  const int jyl = (jc > 0) ? jc - 1 : ny - 1, jyh = (jc < ny - 1) ? jc + 1 : 0;
-  const size_t cxl = (size_t)jc * nx + ixl, cxh = (size_t)jc * nx + ixh;
-  const size_t cyl = (size_t)jyl * nx + ic, cyh = (size_t)jyh * nx + ic;
+  __shared__ __align__(16) double rawp[NSTG][RECT];   // Φ tile + halo, by plane
+  __shared__ __align__(16) double rawf[NSTG][RTY * RTX];  // f tile, by plane
+  __shared__ fxp fx[3][RECT];                         // split Φ planes k−1, k, k+1
   const double* __restrict__ P = a.p;
   const double* __restrict__ F = a.f;
 
-  const int km = (k0 > 0) ? k0 - 1 : nz - 1;
-  fxp pm = ld_fxp(P + (size_t)km * sxy + col, S, iS);
-  fxp pc = ld_fxp(P + (size_t)k0 * sxy + col, S, iS);
-  double pn_raw = __ldg(P + (size_t)((k0 + 1 < nz) ? k0 + 1 : 0) * sxy + col);
-  double f_raw = __ldg(F + (size_t)k0 * sxy + col);
-  // halo values of the current plane, loaded one plane ahead like the centre
-  double hxl = 0, hxh = 0, hyl = 0, hyh = 0;
-  {
-    const size_t pl0 = (size_t)k0 * sxy;
-    if (hx_lo) hxl = __ldg(P + pl0 + cxl);
-    if (hx_hi) hxh = __ldg(P + pl0 + cxh);
-    if (hy_lo) hyl = __ldg(P + pl0 + cyl);
-    if (hy_hi) hyh = __ldg(P + pl0 + cyh);
+  // the (up to) two halo-rectangle cells this thread copies and converts
+  int rc_off[2];
+  bool rc_ok[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + h * (RTX * RTY);
+    const int rr = e / RW, cc = e - rr * RW;
+    int gi = x0 - 1 + cc, gj = y0 - 1 + rr;
+    bool ok = e < RECT && !((rr == 0 || rr == RH - 1) && (cc == 0 || cc == RW - 1));
+    if (gi < 0) { if (a.bcx == BC_P) gi += nx; else ok = false; }
+    if (gi >= nx) { if (a.bcx == BC_P && gi - nx < nx && x0 + RTX >= nx) gi -= nx; else ok = false; }
+    if (gj < 0) { if (a.bcy == BC_P) gj += ny; else ok = false; }
+    if (gj >= ny) { if (a.bcy == BC_P && gj - ny < ny && y0 + RTY >= ny) gj -= ny; else ok = false; }
+    rc_ok[h] = ok;
+    rc_off[h] = ok ? gj * nx + gi : 0;
   }
+  auto plane_of = [&](int q) {  // source plane of logical plane q (wrap or clamp)
+    if (q < 0) return perz ? q + nz : 0;
+    if (q >= nz) return perz ? q - nz : nz - 1;
+    return q;
+  };
+  auto issue = [&](int q) {  // raw loads of logical plane q into its ring slot
+    const int slot = (q - k0 + 1) % NSTG;
+    const size_t pl = (size_t)plane_of(q) * sxy;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + h * (RTX * RTY);
+      if (e < RECT) cp_async8(&rawp[slot][e], P + pl + rc_off[h], rc_ok[h]);
+    }
+    const size_t fo = in ? (size_t)j * nx + i : 0;
+    cp_async8(&rawf[slot][tid], F + pl + fo, in && q >= 0 && q < nz);
+    cp_commit();
+  };
+  auto convert = [&](int q) {  // split raw plane q into fx[(q − k0 + 1) % 3]
+    const int slot = (q - k0 + 1) % NSTG, fs = (q - k0 + 1) % 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + h * (RTX * RTY);
+      if (e < RECT) fx[fs][e] = to_fxp(rawp[slot][e], S, iS);
+    }
+  };
+
+  // prologue: planes k0−1 … k0+NSTG−2 in flight; convert k0−1 and k0
+#pragma unroll
+  for (int q = 0; q < NSTG - 1; ++q) issue(k0 - 1 + q);
+  cp_wait<NSTG - 3>();
+  __syncthreads();
+  convert(k0 - 1);
+  convert(k0);
+
   float rmax = -INFINITY, rmin = INFINITY, fmax_ = -INFINITY, fmin_ = INFINITY;
   float wr = 0.f;
   df wf = {0.f, 0.f};
   const bool first = a.singular && a.first;
   const df mu = a.singular ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
+  const int c = (ty + 1) * RW + (tx + 1);  // this thread's cell in the rectangle
 
   for (int k = k0; k < k1; ++k) {
-    const int b = k & 1;
-    const size_t plane = (size_t)k * sxy;
-    if (in) {
-      sp[b][ty + 1][tx + 1] = pc;
-      if (hx_lo) sp[b][ty + 1][tx] = to_fxp(hxl, S, iS);
-      if (hx_hi) sp[b][ty + 1][tx + 2] = to_fxp(hxh, S, iS);
-      if (hy_lo) sp[b][ty][tx + 1] = to_fxp(hyl, S, iS);
-      if (hy_hi) sp[b][ty + 2][tx + 1] = to_fxp(hyh, S, iS);
-    }
-    // values of this iteration, then prefetch the next plane's raw loads
-    const fxp pp = to_fxp(pn_raw, S, iS);
-    const df fv = df_from_f64(f_raw);
-    if (k + 1 < k1) {
-      const int kn = (k + 2 < nz) ? k + 2 : 0;
-      const size_t pl1 = plane + sxy;
-      pn_raw = __ldg(P + (size_t)kn * sxy + col);
-      f_raw = __ldg(F + pl1 + col);
-      if (hx_lo) hxl = __ldg(P + pl1 + cxl);
-      if (hx_hi) hxh = __ldg(P + pl1 + cxh);
-      if (hy_lo) hyl = __ldg(P + pl1 + cyl);
-      if (hy_hi) hyh = __ldg(P + pl1 + cyh);
-    }
+    // keep NSTG−1 planes in flight (an empty group keeps the wait count uniform)
+    if (k + NSTG - 2 <= k1) issue(k + NSTG - 2);
+    else cp_commit();
+    cp_wait<NSTG - 3>();  // plane k+1 has landed (planes k+2 … k+NSTG−2 may be pending)
     __syncthreads();
-    fxp xm = sp[b][ty + 1][tx], xp = sp[b][ty + 1][tx + 2];
-    fxp ym = sp[b][ty][tx + 1], yp = sp[b][ty + 2][tx + 1];
+    convert(k + 1);
+    __syncthreads();
+    const fxp* Pm = fx[(k - k0) % 3];
+    const fxp* Pc = fx[(k - k0 + 1) % 3];
+    const fxp* Pp = fx[(k - k0 + 2) % 3];
+    const fxp pc = Pc[c];
+    fxp xm = Pc[c - 1], xp = Pc[c + 1], ym = Pc[c - RW], yp = Pc[c + RW];
+    fxp zm = Pm[c], zp = Pp[c];
     const fxp nc = {-pc.h, -pc.l};
     if (i == 0 && xl != END_WRAP) xm = (xl == END_N) ? pc : nc;
     if (i == nx - 1 && xh != END_WRAP) xp = (xh == END_N) ? pc : nc;
     if (j == 0 && yl != END_WRAP) ym = (yl == END_N) ? pc : nc;
     if (j == ny - 1 && yh != END_WRAP) yp = (yh == END_N) ? pc : nc;
-    fxp zm = pm, zp = pp;
     if (k == 0 && zl != END_WRAP) zm = (zl == END_N) ? pc : nc;
     if (k == nz - 1 && zh != END_WRAP) zp = (zh == END_N) ? pc : nc;
+    const df fv = df_from_f64(rawf[(k - k0 + 1) % NSTG][tid]);
     // exact high-part stencil sums (fixed-point grid), FP32 low parts
     const float sx = (xm.h + xp.h) - 2.f * pc.h, sy = (ym.h + yp.h) - 2.f * pc.h;
     const float dm = zm.h - pc.h, dpz = zp.h - pc.h;
@@ -166,7 +196,6 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
     const df s123 = two_sum(s12.h, t3.h);
     const df s1234 = two_sum(s123.h, t4.h);
     const float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
-    // r = (f − μ) − A·Φ
     df r;
     if (a.singular) {
       const df d1 = two_sum(fv.h, -mu.h);
@@ -178,7 +207,8 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
     }
     const float rf = r.h + r.l;
     if (in) {
-      if (a.r) a.r[plane + col] = rf;
+      const size_t g = (size_t)k * sxy + (size_t)j * nx + i;
+      if (a.r) a.r[g] = rf;
       const float ff = fv.h + fv.l;
       rmax = fmaxf(rmax, rf);
       rmin = fminf(rmin, rf);
@@ -193,9 +223,8 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
         }
       }
     }
-    pm = pc;
-    pc = pp;
   }
+  cp_wait<0>();
 
   // block reductions: warp shuffles, then one thread over the warps
   const unsigned full = 0xffffffffu;

@@ -7,14 +7,34 @@ namespace ps {
 
 thread_local char g_launch_diag[256] = "";
 
+// Asynchronous global→shared copies (cp.async): 16-byte and element-sized.
+__device__ __forceinline__ void cpa16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+template <int B>
+__device__ __forceinline__ void cpa_elem(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(B));
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// Bytes of the twiddle tables for a given BC (16-byte aligned).
+template <class T, int M>
+__host__ __device__ constexpr size_t fast_table_bytes(int bc) {
+  return ((size_t)(2 * M + 1 + (bc == 0 ? 0 : 2 * M + 1)) * sizeof(cplx<T>) + 15) / 16 * 16;
+}
+
 using fast::Shape;
+using fast::cpad;
 
 template <class T, class TI, class TO, int M, bool FWD>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel(FastArgs<T> a) {
   if (a.skip && *a.skip) return;
   constexpr int N = 2 * M;
   constexpr int E = Shape<M>::E, TPL = Shape<M>::TPL;
-  constexpr int LD = N + (sizeof(T) == 4 ? 4 : 2);  // reals per line buffer (16-byte rows)
+  constexpr int LD = N + N / 8 + (sizeof(T) == 4 ? 4 : 2);  // reals per line buffer (16-byte rows; room for the skewed complex view)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int bc = a.bc;
   const int lpc = a.lpc;
@@ -22,7 +42,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
   cplx<T>* stw = reinterpret_cast<cplx<T>*>(smem_raw);  // ω_M^t, t < M
   cplx<T>* ptw = stw + M;                               // e^{−2πik/n}, k ≤ M  (P, NN, DD)
   cplx<T>* xtw = ptw + (M + 1);                         // NN/DD: e^{−iπq/2n}, q < n; ND: pre, post
-  T* lines = reinterpret_cast<T*>(xtw + N + 1);
+  T* lines = reinterpret_cast<T*>(smem_raw + fast_table_bytes<T, M>(bc));
+  // FP32 passes whose input is FP32 stream the next group into a second buffer
+  constexpr bool kAsyncType = (sizeof(T) == 4) && (sizeof(TI) == sizeof(T));
+  const bool async_in = kAsyncType && a.axis == 0 && !(FWD && a.plane_scale);
+  T* lines_alt = lines + lpc * LD;
   for (int i = threadIdx.x; i < M; i += blockDim.x) stw[i] = a.tw[16 * i];
   for (int i = threadIdx.x; i <= M; i += blockDim.x) ptw[i] = a.tw[8 * i];
   if (bc == BC_NN || bc == BC_DD) {
@@ -35,8 +59,6 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
   }
   const int li = threadIdx.x / TPL;  // line within the CTA
   const int t = threadIdx.x % TPL;
-  T* lr = lines + li * LD;                      // this line's reals
-  cplx<T>* lc = reinterpret_cast<cplx<T>*>(lr);  // same buffer as M complex
   const TI* __restrict__ in = static_cast<const TI*>(a.in);
   TO* __restrict__ out = static_cast<TO*>(a.out);
   const int nx = a.nx, ny = a.ny;
@@ -45,13 +67,51 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
   constexpr int VO = 16 / sizeof(TO);
   unsigned long long amax = 0;  // max |value| bits of FP64 outputs (when requested)
 
-  for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+  // issue the asynchronous load of group gg into buffer dst
+  auto issue = [&](int gg, T* dst) {
+    if (a.axis == 0) {
+      const int nlg = min(lpc, a.nlines - gg * lpc);
+      const T* src = reinterpret_cast<const T*>(in) + (size_t)gg * lpc * N;
+      constexpr int V = 16 / sizeof(T);
+      for (int v = threadIdx.x; v < nlg * N / V; v += blockDim.x) {
+        const int l = v / (N / V), e = (v % (N / V)) * V;
+        cpa16(dst + l * LD + e, src + (size_t)v * V);
+      }
+    } else {
+      const int gpz = nx / lpc;
+      const int zz = gg / gpz, xx = (gg - zz * gpz) * lpc;
+      const T* src = reinterpret_cast<const T*>(in) + (size_t)zz * ny * nx + xx;
+      for (int v = threadIdx.x; v < N * lpc; v += blockDim.x) {
+        const int e = v / lpc, c = v - e * lpc;
+        cpa_elem<sizeof(T)>(dst + c * LD + e, src + (size_t)e * nx + c);
+      }
+    }
+    cpa_commit();
+  };
+  if (async_in && (int)blockIdx.x < ngroups) issue(blockIdx.x, lines);
+
+  int it = 0;
+  for (int g = blockIdx.x; g < ngroups; g += gridDim.x, ++it) {
+    T* cur = (async_in && (it & 1)) ? lines_alt : lines;
+    T* lr = cur + li * LD;                          // this line's reals
+    cplx<T>* lc = reinterpret_cast<cplx<T>*>(lr);  // same buffer as M complex
     __syncthreads();  // tables ready / previous group's store done
     // ---- stage in ----
     int zb = 0, x0 = 0;
     int nl = lpc;
-    if (a.axis == 0) {
+    if (a.axis == 1) {
+      const int gpz = nx / lpc;
+      zb = g / gpz;
+      x0 = (g - zb * gpz) * lpc;
+    } else {
       nl = min(lpc, a.nlines - g * lpc);
+    }
+    if (async_in) {
+      const int gn = g + gridDim.x;
+      if (gn < ngroups) issue(gn, (it & 1) ? lines : lines_alt);
+      else cpa_commit();  // empty group keeps the wait count uniform
+      cpa_wait1();
+    } else if (a.axis == 0) {
       const size_t base = (size_t)g * lpc * N;
       const int nvec = nl * N / VI;
       for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
@@ -61,12 +121,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         T s = (T)1;
         if (FWD && a.plane_scale) s = a.plane_scale[(g * lpc + l) / ny];
 #pragma unroll
-        for (int u = 0; u < VI; ++u) lines[l * LD + e + u] = ld_cvt<T, TI>::f(buf[u]) * s;
+        for (int u = 0; u < VI; ++u) cur[l * LD + e + u] = ld_cvt<T, TI>::f(buf[u]) * s;
       }
     } else {
-      const int gpz = nx / lpc;
-      zb = g / gpz;
-      x0 = (g - zb * gpz) * lpc;
       const size_t base = (size_t)zb * ny * nx + x0;
       const int vpr = lpc / VI;  // vectors per row
       T s = (T)1;
@@ -76,7 +133,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         TI buf[VI];
         *reinterpret_cast<uint4*>(buf) = *reinterpret_cast<const uint4*>(in + base + (size_t)e * nx + c);
 #pragma unroll
-        for (int u = 0; u < VI; ++u) lines[(c + u) * LD + e] = ld_cvt<T, TI>::f(buf[u]) * s;
+        for (int u = 0; u < VI; ++u) cur[(c + u) * LD + e] = ld_cvt<T, TI>::f(buf[u]) * s;
       }
     }
     __syncthreads();
@@ -118,14 +175,14 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
 #pragma unroll
         for (int q = 0; q < E / RL; ++q)
 #pragma unroll
-          for (int r = 0; r < RL; ++r) lc[t + q * TPL + r * (M / RL)] = v[q * RL + r];
+          for (int r = 0; r < RL; ++r) lc[cpad(t + q * TPL + r * (M / RL))] = v[q * RL + r];
         __syncwarp();
         if (bc == BC_ND) {
           cplx<T> c[E];
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const int k = t + i * TPL;
-            c[i] = cmul(xtw[M + k], lc[k]);
+            c[i] = cmul(xtw[M + k], lc[cpad(k)]);
           }
           __syncwarp();
 #pragma unroll
@@ -142,7 +199,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
           for (int i = 0; i < NP; ++i) {
             const int k = t + i * TPL;
             if (k > M / 2) break;
-            const cplx<T> Zk = lc[k], Zmk = lc[k == 0 ? 0 : M - k];
+            const cplx<T> Zk = lc[cpad(k)], Zmk = lc[cpad(k == 0 ? 0 : M - k)];
             const cplx<T> Ek = cscale(cadd(Zk, conj_(Zmk)), (T)0.5);
             const cplx<T> Ok = cscale(mul_mi(csub(Zk, conj_(Zmk))), (T)0.5);
             const cplx<T> B = cmul(ptw[k], Ok);
@@ -197,7 +254,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
           }
           __syncwarp();
 #pragma unroll
-          for (int i = 0; i < E; ++i) lc[t + i * TPL] = z[i];
+          for (int i = 0; i < E; ++i) lc[cpad(t + i * TPL)] = z[i];
         } else {
           constexpr int NP = (M / 2) / TPL + 1;
           cplx<T> Zk[NP], Zmk[NP];
@@ -237,8 +294,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
           for (int i = 0; i < NP; ++i) {
             const int k = t + i * TPL;
             if (k > M / 2) break;
-            if (k < M) lc[k] = Zk[i];
-            if (k != 0 && 2 * k != M) lc[M - k] = Zmk[i];
+            if (k < M) lc[cpad(k)] = Zk[i];
+            if (k != 0 && 2 * k != M) lc[cpad(M - k)] = Zmk[i];
           }
         }
         __syncwarp();
@@ -246,7 +303,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
 #pragma unroll
         for (int q = 0; q < E / R0; ++q)
 #pragma unroll
-          for (int r = 0; r < R0; ++r) v[q * R0 + r] = lc[t + q * TPL + r * (M / R0)];
+          for (int r = 0; r < R0; ++r) v[q * R0 + r] = lc[cpad(t + q * TPL + r * (M / R0))];
         if (bc == BC_ND) fast::fft_stages<T, M, false, 0, 1>(v, lc, stw, t);
         else fast::fft_stages<T, M, true, 0, 1>(v, lc, stw, t);
         // ---- backward post-processing straight from the last stage's outputs ----
@@ -297,7 +354,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         if (a.accumulate) *reinterpret_cast<uint4*>(ob) = *reinterpret_cast<const uint4*>(dst);
 #pragma unroll
         for (int u = 0; u < VO; ++u) {
-          const TO val = st_cvt<TO, T>::f(lines[l * LD + e + u] * s);
+          const TO val = st_cvt<TO, T>::f(cur[l * LD + e + u] * s);
           ob[u] = a.accumulate ? ob[u] + val : val;
           if constexpr (sizeof(TO) == 8)
             amax = max(amax, (unsigned long long)__double_as_longlong(ob[u]) & 0x7FFFFFFFFFFFFFFFull);
@@ -316,7 +373,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         if (a.accumulate) *reinterpret_cast<uint4*>(ob) = *reinterpret_cast<const uint4*>(dst);
 #pragma unroll
         for (int u = 0; u < VO; ++u) {
-          const TO val = st_cvt<TO, T>::f(lines[(c + u) * LD + e] * s);
+          const TO val = st_cvt<TO, T>::f(cur[(c + u) * LD + e] * s);
           ob[u] = a.accumulate ? ob[u] + val : val;
           if constexpr (sizeof(TO) == 8)
             amax = max(amax, (unsigned long long)__double_as_longlong(ob[u]) & 0x7FFFFFFFFFFFFFFFull);
@@ -325,6 +382,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
       }
     }
   }
+  if (async_in) asm volatile("cp.async.wait_group 0;\n" ::);
   if constexpr (sizeof(TO) == 8) {
     if (a.amax) {
       for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -337,24 +395,27 @@ template <class T, class TI, class TO, int M, bool FWD>
 cudaError_t launch_xform_fast(FastArgs<T> a, cudaStream_t st) {
   constexpr int N = 2 * M;
   constexpr int TPL = Shape<M>::TPL;
-  constexpr int LD = N + (sizeof(T) == 4 ? 4 : 2);
+  constexpr int LD = N + N / 8 + (sizeof(T) == 4 ? 4 : 2);
   if (a.axis == 0) a.lpc = 256 / TPL;
   else a.lpc = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
   const int threads = a.lpc * TPL;
-  const size_t smem = (size_t)(M + (M + 1) + (N + 1)) * sizeof(cplx<T>) + (size_t)a.lpc * LD * sizeof(T);
+  constexpr bool kAsyncType = (sizeof(T) == 4) && (sizeof(TI) == sizeof(T));
+  const bool async_in = kAsyncType && a.axis == 0 && !(FWD && a.plane_scale);
+  const size_t smem = fast_table_bytes<T, M>(a.bc) + (size_t)(async_in ? 2 : 1) * a.lpc * LD * sizeof(T);
   auto k = xform_fast_kernel<T, TI, TO, M, FWD>;
   // One instantiation serves both axes with different tile sizes: the dynamic
   // shared-memory cap is set once, to the larger of the two configurations.
   static int smem_set = 0;
-  static int blocks_per_sm[2] = {0, 0};
+  static int blocks_per_sm[2][2][2] = {};  // [axis][bc != P][async]
   if (!smem_set) {
-    const size_t tables = (size_t)(M + (M + 1) + (N + 1)) * sizeof(cplx<T>);
-    const size_t smax = tables + (size_t)16 * LD * sizeof(T);
+    const size_t tables = fast_table_bytes<T, M>(1);
+    const size_t lx = 256 / TPL, ly = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
+    const size_t sx = (kAsyncType ? 2 : 1) * lx, smax = tables + (sx > ly ? sx : ly) * LD * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     if (e != cudaSuccess) return e;
     smem_set = 1;
   }
-  int& bps = blocks_per_sm[a.axis];
+  int& bps = blocks_per_sm[a.axis][a.bc != 0][async_in ? 1 : 0];
   if (bps == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, threads, smem);
     if (e != cudaSuccess) return e;

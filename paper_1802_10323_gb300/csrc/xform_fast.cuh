@@ -31,6 +31,10 @@ struct Shape {
   }
 };
 
+// Skewed index of the complex exchange buffer: one pad slot per 8 entries turns
+// the stride-8 (64-byte) writes of a radix-8 stage into conflict-free ones.
+__device__ __forceinline__ int cpad(int i) { return i + (i >> 3); }
+
 template <class T, bool INV>
 __device__ __forceinline__ void dft2(cplx<T>& a, cplx<T>& b) {
   cplx<T> t = a;
@@ -114,14 +118,14 @@ __device__ __forceinline__ void fft_stages(cplx<T> (&v)[Shape<M>::E], cplx<T>* b
       const int b = t + q * TPL;
       const int o = (b / NS) * NS * R + (b & (NS - 1));
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[o + r * NS] = v[q * R + r];
+      for (int r = 0; r < R; ++r) buf[cpad(o + r * NS)] = v[q * R + r];
     }
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < E / R2; ++q) {
       const int b = t + q * TPL;
 #pragma unroll
-      for (int r = 0; r < R2; ++r) v[q * R2 + r] = buf[b + r * (M / R2)];
+      for (int r = 0; r < R2; ++r) v[q * R2 + r] = buf[cpad(b + r * (M / R2))];
     }
     fft_stages<T, M, INV, STAGE + 1, NS * R>(v, buf, stw, t);
   }
