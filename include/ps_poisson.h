@@ -129,6 +129,22 @@ ps_status ps_solve_transpose_f32(ps_plan* plan, const float* g, float* p, void* 
 ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, double* f_dev,
                         double* p_dev, void* ws, void* stream, ps_info* info_host);
 
+/* Solve without a caller-provided workspace (same arguments and results as
+ * ps_solve, for PS_FP64 and PS_FP32_REFINE plans). The paper has no
+ * counterpart: this is a convenience for callers that cannot allocate device
+ * memory at solve time (for example code running under another framework's
+ * memory pool, or an interface through which no workspace can be passed).
+ * The workspace lives in one fixed 8 MiB device array compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits; plans whose ps_workspace_bytes exceeds 8 MiB (roughly more than 10^6
+ * cells) are rejected with PS_UNSUPPORTED_SIZE and a message in
+ * ps_last_error(plan). The first call on a device looks up the array's device
+ * address (a set-up step; make that first call before any stream capture).
+ * This entry point performs no device allocation. All calls share the one
+ * array: calls whose GPU work overlaps (on different streams, or from
+ * different threads) race on it and must be serialised by the caller. */
+ps_status ps_solve_static(ps_plan* plan, const double* f, double* p, void* stream, ps_info* info);
+
 /* Destroy a plan and free its device tables (NULL is accepted). */
 ps_status ps_plan_destroy(ps_plan* plan);
 

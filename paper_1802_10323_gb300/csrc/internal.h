@@ -104,4 +104,7 @@ cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, doubl
                             cudaStream_t st);
 cudaError_t launch_info_plain(ps_info* info, cudaStream_t st);
 
+// Record a message for ps_last_error(plan).
+void set_plan_error(ps_plan* plan, const char* msg);
+
 }  // namespace ps

@@ -394,6 +394,10 @@ ps_status check_solve_args(ps_plan* p, const void* f, const void* out, const voi
 
 }  // namespace
 
+namespace ps {
+void set_plan_error(ps_plan* plan, const char* msg) { fail(plan, PS_OK, msg); }
+}  // namespace ps
+
 extern "C" {
 
 ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, double dy,
