@@ -110,11 +110,11 @@ ps_status ps_solve(ps_plan* plan, const double* f, double* p, void* ws, void* st
 ps_status ps_solve_f32(ps_plan* plan, const float* f, float* p, void* ws, void* stream,
                        ps_info* info);
 
-/* Apply the transpose of the solve map, Aᵀ-solve (for reverse-mode
- * differentiation). With A = W⁻¹S, W = diag(Δz^f_k), S symmetric, the
- * transpose is p = W · solve(W⁻¹ g); singular problems use the transposed
- * projector accordingly. Same arguments and rules as ps_solve (FP64 fields,
- * PS_FP64 or PS_FP32_REFINE plans). */
+/* Apply the transpose of the solve map (for reverse-mode differentiation).
+ * With A = W⁻¹S, W = diag(Δz^f_k), S symmetric, the transpose is
+ * p = W · solve(W⁻¹ g); for singular problems the mean-removing projector is
+ * transposed the same way. FP64 fields, PS_FP64 plans (PS_FP32 plans use
+ * ps_solve_transpose_f32); p == g is allowed. */
 ps_status ps_solve_transpose(ps_plan* plan, const double* g, double* p, void* ws, void* stream,
                              ps_info* info);
 
@@ -151,6 +151,30 @@ ps_status ps_plan_destroy(ps_plan* plan);
 /* Static, NUL-terminated description of the last failure on this plan (or,
  * for plan == NULL, of the last failed ps_plan_create / ps_batch_create). */
 const char* ps_last_error(const ps_plan* plan);
+
+/* ---- Projection step around the solve (Eqs. 2b–2c) ---------------------------
+ * Staggered (MAC) velocity of §2: component c of a velocity field is stored
+ * with the cell array's shape, and the three components are stacked: u is
+ * 3·nx·ny·nz values, [u | v | w]. Entry i of a component along its own axis
+ * is the face on the low side of cell i: on a periodic axis face 0 is the wrap
+ * face; on a Neumann–Neumann axis (prescribed velocity, end of §2) face 0 is
+ * the wall, carried through unchanged, and the high wall is implicit. D is the
+ * cell divergence (wall faces excluded), G the face gradient (zero on walls),
+ * with D·G equal to the operator of Eq. 4; the projection of Eqs. 2b–2c (γΔt
+ * cancels) is u = u* − G·solve(D·u*). Only P and NN axes are accepted.
+ * Field types follow the plan: float for PS_FP32 plans, double otherwise. All
+ * pointers are device pointers; the calls enqueue one kernel on the stream. */
+
+/* f = D·u* (cell-centred right-hand side of Eq. 2b). */
+ps_status ps_div(ps_plan* plan, const void* u, void* f, void* stream);
+/* u = u* − G·φ (Eq. 2c). u may equal ustar. */
+ps_status ps_grad_correct(ps_plan* plan, const void* ustar, const void* phi, void* u, void* stream);
+/* h = Gᵀ·g (cells from a stacked face field g): first step of the projection's
+ * vector–Jacobian product. */
+ps_status ps_grad_adjoint(ps_plan* plan, const void* g, void* h, void* stream);
+/* out = g − Dᵀ·s (stacked faces): last step of the vector–Jacobian product
+ * ḡ* = ḡ − Dᵀ·solveᵀ(Gᵀ·ḡ). out may equal g. */
+ps_status ps_div_adjoint_correct(ps_plan* plan, const void* g, const void* s, void* out, void* stream);
 
 /* ---- Per-kernel timing (optional) --------------------------------------------
  * When enabled on a plan, every kernel launch of its solves is bracketed by a

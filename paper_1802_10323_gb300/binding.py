@@ -61,6 +61,10 @@ _SIGS = {
     "ps_solve_host": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "ps_plan_destroy": [_vp],
     "ps_solve_static": [_vp, _vp, _vp, _vp, _vp],
+    "ps_div": [_vp, _vp, _vp, _vp],
+    "ps_grad_correct": [_vp, _vp, _vp, _vp, _vp],
+    "ps_grad_adjoint": [_vp, _vp, _vp, _vp],
+    "ps_div_adjoint_correct": [_vp, _vp, _vp, _vp, _vp],
     "ps_profile_enable": [_vp, _i],
     "ps_profile_read": [_vp, ctypes.POINTER(PsKernelStat), _i, ctypes.POINTER(_i)],
     "ps_batch_create": [ctypes.POINTER(_vp), _i, ctypes.POINTER(PsGridDesc), _i, _d, _i],

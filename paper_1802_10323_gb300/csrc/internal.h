@@ -104,6 +104,20 @@ cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, doubl
                             cudaStream_t st);
 cudaError_t launch_info_plain(ps_info* info, cudaStream_t st);
 
+// Staggered divergence / gradient of the projection step and their adjoints.
+template <class T>
+struct ProjArgs {
+  int nx, ny, nz;
+  int per[3];
+  T idx, idy;
+  const T* idzf;
+  const T* idzc;
+};
+// op: 0 f = D u; 1 u = u* − G φ; 2 h = Gᵀ g; 3 out = g − Dᵀ s
+template <class T>
+cudaError_t launch_projection(int op, const ProjArgs<T>& a, const void* x0, const void* x1, void* y,
+                              cudaStream_t st);
+
 // Record a message for ps_last_error(plan).
 void set_plan_error(ps_plan* plan, const char* msg);
 

@@ -129,8 +129,8 @@ struct ps_plan {
   size_t N;
   AxisTab ax, ay;
   // z tables
-  double *za64, *zb64, *zc64, *dzf64, *idzf64;
-  float *za32, *zb32, *zc32, *dzf32, *idzf32;
+  double *za64, *zb64, *zc64, *dzf64, *idzf64, *idzc64;
+  float *za32, *zb32, *zc32, *dzf32, *idzf32, *idzc32;
   float2 *zlo, *zhi;
   double wsum;  // Σ Δz^f (the per-plane weights of the singular mean, times nx·ny)
   df idx2, idy2;
@@ -482,7 +482,7 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
     bytes += align256(8 * n * sizeof(cplx<double>)) + align256(8 * n * sizeof(cplx<float>));
     bytes += align256(n * sizeof(double)) + align256(n * sizeof(float));
   }
-  bytes += 5 * align256(nz * sizeof(double)) + 5 * align256(nz * sizeof(float)) +
+  bytes += 6 * align256(nz * sizeof(double)) + 6 * align256(nz * sizeof(float)) +
            2 * align256(nz * sizeof(float2));
   char* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, bytes);
@@ -525,12 +525,14 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
     hput(t.lam64, lam.data(), n * sizeof(double));
     hput(t.lam32, lam32.data(), n * sizeof(float));
   }
-  double** d64[5] = {&p->za64, &p->zb64, &p->zc64, &p->dzf64, &p->idzf64};
-  float** d32[5] = {&p->za32, &p->zb32, &p->zc32, &p->dzf32, &p->idzf32};
-  std::vector<double> idzf(nz);
+  double** d64[6] = {&p->za64, &p->zb64, &p->zc64, &p->dzf64, &p->idzf64, &p->idzc64};
+  float** d32[6] = {&p->za32, &p->zb32, &p->zc32, &p->dzf32, &p->idzf32, &p->idzc32};
+  std::vector<double> idzf(nz), idzc(nz, 0.0);
   for (int k = 0; k < nz; ++k) idzf[k] = 1.0 / dzf[k];
-  const std::vector<double>* srcs[5] = {&za, &zb, &zc, &dzf, &idzf};
-  for (int i = 0; i < 5; ++i) {
+  for (int k = 1; k < nz; ++k) idzc[k] = 1.0 / dzc[k - 1];
+  if (bcz == PS_BC_PERIODIC) idzc[0] = 1.0 / (0.5 * (dzf[0] + dzf[nz - 1]));
+  const std::vector<double>* srcs[6] = {&za, &zb, &zc, &dzf, &idzf, &idzc};
+  for (int i = 0; i < 6; ++i) {
     *d64[i] = reinterpret_cast<double*>(take(nz * sizeof(double)));
     *d32[i] = reinterpret_cast<float*>(take(nz * sizeof(float)));
     std::vector<float> f32(srcs[i]->begin(), srcs[i]->end());
@@ -660,6 +662,55 @@ ps_status ps_profile_read(ps_plan* plan, ps_kernel_stat* stats, int max, int* co
   *count = c;
   pr.n = 0;
   return PS_OK;
+}
+
+// ---- projection step around the solve (Eqs. 2b–2c) -----------------------------
+
+}  // extern "C"
+
+namespace {
+template <class T>
+ProjArgs<T> proj_args(const ps_plan* p) {
+  ProjArgs<T> a{};
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.per[0] = p->bcx == PS_BC_PERIODIC;
+  a.per[1] = p->bcy == PS_BC_PERIODIC;
+  a.per[2] = p->bcz == PS_BC_PERIODIC;
+  a.idx = (T)(1.0 / p->dx);
+  a.idy = (T)(1.0 / p->dy);
+  if constexpr (sizeof(T) == 8) { a.idzf = p->idzf64; a.idzc = p->idzc64; }
+  else { a.idzf = p->idzf32; a.idzc = p->idzc32; }
+  return a;
+}
+
+ps_status projection_op(ps_plan* p, int op, const void* x0, const void* x1, void* y, void* stream) {
+  if (!p) return fail(nullptr, PS_INVALID_ARG, "null plan");
+  if (!x0 || !y || ((op == 1 || op == 3) && !x1)) return fail(p, PS_INVALID_ARG, "null field pointer");
+  auto pn = [](int b) { return b == PS_BC_PERIODIC || b == PS_BC_NEUMANN_NEUMANN; };
+  if (!pn(p->bcx) || !pn(p->bcy) || !pn(p->bcz))
+    return fail(p, PS_INVALID_ARG, "projection needs periodic or Neumann-Neumann axes");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = (p->prec == PS_FP32) ? launch_projection<float>(op, proj_args<float>(p), x0, x1, y, st)
+                                       : launch_projection<double>(op, proj_args<double>(p), x0, x1, y, st);
+  return e == cudaSuccess ? PS_OK : cuda_fail(p, e, "projection kernel");
+}
+}  // namespace
+
+extern "C" {
+
+ps_status ps_div(ps_plan* plan, const void* u, void* f, void* stream) {
+  return projection_op(plan, 0, u, nullptr, f, stream);
+}
+ps_status ps_grad_correct(ps_plan* plan, const void* ustar, const void* phi, void* u, void* stream) {
+  return projection_op(plan, 1, ustar, phi, u, stream);
+}
+ps_status ps_grad_adjoint(ps_plan* plan, const void* g, void* h, void* stream) {
+  return projection_op(plan, 2, g, nullptr, h, stream);
+}
+ps_status ps_div_adjoint_correct(ps_plan* plan, const void* g, const void* s, void* out, void* stream) {
+  return projection_op(plan, 3, g, s, out, stream);
 }
 
 ps_status ps_plan_destroy(ps_plan* plan) {
