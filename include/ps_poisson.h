@@ -212,8 +212,9 @@ typedef struct {
   ps_bc bcx, bcy, bcz;
 } ps_grid_desc;
 
-/* Create a batch of `count` grids (1 ≤ count ≤ 4096); precision PS_FP64 or
- * PS_FP32_REFINE. Tables for every grid are built as in ps_plan_create. */
+/* Create a batch of `count` grids (1 ≤ count ≤ 4096); precision
+ * PS_FP32_REFINE (FP32 bulk, FP64 refinement), 0 ≤ max_iter ≤ 16. Tables for
+ * every grid are built as in ps_plan_create. */
 ps_status ps_batch_create(ps_batch** out, int count, const ps_grid_desc* descs,
                           ps_precision prec, double rtol, int max_iter);
 
@@ -228,6 +229,29 @@ ps_status ps_batch_workspace_bytes(const ps_batch* batch, size_t* bytes);
  * graph (no host synchronisation, no allocation). */
 ps_status ps_batch_solve(ps_batch* batch, double* const* f_dev, double* const* p_dev, void* ws,
                          void* stream, ps_info* infos);
+
+/* Pick the tile sizes of the batched solve (lines per transform task, points
+ * per residual task) by timing candidate scales on the caller's fields; the
+ * choice is kept in the batch and, when the environment variable
+ * PS_AUTOTUNE_CACHE names a file, appended to it as one JSON line keyed by the
+ * grid descriptions and the GPU name (later calls read it back instead of
+ * timing). Runs several solves and synchronises the stream; not capturable.
+ * best_ms (may be NULL) receives the time of one batched solve. */
+ps_status ps_batch_autotune(ps_batch* batch, double* const* f_dev, double* const* p_dev, void* ws,
+                            void* stream, double* best_ms);
+
+/* Current tile scale of the batch (1, 2 or 4). */
+int ps_batch_tile_scale(const ps_batch* batch);
+
+/* Wait limit of the persistent kernel's dependency waits, in seconds
+ * (default 2). flags bit 0 makes one dependency of grid 0 unsatisfiable, so a
+ * test can exercise the bounded wait: the solve then returns with PS_TIMEOUT
+ * in the grids' ps_info instead of hanging. */
+ps_status ps_batch_configure(ps_batch* batch, double wait_limit_seconds, int flags);
+
+/* Static description of the last failure of ps_batch_* on this batch (or, for
+ * NULL, of the last failed ps_batch_create). */
+const char* ps_batch_last_error(const ps_batch* batch);
 
 ps_status ps_batch_destroy(ps_batch* batch);
 

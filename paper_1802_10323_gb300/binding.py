@@ -71,6 +71,8 @@ _SIGS = {
     "ps_batch_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "ps_batch_solve": [_vp, _vp, _vp, _vp, _vp, _vp],
     "ps_batch_destroy": [_vp],
+    "ps_batch_autotune": [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)],
+    "ps_batch_configure": [_vp, _d, _i],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -78,12 +80,17 @@ for _name, _args in _SIGS.items():
     _fn.restype = _st
 _lib.ps_last_error.argtypes = [_vp]
 _lib.ps_last_error.restype = ctypes.c_char_p
+_lib.ps_batch_last_error.argtypes = [_vp]
+_lib.ps_batch_last_error.restype = ctypes.c_char_p
+_lib.ps_batch_tile_scale.argtypes = [_vp]
+_lib.ps_batch_tile_scale.restype = ctypes.c_int
 
-EXPORTS = sorted(list(_SIGS) + ["ps_last_error"])
+_OTHER = ["ps_last_error", "ps_batch_last_error", "ps_batch_tile_scale"]
+EXPORTS = sorted(list(_SIGS) + _OTHER)
 
 
 def __getattr__(name):
-    if name in _SIGS or name == "ps_last_error":
+    if name in _SIGS or name in _OTHER:
         return getattr(_lib, name)
     raise AttributeError(name)
 
@@ -195,3 +202,95 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many independent grids solved by one persistent launch (see ps_batch_create).
+
+    grids: list of dicts with nx, ny, nz, dx, dy, zf (array or None), dz, bcs.
+    """
+
+    def __init__(self, grids, rtol=1e-10, max_iter=3):
+        self.count = len(grids)
+        self._zf = []
+        descs = (PsGridDesc * self.count)()
+        for g, d in enumerate(grids):
+            zf = d.get("zf")
+            zp = None
+            if zf is not None:
+                arr = np.ascontiguousarray(zf, dtype=np.float64)
+                self._zf.append(arr)
+                zp = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            bcs = d.get("bcs", ("P", "P", "NN"))
+            descs[g] = PsGridDesc(d["nx"], d["ny"], d["nz"], float(d["dx"]), float(d["dy"]), zp,
+                                  float(d.get("dz") or 0.0), BC[bcs[0]], BC[bcs[1]], BC[bcs[2]])
+        h = _vp()
+        st = _lib.ps_batch_create(ctypes.byref(h), self.count, descs, PRECISION["fp32_refine"],
+                                  float(rtol), int(max_iter))
+        if st != PS_OK:
+            raise PoissonError(st, _lib.ps_batch_last_error(None).decode())
+        self.handle = h
+        n = ctypes.c_size_t()
+        self._chk(_lib.ps_batch_workspace_bytes(h, ctypes.byref(n)))
+        self.workspace_bytes = n.value
+        self._ws = None
+        self._ptrs = None
+
+    def _chk(self, st):
+        if st != PS_OK:
+            raise PoissonError(st, _lib.ps_batch_last_error(self.handle).decode())
+
+    def workspace(self, device="cuda"):
+        import torch
+        if self._ws is None:
+            self._ws = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
+        return self._ws
+
+    def pointers(self, fs, ps):
+        """Device arrays of the fields' device pointers (kept alive by the batch)."""
+        import torch
+        dev = fs[0].device
+        fptr = torch.tensor([t.data_ptr() for t in fs], dtype=torch.int64, device=dev)
+        pptr = torch.tensor([t.data_ptr() for t in ps], dtype=torch.int64, device=dev)
+        self._ptrs = (fptr, pptr, list(fs), list(ps))
+        return fptr, pptr
+
+    def solve(self, fptr, pptr, infos=None, stream=None):
+        ws = self.workspace(fptr.device)
+        ip = _vp(infos.data_ptr()) if infos is not None else None
+        self._chk(_lib.ps_batch_solve(self.handle, _vp(fptr.data_ptr()), _vp(pptr.data_ptr()),
+                                      _vp(ws.data_ptr()), _stream_ptr(stream), ip))
+
+    def autotune(self, fptr, pptr, stream=None):
+        ws = self.workspace(fptr.device)
+        best = ctypes.c_double()
+        self._chk(_lib.ps_batch_autotune(self.handle, _vp(fptr.data_ptr()), _vp(pptr.data_ptr()),
+                                         _vp(ws.data_ptr()), _stream_ptr(stream), ctypes.byref(best)))
+        return _lib.ps_batch_tile_scale(self.handle), best.value
+
+    def configure(self, wait_limit_seconds=2.0, inject_unsatisfiable_wait=False):
+        self._chk(_lib.ps_batch_configure(self.handle, float(wait_limit_seconds),
+                                          1 if inject_unsatisfiable_wait else 0))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ps_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def infos_tensor(count, device="cuda"):
+    """Device buffer for `count` ps_info records."""
+    import torch
+    return torch.zeros(count * 4, dtype=torch.float64, device=device)
+
+
+def read_infos(t, count):
+    raw = t.detach().cpu().numpy().tobytes()
+    sz = ctypes.sizeof(PsInfo)
+    return [PsInfo.from_buffer_copy(raw[i * sz:(i + 1) * sz]) for i in range(count)]

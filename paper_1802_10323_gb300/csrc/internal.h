@@ -121,4 +121,11 @@ cudaError_t launch_projection(int op, const ProjArgs<T>& a, const void* x0, cons
 // Record a message for ps_last_error(plan).
 void set_plan_error(ps_plan* plan, const char* msg);
 
+// The FP32 tables of a plan (used by the batched solve).
+void ps_plan_internal_tables(const ps_plan* p, const cplx<float>** twx, const cplx<float>** twy,
+                             const float** lamx, const float** lamy, const float** za, const float** zb,
+                             const float** zc, const float** dzf, const float2** zlo, const float2** zhi,
+                             df* idx2, df* idy2, double* wsum_total, int* radx, int* rady, int* nstx,
+                             int* nsty);
+
 }  // namespace ps

@@ -396,6 +396,32 @@ ps_status check_solve_args(ps_plan* p, const void* f, const void* out, const voi
 
 namespace ps {
 void set_plan_error(ps_plan* plan, const char* msg) { fail(plan, PS_OK, msg); }
+
+void ps_plan_internal_tables(const ps_plan* p, const cplx<float>** twx, const cplx<float>** twy,
+                             const float** lamx, const float** lamy, const float** za, const float** zb,
+                             const float** zc, const float** dzf, const float2** zlo, const float2** zhi,
+                             df* idx2, df* idy2, double* wsum_total, int* radx, int* rady, int* nstx,
+                             int* nsty) {
+  *twx = p->ax.tw32;
+  *twy = p->ay.tw32;
+  *lamx = p->ax.lam32;
+  *lamy = p->ay.lam32;
+  *za = p->za32;
+  *zb = p->zb32;
+  *zc = p->zc32;
+  *dzf = p->dzf32;
+  *zlo = p->zlo;
+  *zhi = p->zhi;
+  *idx2 = p->idx2;
+  *idy2 = p->idy2;
+  *wsum_total = p->wsum * p->nx * p->ny;
+  for (int i = 0; i < kMaxStages; ++i) {
+    radx[i] = p->ax.radix[i];
+    rady[i] = p->ay.radix[i];
+  }
+  *nstx = p->ax.nstages;
+  *nsty = p->ay.nstages;
+}
 }  // namespace ps
 
 extern "C" {

@@ -16,7 +16,7 @@ def _declared():
     for fn in os.listdir(inc):
         if fn.endswith(".h"):
             src = open(os.path.join(inc, fn)).read()
-            names |= set(re.findall(r"^(?:ps_status|const char\*)\s+(ps_\w+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^(?:ps_status|const char\*|int)\s+(ps_\w+)\s*\(", src, re.M))
     return names
 
 
