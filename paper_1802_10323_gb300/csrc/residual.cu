@@ -11,16 +11,23 @@
 // in FP32, the four products with the double-float coefficients are made exact
 // with FMA, and the small pl part only needs FP32. f is split into hi + lo.
 //
-// Blocking: a CTA of 32 × 8 threads owns a 32 × 8 (x, y) tile and marches along
-// z over a chunk of planes. Raw FP64 planes of Φ (tile plus one halo cell per
-// side, periodic wrap resolved in the addresses) and of f stream into a
-// six-stage shared-memory ring with cp.async, up to four planes ahead of the one
-// being computed; each Φ value is split once into a three-plane ring of fixed-point
-// pairs from which the 7-point stencil reads all its neighbours.
+// Blocking: a CTA of 32 × 8 threads owns a 32 × (8·RPT) (x, y) tile and
+// marches along z over a chunk of planes; each thread computes RPT consecutive
+// rows of one x column. Raw FP64 planes of Φ (tile plus one halo cell per side)
+// stream into a shared-memory ring with cp.async, RDEPTH − 2 planes ahead of
+// the one being split; each plane is split once into fixed-point pairs (two
+// plane slots), from which the in-plane neighbours are read. The z neighbours
+// of a thread's own cells stay in registers (planes k−1, k, k+1), and f streams
+// through registers one plane ahead with plain loads. The kernel is bound by
+// instruction issue rather than bytes, so the per-plane work that does not
+// scale with the points (ring control, barriers, coefficient loads) is shared
+// by RPT points and the ring slots advance by counters, not by division.
 //
-// Ends of each axis (staggered ghost rules of Table 1): periodic wraps; a
-// Neumann end contributes nothing; a Dirichlet end contributes
-// coef·(ghost − Φ) = coef·(−2Φ). In z the coefficients zlo/zhi already hold
+// Ends of each axis (staggered ghost rules of Table 1) are folded into the halo
+// load: a periodic end wraps; a Neumann end loads the adjacent interior cell
+// (ghost = Φ, so its term vanishes); a Dirichlet end loads it with the sign
+// flipped (ghost = −Φ, term coef·(−2Φ)). In z the same holds for the ghost
+// planes below k = 0 and above k = n_z − 1, and the coefficients zlo/zhi hold
 // a_k, c_k, the wrap couplings, or 1/(Δz^f)² at a Dirichlet end.
 //
 // Reductions per pass (deterministic): max and min of r and of f (order-
@@ -34,7 +41,13 @@
 namespace ps {
 
 enum { END_WRAP = 0, END_N = 1, END_D = 2 };
-constexpr int RTX = 32, RTY = 8;
+constexpr int RTX = 32, RWARPS = 8, RTHREADS = RTX * RWARPS;
+constexpr int RDEPTH = 4;  // raw-plane ring: k+1 being split, k+2 … k+3 in flight
+
+__host__ __device__ constexpr int resid_cells(int rpt) { return (RTX + 2) * (RWARPS * rpt + 2); }
+__host__ __device__ constexpr size_t resid_smem(int rpt) {
+  return (size_t)(RDEPTH + 2) * resid_cells(rpt) * sizeof(double);
+}
 
 __device__ __forceinline__ int end_lo(int bc) { return bc == BC_P ? END_WRAP : (bc == BC_DD ? END_D : END_N); }
 __device__ __forceinline__ int end_hi(int bc) { return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_ND) ? END_D : END_N); }
@@ -63,9 +76,12 @@ __device__ __forceinline__ df prod(float x, df w) {
   const float p = __fmul_rn(x, w.h);
   return {p, __fmaf_rn(x, w.l, __fmaf_rn(x, w.h, -p))};
 }
+__device__ __forceinline__ double flip_sign(double d, uint32_t sgn) {
+  return __hiloint2double(__double2hiint(d) ^ (int)sgn, __double2loint(d));
+}
 
 // 8-byte asynchronous global→shared copy; a zero source size fills zeros and
-// reads nothing (used for cells outside the domain).
+// reads nothing (used for cells that no in-domain point needs).
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem),
@@ -75,153 +91,197 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-constexpr int RW = RTX + 2, RH = RTY + 2;  // tile with one halo cell per side
-constexpr int RECT = RW * RH;               // 340 cells
-constexpr int NSTG = 6;                     // raw planes in flight (ring)
-
-__global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
+template <int RPT>
+__global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(ResidArgs a) {
+  constexpr int TY = RWARPS * RPT, W = RTX + 2, CELLS = resid_cells(RPT);
+  constexpr int CPT = (CELLS + RTHREADS - 1) / RTHREADS;  // halo cells per thread
   if (a.skip && *a.skip) return;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t sxy = (size_t)nx * ny;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RTX + tx;
-  const int x0 = blockIdx.x * RTX, y0 = blockIdx.y * RTY;
-  const int i = x0 + tx, j = y0 + ty;
-  const bool in = (i < nx) && (j < ny);
+  const int x0 = blockIdx.x * RTX, y0 = blockIdx.y * TY;
+  const int i = x0 + tx, jb = y0 + ty * RPT;  // rows jb … jb+RPT−1 of column i
   const int k0 = blockIdx.z * a.zchunk, k1 = min(nz, k0 + a.zchunk);
-  const int xl = end_lo(a.bcx), xh = end_hi(a.bcx);
-  const int yl = end_lo(a.bcy), yh = end_hi(a.bcy);
-  const int zl = end_lo(a.bcz), zh = end_hi(a.bcz);
   const bool perz = (a.bcz == BC_P);
+  const uint32_t zsg_lo = end_lo(a.bcz) == END_D ? 0x80000000u : 0u;
+  const uint32_t zsg_hi = end_hi(a.bcz) == END_D ? 0x80000000u : 0u;
   float S, iS;
   {
     const int e = (int)((*a.pmax_bits >> 52) & 0x7FF) - 1023;  // max|Φ| ∈ [2^e, 2^(e+1))
-    int sc = max(-100, min(100, 19 - e));
+    const int sc = max(-100, min(100, 19 - e));
     S = __uint_as_float((uint32_t)(sc + 127) << 23);
     iS = __uint_as_float((uint32_t)(127 - sc) << 23);
   }
-  __shared__ __align__(16) double rawp[NSTG][RECT];   // Φ tile + halo, by plane
-  __shared__ __align__(16) double rawf[NSTG][RTY * RTX];  // f tile, by plane
-  __shared__ fxp fx[3][RECT];                         // split Φ planes k−1, k, k+1
+  extern __shared__ __align__(16) double rsm[];
+  double* raw = rsm;                                       // [RDEPTH][CELLS] raw Φ planes
+  fxp* fx = reinterpret_cast<fxp*>(rsm + RDEPTH * CELLS);  // [2][CELLS] split planes
   const double* __restrict__ P = a.p;
   const double* __restrict__ F = a.f;
 
-  // the (up to) two halo-rectangle cells this thread copies and converts
-  int rc_off[2];
-  bool rc_ok[2];
+  // The halo-rectangle cells this thread copies and splits: in-plane offset of
+  // the source cell, and per-cell bits "copy" and "flip sign" (Dirichlet ghost).
+  int off[CPT];
+  uint32_t okm = 0, negm = 0;
+  {
+    const int xl = end_lo(a.bcx), xh = end_hi(a.bcx), yl = end_lo(a.bcy), yh = end_hi(a.bcy);
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int e = tid + h * (RTX * RTY);
-    const int rr = e / RW, cc = e - rr * RW;
-    int gi = x0 - 1 + cc, gj = y0 - 1 + rr;
-    bool ok = e < RECT && !((rr == 0 || rr == RH - 1) && (cc == 0 || cc == RW - 1));
-    if (gi < 0) { if (a.bcx == BC_P) gi += nx; else ok = false; }
-    if (gi >= nx) { if (a.bcx == BC_P && gi - nx < nx && x0 + RTX >= nx) gi -= nx; else ok = false; }
-    if (gj < 0) { if (a.bcy == BC_P) gj += ny; else ok = false; }
-    if (gj >= ny) { if (a.bcy == BC_P && gj - ny < ny && y0 + RTY >= ny) gj -= ny; else ok = false; }
-    rc_ok[h] = ok;
-    rc_off[h] = ok ? gj * nx + gi : 0;
-  }
-  auto plane_of = [&](int q) {  // source plane of logical plane q (wrap or clamp)
-    if (q < 0) return perz ? q + nz : 0;
-    if (q >= nz) return perz ? q - nz : nz - 1;
-    return q;
-  };
-  auto issue = [&](int q) {  // raw loads of logical plane q into its ring slot
-    const int slot = (q - k0 + 1) % NSTG;
-    const size_t pl = (size_t)plane_of(q) * sxy;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = tid + h * (RTX * RTY);
-      if (e < RECT) cp_async8(&rawp[slot][e], P + pl + rc_off[h], rc_ok[h]);
+    for (int h = 0; h < CPT; ++h) {
+      const int e = tid + h * RTHREADS;
+      const int rr = e / W, cc = e - rr * W;
+      int gi = x0 - 1 + cc, gj = y0 - 1 + rr;
+      bool ok = e < CELLS && !((gi < 0 || gi >= nx) && (gj < 0 || gj >= ny));  // corners unused
+      bool neg = false;
+      if (gi < 0) {
+        if (a.bcx == BC_P) gi = nx - 1; else { gi = 0; neg ^= (xl == END_D); }
+      } else if (gi == nx) {
+        if (a.bcx == BC_P) gi = 0; else { gi = nx - 1; neg ^= (xh == END_D); }
+      } else if (gi > nx) {
+        ok = false;
+      }
+      if (gj < 0) {
+        if (a.bcy == BC_P) gj = ny - 1; else { gj = 0; neg ^= (yl == END_D); }
+      } else if (gj == ny) {
+        if (a.bcy == BC_P) gj = 0; else { gj = ny - 1; neg ^= (yh == END_D); }
+      } else if (gj > ny) {
+        ok = false;
+      }
+      off[h] = ok ? gj * nx + gi : 0;
+      okm |= (ok ? 1u : 0u) << h;
+      negm |= (neg ? 1u : 0u) << h;
     }
-    const size_t fo = in ? (size_t)j * nx + i : 0;
-    cp_async8(&rawf[slot][tid], F + pl + fo, in && q >= 0 && q < nz);
+  }
+  auto issue = [&](int q, int slot) {  // raw copies of logical plane q (wrap or clamp in z)
+    const int pq = q < 0 ? (perz ? q + nz : 0) : (q >= nz ? (perz ? q - nz : nz - 1) : q);
+    const double* src = P + (size_t)pq * sxy;
+    double* dst = raw + slot * CELLS;
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) {
+      const int e = tid + h * RTHREADS;
+      if (h < CPT - 1 || e < CELLS) cp_async8(dst + e, src + off[h], (okm >> h) & 1u);
+    }
     cp_commit();
   };
-  auto convert = [&](int q) {  // split raw plane q into fx[(q − k0 + 1) % 3]
-    const int slot = (q - k0 + 1) % NSTG, fs = (q - k0 + 1) % 3;
+  auto convert = [&](int q, int slot, int fslot) {  // split logical plane q
+    const uint32_t zs = q < 0 ? zsg_lo : (q >= nz ? zsg_hi : 0u);
+    const double* src = raw + slot * CELLS;
+    fxp* dst = fx + fslot * CELLS;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = tid + h * (RTX * RTY);
-      if (e < RECT) fx[fs][e] = to_fxp(rawp[slot][e], S, iS);
+    for (int h = 0; h < CPT; ++h) {
+      const int e = tid + h * RTHREADS;
+      if (h < CPT - 1 || e < CELLS)
+        dst[e] = to_fxp(flip_sign(src[e], (((negm >> h) & 1u) << 31) ^ zs), S, iS);
     }
   };
 
-  // prologue: planes k0−1 … k0+NSTG−2 in flight; convert k0−1 and k0
+  int cidx[RPT];
+  bool in[RPT];
 #pragma unroll
-  for (int q = 0; q < NSTG - 1; ++q) issue(k0 - 1 + q);
-  cp_wait<NSTG - 3>();
+  for (int m = 0; m < RPT; ++m) {
+    cidx[m] = (ty * RPT + m + 1) * W + tx + 1;
+    in[m] = (i < nx) && (jb + m < ny);
+  }
+  auto load_f = [&](int k, double* fv) {
+#pragma unroll
+    for (int m = 0; m < RPT; ++m)
+      fv[m] = in[m] ? __ldg(F + (size_t)k * sxy + (size_t)(jb + m) * nx + i) : 0.0;
+  };
+
+  // prologue: planes k0−1 … k0+RDEPTH−2 in flight; split k0−1 and k0
+#pragma unroll
+  for (int q = 0; q < RDEPTH; ++q) {
+    if (k0 - 1 + q <= k1) issue(k0 - 1 + q, q);
+    else cp_commit();
+  }
+  double fcur[RPT], fnext[RPT];
+  load_f(k0, fcur);
+  cp_wait<RDEPTH - 2>();
   __syncthreads();
-  convert(k0 - 1);
-  convert(k0);
+  convert(k0 - 1, 0, 0);
+  convert(k0, 1, 1);
+  __syncthreads();
+  fxp zm[RPT], zc[RPT], zp[RPT];
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    zm[m] = fx[cidx[m]];
+    zc[m] = fx[CELLS + cidx[m]];
+  }
 
   float rmax = -INFINITY, rmin = INFINITY, fmax_ = -INFINITY, fmin_ = INFINITY;
   float wr = 0.f;
   df wf = {0.f, 0.f};
   const bool first = a.singular && a.first;
   const df mu = a.singular ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
-  const int c = (ty + 1) * RW + (tx + 1);  // this thread's cell in the rectangle
-
+  int islot = 0;                 // raw slot of plane k + RDEPTH − 1 (≡ k − k0 mod RDEPTH)
+  int cslot = 2 % RDEPTH;        // raw slot of plane k + 1
   for (int k = k0; k < k1; ++k) {
-    // keep NSTG−1 planes in flight (an empty group keeps the wait count uniform)
-    if (k + NSTG - 2 <= k1) issue(k + NSTG - 2);
+    const int par = (k - k0) & 1;  // split slot of plane k+1; plane k is in 1 − par
+    if (k + 1 < k1) load_f(k + 1, fnext);
+    // keep the ring full (an empty group keeps the wait count uniform)
+    if (k + RDEPTH - 1 <= k1) issue(k + RDEPTH - 1, islot);
     else cp_commit();
-    cp_wait<NSTG - 3>();  // plane k+1 has landed (planes k+2 … k+NSTG−2 may be pending)
+    cp_wait<RDEPTH - 2>();  // plane k+1 has landed
     __syncthreads();
-    convert(k + 1);
+    convert(k + 1, cslot, par);
     __syncthreads();
-    const fxp* Pm = fx[(k - k0) % 3];
-    const fxp* Pc = fx[(k - k0 + 1) % 3];
-    const fxp* Pp = fx[(k - k0 + 2) % 3];
-    const fxp pc = Pc[c];
-    fxp xm = Pc[c - 1], xp = Pc[c + 1], ym = Pc[c - RW], yp = Pc[c + RW];
-    fxp zm = Pm[c], zp = Pp[c];
-    const fxp nc = {-pc.h, -pc.l};
-    if (i == 0 && xl != END_WRAP) xm = (xl == END_N) ? pc : nc;
-    if (i == nx - 1 && xh != END_WRAP) xp = (xh == END_N) ? pc : nc;
-    if (j == 0 && yl != END_WRAP) ym = (yl == END_N) ? pc : nc;
-    if (j == ny - 1 && yh != END_WRAP) yp = (yh == END_N) ? pc : nc;
-    if (k == 0 && zl != END_WRAP) zm = (zl == END_N) ? pc : nc;
-    if (k == nz - 1 && zh != END_WRAP) zp = (zh == END_N) ? pc : nc;
-    const df fv = df_from_f64(rawf[(k - k0 + 1) % NSTG][tid]);
-    // exact high-part stencil sums (fixed-point grid), FP32 low parts
-    const float sx = (xm.h + xp.h) - 2.f * pc.h, sy = (ym.h + yp.h) - 2.f * pc.h;
-    const float dm = zm.h - pc.h, dpz = zp.h - pc.h;
-    const float lx = (xm.l + xp.l) - 2.f * pc.l, ly = (ym.l + yp.l) - 2.f * pc.l;
-    const float2 cl = a.zlo[k], ch = a.zhi[k];
-    const float lo_terms = lx * a.idx2.h + ly * a.idy2.h + cl.x * (zm.l - pc.l) + ch.x * (zp.l - pc.l);
-    const df t1 = prod(sx, a.idx2), t2 = prod(sy, a.idy2);
-    const df t3 = prod(dm, df{cl.x, cl.y}), t4 = prod(dpz, df{ch.x, ch.y});
-    const df s12 = two_sum(t1.h, t2.h);
-    const df s123 = two_sum(s12.h, t3.h);
-    const df s1234 = two_sum(s123.h, t4.h);
-    const float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
-    df r;
-    if (a.singular) {
-      const df d1 = two_sum(fv.h, -mu.h);
-      const df d2 = two_sum(d1.h, -s1234.h);
-      r = {d2.h, ((d1.l + d2.l) + (fv.l - mu.l)) - ap_lo};
-    } else {
-      const df d2 = two_sum(fv.h, -s1234.h);
-      r = {d2.h, (d2.l + fv.l) - ap_lo};
-    }
-    const float rf = r.h + r.l;
-    if (in) {
-      const size_t g = (size_t)k * sxy + (size_t)j * nx + i;
-      if (a.r) a.r[g] = rf;
-      const float ff = fv.h + fv.l;
-      rmax = fmaxf(rmax, rf);
-      rmin = fminf(rmin, rf);
-      fmax_ = fmaxf(fmax_, ff);
-      fmin_ = fminf(fmin_, ff);
+    islot = (islot + 1 == RDEPTH) ? 0 : islot + 1;
+    cslot = (cslot + 1 == RDEPTH) ? 0 : cslot + 1;
+    const fxp* Fc = fx + (1 - par) * CELLS;
+    const fxp* Fn = fx + par * CELLS;
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) zp[m] = Fn[cidx[m]];
+    const float2 cl = __ldg(a.zlo + k), ch = __ldg(a.zhi + k);
+    const float w = a.singular ? __ldg(a.wz + k) : 0.f;
+    const size_t gk = (size_t)k * sxy + (size_t)jb * nx + i;
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      const fxp pc = zc[m];
+      const fxp xm = Fc[cidx[m] - 1], xp = Fc[cidx[m] + 1];
+      const fxp ym = (m == 0) ? Fc[cidx[0] - W] : zc[m > 0 ? m - 1 : 0];
+      const fxp yp = (m == RPT - 1) ? Fc[cidx[RPT - 1] + W] : zc[m + 1 < RPT ? m + 1 : 0];
+      const fxp zmv = zm[m], zpv = zp[m];
+      const df fv = df_from_f64(fcur[m]);
+      // exact high-part stencil sums (fixed-point grid), FP32 low parts
+      const float sx = (xm.h + xp.h) - 2.f * pc.h, sy = (ym.h + yp.h) - 2.f * pc.h;
+      const float dm = zmv.h - pc.h, dpz = zpv.h - pc.h;
+      const float lx = (xm.l + xp.l) - 2.f * pc.l, ly = (ym.l + yp.l) - 2.f * pc.l;
+      const float lo_terms = lx * a.idx2.h + ly * a.idy2.h + cl.x * (zmv.l - pc.l) + ch.x * (zpv.l - pc.l);
+      const df t1 = prod(sx, a.idx2), t2 = prod(sy, a.idy2);
+      const df t3 = prod(dm, df{cl.x, cl.y}), t4 = prod(dpz, df{ch.x, ch.y});
+      const df s12 = two_sum(t1.h, t2.h);
+      const df s123 = two_sum(s12.h, t3.h);
+      const df s1234 = two_sum(s123.h, t4.h);
+      const float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
+      df r;
       if (a.singular) {
-        const float w = a.wz[k];
-        wr = fmaf(w, rf, wr);
-        if (first) {  // Σ Δz^f·f in double-float (only the first pass needs μ_f)
-          wf = add_u(wf, prod(fv.h, df{w, 0.f}));
-          wf.l = fmaf(w, fv.l, wf.l);
+        const df d1 = two_sum(fv.h, -mu.h);
+        const df d2 = two_sum(d1.h, -s1234.h);
+        r = {d2.h, ((d1.l + d2.l) + (fv.l - mu.l)) - ap_lo};
+      } else {
+        const df d2 = two_sum(fv.h, -s1234.h);
+        r = {d2.h, (d2.l + fv.l) - ap_lo};
+      }
+      const float rf = r.h + r.l;
+      if (in[m]) {
+        if (a.r) a.r[gk + (size_t)m * nx] = rf;
+        const float ff = fv.h + fv.l;
+        rmax = fmaxf(rmax, rf);
+        rmin = fminf(rmin, rf);
+        fmax_ = fmaxf(fmax_, ff);
+        fmin_ = fminf(fmin_, ff);
+        if (a.singular) {
+          wr = fmaf(w, rf, wr);
+          if (first) {  // Σ Δz^f·f in double-float (only the first pass needs μ_f)
+            wf = add_u(wf, prod(fv.h, df{w, 0.f}));
+            wf.l = fmaf(w, fv.l, wf.l);
+          }
         }
       }
+    }
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      zm[m] = zc[m];
+      zc[m] = zp[m];
+      fcur[m] = fnext[m];
     }
   }
   cp_wait<0>();
@@ -238,14 +298,14 @@ __global__ void __launch_bounds__(RTX * RTY) residual_kernel(ResidArgs a) {
     wrd = add_u(wrd, df{__shfl_xor_sync(full, wrd.h, o), __shfl_xor_sync(full, wrd.l, o)});
     wf = add_u(wf, df{__shfl_xor_sync(full, wf.h, o), __shfl_xor_sync(full, wf.l, o)});
   }
-  __shared__ float red[RTY][8];
+  __shared__ float red[RWARPS][8];
   if (tx == 0) {
     red[ty][0] = rmax; red[ty][1] = rmin; red[ty][2] = fmax_; red[ty][3] = fmin_;
     red[ty][4] = wrd.h; red[ty][5] = wrd.l; red[ty][6] = wf.h; red[ty][7] = wf.l;
   }
   __syncthreads();
   if (ty == 0 && tx == 0) {
-    for (int w = 1; w < RTY; ++w) {
+    for (int w = 1; w < RWARPS; ++w) {
       rmax = fmaxf(rmax, red[w][0]);
       rmin = fminf(rmin, red[w][1]);
       fmax_ = fmaxf(fmax_, red[w][2]);
@@ -271,18 +331,50 @@ __global__ void reset_red_kernel(int* red, const int* skip) {
   red[3] = f32_key(INFINITY);
 }
 
+namespace {
+// Launch shape of one residual pass: rows per thread, planes per CTA, grid.
+struct ResidShape {
+  int rpt, zchunk;
+  dim3 grid;
+};
+ResidShape resid_shape(int nx, int ny, int nz) {
+  ResidShape s;
+  s.rpt = ny >= 4 * RWARPS ? 4 : 2;
+  const int tiles = ((nx + RTX - 1) / RTX) * ((ny + RWARPS * s.rpt - 1) / (RWARPS * s.rpt));
+  // about four waves of three CTAs per SM, 8 … 64 planes per CTA
+  const long long want = 152LL * 3 * 4;
+  long long zc = ((long long)nz * tiles) / want;
+  zc = zc < 8 ? 8 : (zc > 64 ? 64 : zc);
+  s.zchunk = (int)(zc < nz ? zc : nz);
+  s.grid = dim3((nx + RTX - 1) / RTX, (ny + RWARPS * s.rpt - 1) / (RWARPS * s.rpt),
+                (nz + s.zchunk - 1) / s.zchunk);
+  return s;
+}
+template <int RPT>
+cudaError_t launch_resid_rpt(const ResidArgs& b, dim3 grid, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(residual_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)resid_smem(RPT));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  residual_kernel<RPT><<<grid, dim3(RTX, RWARPS), resid_smem(RPT), st>>>(b);
+  return cudaGetLastError();
+}
+}  // namespace
+
 int residual_blocks(int nx, int ny, int nz) {
-  const int zc = nz < 32 ? nz : 32;
-  return ((nx + RTX - 1) / RTX) * ((ny + RTY - 1) / RTY) * ((nz + zc - 1) / zc);
+  const ResidShape s = resid_shape(nx, ny, nz);
+  return (int)(s.grid.x * s.grid.y * s.grid.z);
 }
 
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st) {
   reset_red_kernel<<<1, 1, 0, st>>>(a.red, a.skip);
+  const ResidShape s = resid_shape(a.nx, a.ny, a.nz);
   ResidArgs b = a;
-  b.zchunk = a.nz < 32 ? a.nz : 32;
-  const dim3 grid((a.nx + RTX - 1) / RTX, (a.ny + RTY - 1) / RTY, (a.nz + b.zchunk - 1) / b.zchunk);
-  residual_kernel<<<grid, dim3(RTX, RTY), 0, st>>>(b);
-  return cudaGetLastError();
+  b.zchunk = s.zchunk;
+  return s.rpt == 4 ? launch_resid_rpt<4>(b, s.grid, st) : launch_resid_rpt<2>(b, s.grid, st);
 }
 
 // One CTA: weighted means (singular), norms, convergence test, info record.

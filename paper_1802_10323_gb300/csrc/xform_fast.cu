@@ -20,6 +20,12 @@ __device__ __forceinline__ void cpa_elem(void* smem, const void* gmem) {
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
+// Vector of N elements of T for one shared-memory access.
+template <class T, int N>
+struct alignas(sizeof(T) * N) svec {
+  T v[N];
+};
+
 // Bytes of the twiddle tables for a given BC (16-byte aligned).
 template <class T, int M>
 __host__ __device__ constexpr size_t fast_table_bytes(int bc) {
@@ -120,8 +126,10 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         *reinterpret_cast<uint4*>(buf) = *reinterpret_cast<const uint4*>(in + base + (size_t)v * VI);
         T s = (T)1;
         if (FWD && a.plane_scale) s = a.plane_scale[(g * lpc + l) / ny];
+        svec<T, VI> sv;
 #pragma unroll
-        for (int u = 0; u < VI; ++u) cur[l * LD + e + u] = ld_cvt<T, TI>::f(buf[u]) * s;
+        for (int u = 0; u < VI; ++u) sv.v[u] = ld_cvt<T, TI>::f(buf[u]) * s;
+        *reinterpret_cast<svec<T, VI>*>(&cur[l * LD + e]) = sv;
       }
     } else {
       const size_t base = (size_t)zb * ny * nx + x0;
@@ -152,7 +160,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
             const int p = t + q * TPL + r * (M / R0);
             cplx<T> z;
             if (bc == BC_P) {
-              z = {lr[2 * p], lr[2 * p + 1]};
+              z = *reinterpret_cast<const cplx<T>*>(&lr[2 * p]);
             } else if (bc == BC_ND) {
               z = cmul(cplx<T>{lr[2 * p], lr[N - 1 - 2 * p]}, xtw[p]);
             } else {
@@ -352,9 +360,10 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         TO ob[VO];
         TO* dst = out + base + (size_t)v * VO;
         if (a.accumulate) *reinterpret_cast<uint4*>(ob) = *reinterpret_cast<const uint4*>(dst);
+        const svec<T, VO> sv = *reinterpret_cast<const svec<T, VO>*>(&cur[l * LD + e]);
 #pragma unroll
         for (int u = 0; u < VO; ++u) {
-          const TO val = st_cvt<TO, T>::f(cur[l * LD + e + u] * s);
+          const TO val = st_cvt<TO, T>::f(sv.v[u] * s);
           ob[u] = a.accumulate ? ob[u] + val : val;
           if constexpr (sizeof(TO) == 8)
             amax = max(amax, (unsigned long long)__double_as_longlong(ob[u]) & 0x7FFFFFFFFFFFFFFFull);
