@@ -65,7 +65,7 @@ cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st);  // FP32, non-p
 struct ResidArgs {
   const double* p;
   const double* f;
-  float* r;                 // FP32 residual out (may be null: norms only)
+  float* r;                 // FP32 residual out (n_x·n_y·n_z floats)
   int nx, ny, nz;
   int bcx, bcy, bcz;        // ends: see residual.cu
   df idx2, idy2;            // 1/Δx², 1/Δy²

@@ -370,7 +370,7 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   if ((e = correction(true)) != cudaSuccess) return cuda_fail(pl, e, "initial solve");
   for (int it = 0; it <= pl->max_iter; ++it) {
     const bool last = (it == pl->max_iter);
-    ra.r = last ? nullptr : w;
+    ra.r = w;  // the last pass only checks; its r is not used
     ra.first = (it == 0);
     if ((e = run(pl, last ? K_CHK : K_RES, st, [&] { return launch_residual(ra, st); })) != cudaSuccess)
       return cuda_fail(pl, e, "residual");

@@ -36,6 +36,8 @@
 // finalize kernel forms ‖r_c‖∞ = max(max r − μ_r, μ_r − min r) and the same for
 // f, compares with rtol and sets the convergence flag that makes every later
 // kernel of the solve return at once.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace ps {
@@ -91,8 +93,11 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <int RPT>
+// MODE: 0 non-singular; 1 singular (subtract μ_f, weighted sum of r); 2 the
+// singular problem's first pass (also the weighted sum of f that gives μ_f).
+template <int RPT, int MODE>
 __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(ResidArgs a) {
+  constexpr bool SING = MODE >= 1, FIRST = MODE == 2;
   constexpr int TY = RWARPS * RPT, W = RTX + 2, CELLS = resid_cells(RPT);
   constexpr int CPT = (CELLS + RTHREADS - 1) / RTHREADS;  // halo cells per thread
   if (a.skip && *a.skip) return;
@@ -180,10 +185,15 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     cidx[m] = (ty * RPT + m + 1) * W + tx + 1;
     in[m] = (i < nx) && (jb + m < ny);
   }
-  auto load_f = [&](int k, double* fv) {
+  // Interior tiles (every row and column in the domain) take a copy of the
+  // march without the per-point domain tests.
+  const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny);
+  const double* fcol = F + (size_t)jb * nx + i;  // this thread's column, row jb, plane 0
+  auto load_f = [&](int k, double* fv, auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
     for (int m = 0; m < RPT; ++m)
-      fv[m] = in[m] ? __ldg(F + (size_t)k * sxy + (size_t)(jb + m) * nx + i) : 0.0;
+      fv[m] = (FULL || in[m]) ? __ldg(fcol + (size_t)k * sxy + (size_t)m * nx) : 0.0;
   };
 
   // prologue: planes k0−1 … k0+RDEPTH−2 in flight; split k0−1 and k0
@@ -193,7 +203,8 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     else cp_commit();
   }
   double fcur[RPT], fnext[RPT];
-  load_f(k0, fcur);
+  if (interior) load_f(k0, fcur, std::true_type{});
+  else load_f(k0, fcur, std::false_type{});
   cp_wait<RDEPTH - 2>();
   __syncthreads();
   convert(k0 - 1, 0, 0);
@@ -209,13 +220,14 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   float rmax = -INFINITY, rmin = INFINITY, fmax_ = -INFINITY, fmin_ = INFINITY;
   float wr = 0.f;
   df wf = {0.f, 0.f};
-  const bool first = a.singular && a.first;
-  const df mu = a.singular ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
+  const df mu = SING ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
   int islot = 0;                 // raw slot of plane k + RDEPTH − 1 (≡ k − k0 mod RDEPTH)
   int cslot = 2 % RDEPTH;        // raw slot of plane k + 1
+  auto march = [&](auto full_tag) {
+  constexpr bool FULL = decltype(full_tag)::value;
   for (int k = k0; k < k1; ++k) {
     const int par = (k - k0) & 1;  // split slot of plane k+1; plane k is in 1 − par
-    if (k + 1 < k1) load_f(k + 1, fnext);
+    if (k + 1 < k1) load_f(k + 1, fnext, full_tag);
     // keep the ring full (an empty group keeps the wait count uniform)
     if (k + RDEPTH - 1 <= k1) issue(k + RDEPTH - 1, islot);
     else cp_commit();
@@ -230,8 +242,8 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
 #pragma unroll
     for (int m = 0; m < RPT; ++m) zp[m] = Fn[cidx[m]];
     const float2 cl = __ldg(a.zlo + k), ch = __ldg(a.zhi + k);
-    const float w = a.singular ? __ldg(a.wz + k) : 0.f;
-    const size_t gk = (size_t)k * sxy + (size_t)jb * nx + i;
+    const float w = SING ? __ldg(a.wz + k) : 0.f;
+    float* rcol = a.r + (size_t)k * sxy + (size_t)jb * nx + i;
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
       const fxp pc = zc[m];
@@ -252,7 +264,7 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
       const df s1234 = two_sum(s123.h, t4.h);
       const float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
       df r;
-      if (a.singular) {
+      if (SING) {
         const df d1 = two_sum(fv.h, -mu.h);
         const df d2 = two_sum(d1.h, -s1234.h);
         r = {d2.h, ((d1.l + d2.l) + (fv.l - mu.l)) - ap_lo};
@@ -261,16 +273,16 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
         r = {d2.h, (d2.l + fv.l) - ap_lo};
       }
       const float rf = r.h + r.l;
-      if (in[m]) {
-        if (a.r) a.r[gk + (size_t)m * nx] = rf;
+      if (FULL || in[m]) {
+        rcol[(size_t)m * nx] = rf;
         const float ff = fv.h + fv.l;
         rmax = fmaxf(rmax, rf);
         rmin = fminf(rmin, rf);
         fmax_ = fmaxf(fmax_, ff);
         fmin_ = fminf(fmin_, ff);
-        if (a.singular) {
+        if (SING) {
           wr = fmaf(w, rf, wr);
-          if (first) {  // Σ Δz^f·f in double-float (only the first pass needs μ_f)
+          if (FIRST) {  // Σ Δz^f·f in double-float (only the first pass needs μ_f)
             wf = add_u(wf, prod(fv.h, df{w, 0.f}));
             wf.l = fmaf(w, fv.l, wf.l);
           }
@@ -284,6 +296,9 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
       fcur[m] = fnext[m];
     }
   }
+  };
+  if (interior) march(std::true_type{});
+  else march(std::false_type{});
   cp_wait<0>();
 
   // block reductions: warp shuffles, then one thread over the warps
@@ -350,17 +365,22 @@ ResidShape resid_shape(int nx, int ny, int nz) {
                 (nz + s.zchunk - 1) / s.zchunk);
   return s;
 }
-template <int RPT>
-cudaError_t launch_resid_rpt(const ResidArgs& b, dim3 grid, cudaStream_t st) {
+template <int RPT, int MODE>
+cudaError_t launch_resid_mode(const ResidArgs& b, dim3 grid, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(residual_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)resid_smem(RPT));
+    cudaError_t e = cudaFuncSetAttribute(residual_kernel<RPT, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)resid_smem(RPT));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  residual_kernel<RPT><<<grid, dim3(RTX, RWARPS), resid_smem(RPT), st>>>(b);
+  residual_kernel<RPT, MODE><<<grid, dim3(RTX, RWARPS), resid_smem(RPT), st>>>(b);
   return cudaGetLastError();
+}
+template <int RPT>
+cudaError_t launch_resid_rpt(const ResidArgs& b, dim3 grid, cudaStream_t st) {
+  if (!b.singular) return launch_resid_mode<RPT, 0>(b, grid, st);
+  return b.first ? launch_resid_mode<RPT, 2>(b, grid, st) : launch_resid_mode<RPT, 1>(b, grid, st);
 }
 }  // namespace
 
@@ -370,6 +390,7 @@ int residual_blocks(int nx, int ny, int nz) {
 }
 
 cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st) {
+  if (!a.r) return cudaErrorInvalidValue;
   reset_red_kernel<<<1, 1, 0, st>>>(a.red, a.skip);
   const ResidShape s = resid_shape(a.nx, a.ny, a.nz);
   ResidArgs b = a;
