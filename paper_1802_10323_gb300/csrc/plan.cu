@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "xform_fast.cuh"
 
@@ -253,6 +255,15 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
     a.accumulate = accumulate;
     a.skip = skip;
     a.amax = amax;
+    if (axis == 1 && std::is_same<TI, T>::value && std::is_same<TO, T>::value && p->nx % 16 == 0 &&
+        !accumulate && !amax) {
+      switch (t.m) {
+        case 64: return launch_xform_col<T, 64, FWD>(a, st);
+        case 128: return launch_xform_col<T, 128, FWD>(a, st);
+        case 256: return launch_xform_col<T, 256, FWD>(a, st);
+        default: return launch_xform_col<T, 512, FWD>(a, st);
+      }
+    }
     switch (t.m) {
       case 64: return launch_xform_fast<T, TI, TO, 64, FWD>(a, st);
       case 128: return launch_xform_fast<T, TI, TO, 128, FWD>(a, st);

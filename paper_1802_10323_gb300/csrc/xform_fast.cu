@@ -26,12 +26,6 @@ struct alignas(sizeof(T) * N) svec {
   T v[N];
 };
 
-// Bytes of the twiddle tables for a given BC (16-byte aligned).
-template <class T, int M>
-__host__ __device__ constexpr size_t fast_table_bytes(int bc) {
-  return ((size_t)(2 * M + 1 + (bc == 0 ? 0 : 2 * M + 1)) * sizeof(cplx<T>) + 15) / 16 * 16;
-}
-
 using fast::Shape;
 using fast::cpad;
 

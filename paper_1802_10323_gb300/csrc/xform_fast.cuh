@@ -133,6 +133,13 @@ __device__ __forceinline__ void fft_stages(cplx<T> (&v)[Shape<M>::E], cplx<T>* b
 
 }  // namespace fast
 
+// Bytes of the twiddle tables for a given BC (16-byte aligned): ω_M^t (M), the
+// real-FFT split factors (M + 1) and, except for P, the BC factors (≤ 2M).
+template <class T, int M>
+__host__ __device__ constexpr size_t fast_table_bytes(int bc) {
+  return ((size_t)(2 * M + 1 + (bc == 0 ? 0 : 2 * M + 1)) * sizeof(cplx<T>) + 15) / 16 * 16;
+}
+
 template <class T>
 struct FastArgs {
   const void* in;
@@ -149,5 +156,10 @@ struct FastArgs {
 
 template <class T, class TI, class TO, int M, bool FWD>
 cudaError_t launch_xform_fast(FastArgs<T> a, cudaStream_t st);
+
+// y-axis lines with the columns on lanes (xform_col.cu): ny = 2M, nx a multiple
+// of 16, TI = TO = T, no accumulation and no FP64 max tracking.
+template <class T, int M, bool FWD>
+cudaError_t launch_xform_col(FastArgs<T> a, cudaStream_t st);
 
 }  // namespace ps
