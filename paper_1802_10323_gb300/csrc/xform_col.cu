@@ -258,29 +258,48 @@ __global__ void __launch_bounds__(CShape<M>::NT, sizeof(T) == 4 ? 2 : 1) xform_c
           buf[k * CW + c] = cmul(cplx<T>{X(2 * k), X(N - 1 - 2 * k)}, xtw[k]);
         }
       } else {
-        constexpr int NP = (M / 2) / TPL + 1;
+        // all row loads of the pairs first (they are independent), then the arithmetic
+        constexpr int NP = (M / 2) / TPL + 1;  // pairs per thread; only b = 0 has k = M/2 in the last
+        T xv[NP][4];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
           const int k = b + i * TPL;
-          if (k > M / 2) break;
-          cplx<T> Vk, Vm;
+          const bool ok = (i < NP - 1) || (k <= M / 2);
+          int q[4];
+          bool use[4] = {ok, ok, ok, ok};
           if (bc == BC_P) {
-            if (k == 0) {
-              Vk = {X(0), (T)0};
-              Vm = {X(N - 1), (T)0};
-            } else {
-              Vk = {X(2 * k - 1), -X(2 * k)};
-              Vm = {X(2 * (M - k) - 1), -X(2 * (M - k))};
-            }
+            q[0] = k == 0 ? 0 : 2 * k - 1;
+            q[1] = 2 * k;
+            q[2] = k == 0 ? N - 1 : 2 * (M - k) - 1;
+            q[3] = 2 * (M - k);
+            use[1] = use[3] = ok && k != 0;
           } else {
             const bool rev = (bc == BC_DD);
-            auto XQ = [&](int q) { return q >= N ? (T)0 : X(rev ? (N - 1 - q) : q); };
+            const int qq[4] = {k, N - k, M - k, N - M + k};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              q[u] = rev ? (N - 1 - qq[u]) : qq[u];
+              use[u] = ok && qq[u] < N;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) xv[i][u] = use[u] ? X(q[u]) : (T)0;
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const int k = b + i * TPL;
+          if (i == NP - 1 && k > M / 2) break;
+          cplx<T> Vk, Vm;
+          if (bc == BC_P) {
+            Vk = {xv[i][0], -xv[i][1]};
+            Vm = {xv[i][2], -xv[i][3]};
+          } else {
             cplx<T> w = xtw[k];
             w.y = -w.y;
-            Vk = cscale(cmul(w, cplx<T>{XQ(k), -XQ(N - k)}), (T)0.5);
+            Vk = cscale(cmul(w, cplx<T>{xv[i][0], -xv[i][1]}), (T)0.5);
             cplx<T> w2 = xtw[M - k];
             w2.y = -w2.y;
-            Vm = cscale(cmul(w2, cplx<T>{XQ(M - k), -XQ(N - M + k)}), (T)0.5);
+            Vm = cscale(cmul(w2, cplx<T>{xv[i][2], -xv[i][3]}), (T)0.5);
           }
           const cplx<T> Ek = cscale(cadd(Vk, conj_(Vm)), (T)0.5);
           cplx<T> wn = ptw[k];
