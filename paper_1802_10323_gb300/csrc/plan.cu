@@ -264,6 +264,14 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
         default: return launch_xform_col<T, 512, FWD>(a, st);
       }
     }
+    if (axis == 0) {
+      switch (t.m) {
+        case 64: return launch_xform_row<T, TI, TO, 64, FWD>(a, st);
+        case 128: return launch_xform_row<T, TI, TO, 128, FWD>(a, st);
+        case 256: return launch_xform_row<T, TI, TO, 256, FWD>(a, st);
+        default: return launch_xform_row<T, TI, TO, 512, FWD>(a, st);
+      }
+    }
     switch (t.m) {
       case 64: return launch_xform_fast<T, TI, TO, 64, FWD>(a, st);
       case 128: return launch_xform_fast<T, TI, TO, 128, FWD>(a, st);

@@ -157,6 +157,10 @@ struct FastArgs {
 template <class T, class TI, class TO, int M, bool FWD>
 cudaError_t launch_xform_fast(FastArgs<T> a, cudaStream_t st);
 
+// x-axis lines read and written by their own warp (xform_row.cu): nx = 2M.
+template <class T, class TI, class TO, int M, bool FWD>
+cudaError_t launch_xform_row(FastArgs<T> a, cudaStream_t st);
+
 // y-axis lines with the columns on lanes (xform_col.cu): ny = 2M, nx a multiple
 // of 16, TI = TO = T, no accumulation and no FP64 max tracking.
 template <class T, int M, bool FWD>
