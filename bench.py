@@ -41,9 +41,14 @@ MAX_ITER = 4
 # Algorithmic bytes per grid point of each kernel kind (compulsory reads + writes
 # of the fields it must touch; scratch traffic is not counted).
 BYTES_PER_POINT = {
+    # x backward: reads the FP32 line, stores (or adds into) the FP64 p and keeps
+    # the FP32 values for the next residual pass; residual pass 0 reads f (FP64)
+    # and Φ_0 (FP32), later passes r = rh + rl and the correction, and both write
+    # rh + rl (the check pass writes nothing); the exact pass reads p and f.
     "refine": {"x_fwd_f64in": 8 + 4, "x_fwd": 4 + 4, "y_fwd": 4 + 4, "z_solve": 4 + 4,
-               "y_bwd": 4 + 4, "x_bwd_f64store": 4 + 8, "x_bwd_f64acc": 4 + 8 + 8,
-               "residual": 8 + 8 + 4, "residual_check": 8 + 8},
+               "y_bwd": 4 + 4, "x_bwd_f64store": 4 + 8 + 4, "x_bwd_f64acc": 4 + 8 + 8 + 4,
+               "residual_first": 8 + 4 + 8, "residual_first3": 8 + 4 + 8, "residual": 8 + 4 + 8,
+               "residual_check": 8 + 4, "residual_exact": 8 + 8 + 4},
     "fp64": {"x_fwd": 16, "y_fwd": 16, "z_solve": 16, "y_bwd": 16, "x_bwd": 16},
 }
 
@@ -261,8 +266,9 @@ def bench_ours(args):
     bytes_launch = bpp[dom] * N
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
     peak, peak_src = peaks()
-    gpu_launches = sum(v[0] for v in prof.values()) + prof.get("residual", (0,))[0] \
-        + prof.get("residual_check", (0,))[0]
+    gpu_launches = sum(v[0] for v in prof.values()) + sum(
+        prof.get(k, (0,))[0] for k in ("residual_first", "residual_first3", "residual", "residual_check",
+                                       "residual_exact"))
     kernels = {k: {"launches": v[0], "active": v[1], "active_ms_per_step": v[3] / args.steps,
                    "share": v[3] / max(sum(x[3] for x in prof.values()), 1e-9)}
                for k, v in prof.items() if v[0]}

@@ -31,7 +31,8 @@ struct XformArgs {
   const T* plane_scale;     // per-z factor on load (fwd) / store (bwd), or null
   int accumulate;           // store: out = out + v
   const int* skip;          // if non-null and *skip != 0 the kernel returns at once
-  unsigned long long* amax; // FP64 output: atomicMax of |value| bit patterns, or null
+  unsigned long long* amax; // FP64 output: atomicMax of |transform output| bit patterns, or null
+  float* out2;              // FP64 output: also store the FP32 transform output here, or null
 };
 
 template <class T, class TI, class TO, bool FWD>
@@ -61,20 +62,25 @@ template <class T>
 cudaError_t launch_zsingular(ZArgs<T> a, cudaStream_t st);
 cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st);  // FP32, non-periodic
 
-// Residual r = f − A·p (double-float), written as FP32, with reductions.
+// Residuals of the refinement (residual.cu): incremental passes on an FP32
+// operand with a double-float base, and the exact pass from the FP64 solution.
 struct ResidArgs {
-  const double* p;
-  const double* f;
-  float* r;                 // FP32 residual out (n_x·n_y·n_z floats)
+  const double* p;          // exact pass: the stored FP64 solution
+  const double* f;          // exact pass and incremental pass 0: the right-hand side
+  float* r;                 // exact pass: FP32 residual out (n_x·n_y·n_z floats)
+  const float* u;           // incremental: FP32 operand (Φ_0 in pass 0, the last correction later)
+  const float* rh_in;       // incremental pass ≥ 1: r_{m−1} = rh + rl
+  const float* rl_in;
+  float* rh_out;            // incremental: r_m = rh + rl out, or both null (norms only)
+  float* rl_out;
   int nx, ny, nz;
   int bcx, bcy, bcz;        // ends: see residual.cu
   df idx2, idy2;            // 1/Δx², 1/Δy²
   const float2* zlo;        // coefficient of (Φ_{k−1} − Φ_k), ghost rules folded in
   const float2* zhi;        // coefficient of (Φ_{k+1} − Φ_k)
   const float* wz;          // Δz^f_k (weights of the mean, singular problems)
-  const float* mu;          // double-float volume-weighted mean of f (singular), subtracted from f
-  const unsigned long long* pmax_bits;  // bit pattern of max|Φ| (sets the fixed-point scale)
-  int first;                // first pass of a solve (measures μ_f)
+  const float* mu;          // double-float volume-weighted mean of f (singular)
+  const unsigned long long* pmax_bits;  // bit pattern of max|operand| (sets the fixed-point scale)
   int singular;
   int* red;                 // per-call reduction words (see residual.cu)
   float* partial;           // per-block double-float weighted sums (2 floats per block) ×2
@@ -83,25 +89,34 @@ struct ResidArgs {
   const int* skip;
 };
 
-int residual_blocks(int nx, int ny, int nz);  // CTAs of one residual pass (partials buffer size)
-cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st);
+// CTAs of one residual pass: the three-level passes (incremental pass 0 and the
+// exact pass) and the others have different shapes
+int residual_blocks(int nx, int ny, int nz, int split3);
+cudaError_t launch_residual_inc(const ResidArgs& a, int pass, int split3, cudaStream_t st);
+cudaError_t launch_residual_exact(const ResidArgs& a, cudaStream_t st);
 
 // Control block at the start of the workspace.
 struct Ctrl {
   int converged;            // set when ‖r‖ ≤ rtol·‖f_c‖ (refinement done)
   int iterations;
   int status;
-  int pad0;
-  int red[8];               // reduction words of the current residual pass
+  int vskip;                // 1: the exact confirmation pass is not needed
+  int red[8];               // reduction words of the current residual pass (r: 0–1, f: 2–3)
   double rel, rnorm, fnorm;
   float mu[2];              // double-float weighted mean of f, set by the first finalize
   double mf;                // the same mean in FP64
   unsigned long long pmax;  // bit pattern of max|Φ| after the first FP32 solve
+  unsigned long long dmax;  // bit pattern of max|e| of the last correction
+  double bnd;               // accumulated drift bound of the incremental residual
+  int skip_redo;            // 0: pass 0 is repeated with the three-level split
+  int pad1;
 };
 
 cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
-                            int singular, double rtol, int iteration, int last, ps_info* info,
-                            cudaStream_t st);
+                            int singular, double rtol, int iteration, int attempt, int last,
+                            double anorm, const int* skip, ps_info* info, cudaStream_t st);
+cudaError_t launch_finalize_exact(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
+                                  int singular, double rtol, ps_info* info, cudaStream_t st);
 cudaError_t launch_info_plain(ps_info* info, cudaStream_t st);
 
 // Staggered divergence / gradient of the projection step and their adjoints.

@@ -106,10 +106,11 @@ void split_df(double d, float2* out) {
 // per grid point (the FP32 refinement path has separate kinds for its FP64-input
 // x pass, its storing and accumulating x passes and its check-only residual).
 enum Kind { K_XF = 0, K_XF64IN, K_YF, K_Z, K_ZS, K_YB, K_XB, K_XB64ST, K_XB64ACC, K_RES, K_CHK,
-            K_CTL, K_NKINDS };
+            K_CTL, K_VER, K_RES0, K_RES3, K_NKINDS };
 static const char* kKindName[K_NKINDS] = {"x_fwd", "x_fwd_f64in", "y_fwd", "z_solve",
                                           "z_singular", "y_bwd", "x_bwd", "x_bwd_f64store",
-                                          "x_bwd_f64acc", "residual", "residual_check", "control"};
+                                          "x_bwd_f64acc", "residual", "residual_check", "control",
+                                          "residual_exact", "residual_first", "residual_first3"};
 constexpr int kProfMax = 4096;
 
 struct Prof {
@@ -135,9 +136,12 @@ struct ps_plan {
   float *za32, *zb32, *zc32, *dzf32, *idzf32, *idzc32;
   float2 *zlo, *zhi;
   double wsum;  // Σ Δz^f (the per-plane weights of the singular mean, times nx·ny)
+  double anorm; // an upper bound of ‖A‖∞ (the drift bound of the incremental residual)
   df idx2, idy2;
   void* dev;    // one allocation for all of the above
-  int resid_blocks;
+  int resid_blocks;     // CTAs of a residual pass (max over the two shapes: partials size)
+  int resid_blocks3;    // … of a three-level pass (incremental pass 0, exact pass)
+  int resid_blocks2;    // … of the other passes
   char err[256];
 };
 
@@ -158,7 +162,7 @@ ps_status cuda_fail(ps_plan* p, cudaError_t e, const char* where) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t ctrl, partial, info, w, scr_c, scr_u, total;
+  size_t ctrl, partial, info, w, rh, rl, scr_c, scr_u, total;
 };
 
 WsLayout ws_layout(const ps_plan* p) {
@@ -172,7 +176,15 @@ WsLayout ws_layout(const ps_plan* p) {
   off += align256(sizeof(ps_info));
   const size_t tz = (p->prec == PS_FP64) ? sizeof(double) : sizeof(float);
   L.w = off;
-  if (p->prec == PS_FP32_REFINE) off += align256(p->N * sizeof(float));
+  L.rh = off;
+  L.rl = off;
+  if (p->prec == PS_FP32_REFINE) {
+    off += align256(p->N * sizeof(float));
+    L.rh = off;  // the residual r = rh + rl of the refinement (double-float)
+    off += align256(p->N * sizeof(float));
+    L.rl = off;
+    off += align256(p->N * sizeof(float));
+  }
   L.scr_c = off;
   off += align256(p->N * tz);
   L.scr_u = off;
@@ -234,7 +246,7 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
 template <class T, class TI, class TO, bool FWD>
 cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, const T* scale,
                        int accumulate, const int* skip, cudaStream_t st,
-                       unsigned long long* amax = nullptr) {
+                       unsigned long long* amax = nullptr, float* out2 = nullptr) {
   const AxisTab& t = axis == 0 ? p->ax : p->ay;
   const int lpc_y = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
   const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) &&
@@ -255,8 +267,9 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
     a.accumulate = accumulate;
     a.skip = skip;
     a.amax = amax;
+    a.out2 = out2;
     if (axis == 1 && std::is_same<TI, T>::value && std::is_same<TO, T>::value && p->nx % 16 == 0 &&
-        !accumulate && !amax) {
+        !accumulate && !amax && !out2) {
       switch (t.m) {
         case 64: return launch_xform_col<T, 64, FWD>(a, st);
         case 128: return launch_xform_col<T, 128, FWD>(a, st);
@@ -281,6 +294,7 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
   }
   XformArgs<T> ga = xargs<T>(p, axis, in, out, scale, accumulate, skip);
   ga.amax = amax;
+  ga.out2 = out2;
   return launch_xform<T, TI, TO, FWD>(ga, st);
 }
 
@@ -344,13 +358,19 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   const int* skip = &ctrl->converged;
   cudaError_t e;
   if ((e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(pl, e, "reset");
+  float* rh = reinterpret_cast<float*>(wb + L.rh);
+  float* rl = reinterpret_cast<float*>(wb + L.rl);
   const ZArgs<float> zw = zargs<float>(pl, w, ws, L, skip);
+  // One FP32 solve of w (the right-hand side in, in place); the first reads f, later
+  // ones r = rh. The x backward stores Φ_0 (first) or adds e (later) into the FP64 p
+  // and keeps the FP32 values in w, the operand of the next residual pass, with
+  // max|Φ_0| or max|e| in ctrl.
   auto correction = [&](bool first) -> cudaError_t {
     cudaError_t r;
     if (first)
       r = run(pl, K_XF64IN, st, [&] { return line_xform<float, double, float, true>(pl, 0, f, w, nullptr, 0, skip, st); });
     else
-      r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, w, w, nullptr, 0, skip, st); });
+      r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, rh, w, nullptr, 0, skip, st); });
     if (r != cudaSuccess) return r;
     if ((r = run(pl, K_YF, st, [&] { return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
     if ((r = run(pl, K_Z, st, [&] {
@@ -361,12 +381,15 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
     if ((r = run(pl, K_YB, st, [&] { return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
     return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] {
       return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, first ? 0 : 1, skip, st,
-                                                     first ? &ctrl->pmax : nullptr);
+                                                     first ? &ctrl->pmax : &ctrl->dmax, w);
     });
   };
   ResidArgs ra{};
   ra.p = p;
   ra.f = f;
+  ra.u = w;
+  ra.rh_in = rh;
+  ra.rl_in = rl;
   ra.nx = pl->nx;
   ra.ny = pl->ny;
   ra.nz = pl->nz;
@@ -379,27 +402,54 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   ra.zhi = pl->zhi;
   ra.wz = pl->dzf32;
   ra.mu = ctrl->mu;
-  ra.pmax_bits = &ctrl->pmax;
   ra.singular = pl->singular;
   ra.red = ctrl->red;
   ra.partial = partial;
-  ra.nblocks = pl->resid_blocks;
+  ra.nblocks = pl->resid_blocks;  // (informational; each launch sizes its own grid)
   ra.skip = skip;
   const double wsum_total = pl->wsum * pl->nx * pl->ny;
   if ((e = correction(true)) != cudaSuccess) return cuda_fail(pl, e, "initial solve");
   for (int it = 0; it <= pl->max_iter; ++it) {
     const bool last = (it == pl->max_iter);
-    ra.r = w;  // the last pass only checks; its r is not used
-    ra.first = (it == 0);
-    if ((e = run(pl, last ? K_CHK : K_RES, st, [&] { return launch_residual(ra, st); })) != cudaSuccess)
+    ra.rh_out = last ? nullptr : rh;  // the last pass only checks
+    ra.rl_out = last ? nullptr : rl;
+    ra.pmax_bits = it == 0 ? &ctrl->pmax : &ctrl->dmax;
+    ra.skip = skip;
+    if ((e = run(pl, last ? K_CHK : (it == 0 ? K_RES0 : K_RES), st,
+                 [&] { return launch_residual_inc(ra, it, 0, st); })) != cudaSuccess)
       return cuda_fail(pl, e, "residual");
     if ((e = run(pl, K_CTL, st, [&] {
-           return launch_finalize(ctrl, partial, pl->resid_blocks, wsum_total, pl->singular,
-                                  pl->rtol, it, last ? 1 : 0, info, st);
+           return launch_finalize(ctrl, partial, pl->resid_blocks2, wsum_total, pl->singular, pl->rtol,
+                                  it, 0, last ? 1 : 0, pl->anorm, nullptr, info, st);
          })) != cudaSuccess)
       return cuda_fail(pl, e, "finalize");
+    if (it == 0) {
+      // pass 0 again with the three-level split, only if its finalize asked for it
+      ResidArgs r3 = ra;
+      r3.skip = &ctrl->skip_redo;
+      if ((e = run(pl, K_RES3, st, [&] { return launch_residual_inc(r3, 0, 1, st); })) != cudaSuccess)
+        return cuda_fail(pl, e, "residual");
+      if ((e = run(pl, K_CTL, st, [&] {
+             return launch_finalize(ctrl, partial, pl->resid_blocks3, wsum_total, pl->singular,
+                                    pl->rtol, 0, 1, last ? 1 : 0, pl->anorm, &ctrl->skip_redo, info, st);
+           })) != cudaSuccess)
+        return cuda_fail(pl, e, "finalize");
+    }
     if (!last && (e = correction(false)) != cudaSuccess) return cuda_fail(pl, e, "correction");
   }
+  // Exact confirmation from the stored p, only when the drift bound of the
+  // incremental passes was not small (both kernels return at once otherwise).
+  ResidArgs rx = ra;
+  rx.r = rh;
+  rx.pmax_bits = &ctrl->pmax;
+  rx.skip = &ctrl->vskip;
+  if ((e = run(pl, K_VER, st, [&] { return launch_residual_exact(rx, st); })) != cudaSuccess)
+    return cuda_fail(pl, e, "exact residual");
+  if ((e = run(pl, K_CTL, st, [&] {
+         return launch_finalize_exact(ctrl, partial, pl->resid_blocks3, wsum_total, pl->singular,
+                                      pl->rtol, info, st);
+       })) != cudaSuccess)
+    return cuda_fail(pl, e, "finalize");
   return PS_OK;
 }
 
@@ -474,7 +524,9 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
   p->periodic_z = (bcz == PS_BC_PERIODIC);
   auto pn = [](int b) { return b == PS_BC_PERIODIC || b == PS_BC_NEUMANN_NEUMANN; };
   p->singular = pn(bcx) && pn(bcy) && pn(bcz);
-  p->resid_blocks = residual_blocks(nx, ny, nz);
+  p->resid_blocks3 = residual_blocks(nx, ny, nz, 1);
+  p->resid_blocks2 = residual_blocks(nx, ny, nz, 0);
+  p->resid_blocks = p->resid_blocks3 > p->resid_blocks2 ? p->resid_blocks3 : p->resid_blocks2;
 
   // ---- z metric (finite-volume form of Eq. 4 on the faces) ----
   std::vector<double> dzf(nz), dzc(nz > 1 ? nz - 1 : 0), za(nz, 0.0), zb(nz, 0.0), zc(nz, 0.0);
@@ -514,6 +566,15 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
     p->idx2 = df{t.x, t.y};
     split_df(1.0 / (dy * dy), &t);
     p->idy2 = df{t.x, t.y};
+  }
+  {
+    // every row: |diagonal| + Σ|off-diagonal| ≤ 2·(off-diagonal sum) + Dirichlet terms
+    double zmax = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      const double zr = std::fabs(za[k]) + std::fabs(zb[k]) + std::fabs(zc[k]);
+      zmax = zr > zmax ? zr : zmax;
+    }
+    p->anorm = 8.0 / (dx * dx) + 8.0 / (dy * dy) + zmax;
   }
 
   // ---- axis tables ----

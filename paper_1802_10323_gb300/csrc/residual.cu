@@ -1,27 +1,38 @@
-// residual.cu — r = f − A·Φ (Eq. 4) for the iterative refinement, in double-float.
+// residual.cu — residuals r = f − A·Φ (Eq. 4) of the iterative refinement, in double-float.
 //
-// Φ and f are FP64 fields. FP64 arithmetic and f64<->f32 conversions issue at
-// ~1/64 of the FP32 rate on this part, so each value is split on its bit pattern
-// into hi + lo floats (48 significant bits) and the 7-point stencil is evaluated
-// with error-free transformations (TwoSum, FMA products). The residual is
-// rounded once to FP32 (the right-hand side of the next FP32 correction solve).
+// FP64 arithmetic and f64<->f32 conversions issue at ~1/64 of the FP32 rate on
+// this part, so the 7-point stencil is evaluated in FP32 with error-free
+// transformations (TwoSum, FMA products; "double-float", ~48 significant bits).
+// Two kinds of pass share one kernel template:
+//   * incremental (every pass of the refinement loop): the stencil operand U is
+//     an FP32 field — the FP32 solve Φ_0 in pass 0 (its FP64 widening is the
+//     stored Φ, exactly), the last correction e in later passes — and
+//       pass 0:  r_0 = f − A·Φ_0                 (f FP64, split on its bit pattern)
+//       pass m:  r_m = r_{m−1} − c_m − A·e_{m−1}  (r_{m−1} stored as FP32 hi + lo)
+//     with c_1 = μ_f (singular problems) and c_m = 0 otherwise. The result is
+//     stored as hi + lo (the hi part is the right-hand side of the next FP32
+//     correction solve). Since e is small, A·e is evaluated to ~2^-44 of |e|, not
+//     of |Φ|, so later passes are more accurate than a fresh evaluation;
+//   * exact (an optional confirmation at the end): r = f − μ_f − A·Φ from the
+//     stored FP64 Φ, split on its bit pattern.
 //
-// Splitting: Φ = ph + pl with ph on a fixed-point grid 2^−s common to the whole
-// field (s from max|Φ|, so |ph|·2^s < 2^20): the stencil sums of ph are exact
-// in FP32, the four products with the double-float coefficients are made exact
-// with FMA, and the small pl part only needs FP32. f is split into hi + lo.
+// Splitting the operand: U = ph + pl with ph on a fixed-point grid 2^−s common to
+// the whole field (s from max|U|, so |ph|·2^s < 2^20): the stencil sums of ph are
+// exact in FP32, the four products with the double-float coefficients are made
+// exact with FMA, and the small pl part only needs FP32. For an FP32 U the split
+// is exact (pl = U − ph has at most 24 bits); for an FP64 U, pl is rounded.
 //
-// Blocking: a CTA of 32 × 8 threads owns a 32 × (8·RPT) (x, y) tile and
-// marches along z over a chunk of planes; each thread computes RPT consecutive
-// rows of one x column. Raw FP64 planes of Φ (tile plus one halo cell per side)
-// stream into a shared-memory ring with cp.async, RDEPTH − 2 planes ahead of
-// the one being split; each plane is split once into fixed-point pairs (two
-// plane slots), from which the in-plane neighbours are read. The z neighbours
-// of a thread's own cells stay in registers (planes k−1, k, k+1), and f streams
+// Blocking: a CTA of 32 × 8 threads owns a 32 × (8·RPT) (x, y) tile and marches
+// along z over a chunk of planes; each thread computes RPT consecutive rows of one
+// x column. Raw planes of U (tile plus one halo cell per side) stream into a
+// shared-memory ring with cp.async, RDEPTH − 2 planes ahead of the one being
+// split; each plane is split once into fixed-point pairs (two plane slots), from
+// which the in-plane neighbours are read. The z neighbours of a thread's own
+// cells stay in registers (planes k−1, k, k+1), and the base (f or r) streams
 // through registers one plane ahead with plain loads. The kernel is bound by
-// instruction issue rather than bytes, so the per-plane work that does not
-// scale with the points (ring control, barriers, coefficient loads) is shared
-// by RPT points and the ring slots advance by counters, not by division.
+// instruction issue rather than bytes, so the per-plane work that does not scale
+// with the points is shared by RPT points, the ring slots advance by counters,
+// the pass kind is compile-time and interior tiles skip the per-point domain tests.
 //
 // Ends of each axis (staggered ghost rules of Table 1) are folded into the halo
 // load: a periodic end wraps; a Neumann end loads the adjacent interior cell
@@ -30,12 +41,11 @@
 // planes below k = 0 and above k = n_z − 1, and the coefficients zlo/zhi hold
 // a_k, c_k, the wrap couplings, or 1/(Δz^f)² at a Dirichlet end.
 //
-// Reductions per pass (deterministic): max and min of r and of f (order-
-// preserving integer keys, atomicMax/atomicMin), and, for singular problems,
-// per-block double-float sums of Δz^f·r and Δz^f·f for the weighted means. The
-// finalize kernel forms ‖r_c‖∞ = max(max r − μ_r, μ_r − min r) and the same for
-// f, compares with rtol and sets the convergence flag that makes every later
-// kernel of the solve return at once.
+// Reductions per pass (deterministic): max and min of r (and of f in pass 0)
+// through order-preserving integer keys, and, for singular problems, per-block
+// double-float sums of Δz^f·r (and Δz^f·f in pass 0) for the weighted means. The
+// finalize kernels form ‖r_c‖∞ = max(max r − μ_r, μ_r − min r) and the same for
+// f, compare with rtol and set the flags that make later kernels return at once.
 #include <type_traits>
 
 #include "internal.h"
@@ -46,9 +56,19 @@ enum { END_WRAP = 0, END_N = 1, END_D = 2 };
 constexpr int RTX = 32, RWARPS = 8, RTHREADS = RTX * RWARPS;
 constexpr int RDEPTH = 4;  // raw-plane ring: k+1 being split, k+2 … k+3 in flight
 
+// Pass kinds (bit flags of the kernel template).
+enum : int {
+  RK_SING = 1,    // singular problem: weighted sum of r
+  RK_FIRST = 2,   // pass 0: max/min of f, and (singular) the weighted sum of f
+  RK_SUBMU = 4,   // subtract μ_f (double-float) from the base
+  RK_U32 = 8,     // operand U is FP32 (else FP64)
+  RK_DFBASE = 16, // base is r_{m−1} = hi + lo (else f, FP64)
+  RK_SPLIT3 = 32  // three-level split of U (pass 0 and the exact pass; see below)
+};
+
 __host__ __device__ constexpr int resid_cells(int rpt) { return (RTX + 2) * (RWARPS * rpt + 2); }
-__host__ __device__ constexpr size_t resid_smem(int rpt) {
-  return (size_t)(RDEPTH + 2) * resid_cells(rpt) * sizeof(double);
+__host__ __device__ constexpr size_t resid_smem(int rpt, int usize, int csize) {
+  return (size_t)RDEPTH * resid_cells(rpt) * usize + (size_t)2 * resid_cells(rpt) * csize;
 }
 
 __device__ __forceinline__ int end_lo(int bc) { return bc == BC_P ? END_WRAP : (bc == BC_DD ? END_D : END_N); }
@@ -60,12 +80,24 @@ __device__ __forceinline__ df add_u(df a, df b) {
   return {s.h, s.l + a.l + b.l};
 }
 
-// Φ on a fixed-point grid: ph = rint(Φ·2^s)·2^−s (|Φ·2^s| < 2^20 for every Φ of
+// U on a fixed-point grid: ph = rint(U·2^s)·2^−s (|U·2^s| < 2^20 for every U of
 // the field, so sums and differences of a few ph are exact in FP32) and
-// pl = Φ − ph rounded to FP32 (|pl| ≤ 2^−s−1). A·ph is then exact up to the
-// coefficient products, and A·pl only needs FP32.
+// pl = U − ph (|pl| ≤ 2^−s−1), exact for an FP32 U and rounded to FP32 for an FP64
+// U. A·ph is then exact up to the coefficient products, and A·pl only needs FP32.
+//
+// The FP32 evaluation of A·pl errs by ~2^−24·‖A‖·2^−s ≈ 2^−44·‖A‖·max|U|: pl is
+// noise-like, so its second differences do not cancel before they meet the large
+// z coefficients. That is small against the residual when U is a correction, but
+// not when U is the whole solution of an ill-conditioned problem (‖A‖·max|Φ| ≫
+// max|f|). Pass 0 and the exact pass therefore split three ways, U = ph + pm + pr
+// with pm on the grid 2^−s−20 as well: the sums of pm are exact too, their
+// products with the coefficients are made exact with FMA and summed in
+// double-float, and only pr (≤ 2^−s−21) is evaluated in FP32.
 struct fxp {
   float h, l;
+};
+struct __align__(16) fxp3 {
+  float h, m, l, pad;
 };
 __device__ __forceinline__ fxp to_fxp(double d, float S, float iS) {
   float h, l;
@@ -73,31 +105,74 @@ __device__ __forceinline__ fxp to_fxp(double d, float S, float iS) {
   const float ph = __fmul_rn(rintf(__fmul_rn(h, S)), iS);
   return {ph, __fadd_rn(__fsub_rn(h, ph), l)};
 }
+__device__ __forceinline__ fxp to_fxp(float u, float S, float iS) {
+  const float ph = __fmul_rn(rintf(__fmul_rn(u, S)), iS);
+  return {ph, __fsub_rn(u, ph)};
+}
+// Three levels of an FP64 value from its 53-bit significand M (x = ±M·2^(eb−1075)):
+// x·2^(s+20) = I + F·2^−sh with the integer I < 2^40 and sh ≥ 13 fraction bits;
+// ph = ⌊I/2^20⌋·2^−s, pm = (I mod 2^20)·2^−s−20 and pr = F·2^(eb−1075) are exact in
+// FP32 for |x| near max|x| (pr then has ≤ 13 bits); smaller values round only pr,
+// by 2^−24 of itself. (Truncating x to 48 bits instead would leave ~2^−48·|x| of
+// noise, which ‖A‖ amplifies.)
+__device__ __forceinline__ fxp3 to_fxp3(double x, int sc, float iS, float iS2) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = max(0, 1075 - 20 - sc - eb);
+  const unsigned long long I = sh >= 64 ? 0ull : (M >> sh);
+  const unsigned long long F = sh >= 64 ? M : (M - (I << sh));
+  const int er = eb - 948;  // biased FP32 exponent of 2^(eb−1075)
+  const float scale = __uint_as_float((uint32_t)(er > 0 ? er : 0) << 23);
+  float ph = __fmul_rn(__ull2float_rn(I >> 20), iS);
+  float pm = __fmul_rn((float)(uint32_t)(I & 0xFFFFFull), iS2);
+  float pr = __fmul_rn(__ull2float_rn(F), scale);
+  if (eb == 0) ph = pm = pr = 0.f;  // zero (and subnormals, below every grid here)
+  if (b >> 63) {
+    ph = -ph;
+    pm = -pm;
+    pr = -pr;
+  }
+  return {ph, pm, pr, 0.f};
+}
+// three levels of an FP32 value (exact); S2 = S·2^20, iS2 = iS·2^−20
+__device__ __forceinline__ fxp3 to_fxp3(float u, float S, float iS, float S2, float iS2) {
+  const float ph = __fmul_rn(rintf(__fmul_rn(u, S)), iS);
+  const float d = __fsub_rn(u, ph);  // exact
+  const float pm = __fmul_rn(rintf(__fmul_rn(d, S2)), iS2);
+  return {ph, pm, __fsub_rn(d, pm), 0.f};
+}
 // exact product of an FP32 value and a double-float coefficient, unevaluated
 __device__ __forceinline__ df prod(float x, df w) {
   const float p = __fmul_rn(x, w.h);
   return {p, __fmaf_rn(x, w.l, __fmaf_rn(x, w.h, -p))};
 }
+// flip the sign (bit 31 of the float, of the high word of the double) when sgn is set
 __device__ __forceinline__ double flip_sign(double d, uint32_t sgn) {
   return __hiloint2double(__double2hiint(d) ^ (int)sgn, __double2loint(d));
 }
+__device__ __forceinline__ float flip_sign(float u, uint32_t sgn) {
+  return __uint_as_float(__float_as_uint(u) ^ sgn);
+}
 
-// 8-byte asynchronous global→shared copy; a zero source size fills zeros and
+// Asynchronous global→shared copy of B bytes; a zero source size fills zeros and
 // reads nothing (used for cells that no in-domain point needs).
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem),
-               "r"(valid ? 8 : 0));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(B),
+               "r"(valid ? B : 0));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// MODE: 0 non-singular; 1 singular (subtract μ_f, weighted sum of r); 2 the
-// singular problem's first pass (also the weighted sum of f that gives μ_f).
-template <int RPT, int MODE>
+template <int RPT, int KIND>
 __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(ResidArgs a) {
-  constexpr bool SING = MODE >= 1, FIRST = MODE == 2;
+  constexpr bool SING = KIND & RK_SING, FIRST = KIND & RK_FIRST, SUBMU = KIND & RK_SUBMU;
+  constexpr bool U32 = KIND & RK_U32, DFBASE = KIND & RK_DFBASE, SPLIT3 = KIND & RK_SPLIT3;
+  using UT = typename std::conditional<U32, float, double>::type;
+  using CT = typename std::conditional<SPLIT3, fxp3, fxp>::type;  // a split cell
   constexpr int TY = RWARPS * RPT, W = RTX + 2, CELLS = resid_cells(RPT);
   constexpr int CPT = (CELLS + RTHREADS - 1) / RTHREADS;  // halo cells per thread
   if (a.skip && *a.skip) return;
@@ -110,18 +185,20 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   const bool perz = (a.bcz == BC_P);
   const uint32_t zsg_lo = end_lo(a.bcz) == END_D ? 0x80000000u : 0u;
   const uint32_t zsg_hi = end_hi(a.bcz) == END_D ? 0x80000000u : 0u;
-  float S, iS;
+  float S, iS, S2, iS2;
+  int sc;
   {
-    const int e = (int)((*a.pmax_bits >> 52) & 0x7FF) - 1023;  // max|Φ| ∈ [2^e, 2^(e+1))
-    const int sc = max(-100, min(100, 19 - e));
+    const int e = (int)((*a.pmax_bits >> 52) & 0x7FF) - 1023;  // max|U| ∈ [2^e, 2^(e+1))
+    sc = max(-100, min(100, 19 - e));
     S = __uint_as_float((uint32_t)(sc + 127) << 23);
     iS = __uint_as_float((uint32_t)(127 - sc) << 23);
+    S2 = __uint_as_float((uint32_t)(sc + 20 + 127) << 23);
+    iS2 = __uint_as_float((uint32_t)(127 - sc - 20) << 23);
   }
   extern __shared__ __align__(16) double rsm[];
-  double* raw = rsm;                                       // [RDEPTH][CELLS] raw Φ planes
-  fxp* fx = reinterpret_cast<fxp*>(rsm + RDEPTH * CELLS);  // [2][CELLS] split planes
-  const double* __restrict__ P = a.p;
-  const double* __restrict__ F = a.f;
+  UT* raw = reinterpret_cast<UT*>(rsm);  // [RDEPTH][CELLS]
+  CT* fx = reinterpret_cast<CT*>(reinterpret_cast<char*>(rsm) + RDEPTH * CELLS * sizeof(UT));  // [2][CELLS]
+  const UT* __restrict__ P = static_cast<const UT*>(U32 ? static_cast<const void*>(a.u) : a.p);
 
   // The halo-rectangle cells this thread copies and splits: in-plane offset of
   // the source cell, and per-cell bits "copy" and "flip sign" (Dirichlet ghost).
@@ -157,24 +234,28 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   }
   auto issue = [&](int q, int slot) {  // raw copies of logical plane q (wrap or clamp in z)
     const int pq = q < 0 ? (perz ? q + nz : 0) : (q >= nz ? (perz ? q - nz : nz - 1) : q);
-    const double* src = P + (size_t)pq * sxy;
-    double* dst = raw + slot * CELLS;
+    const UT* src = P + (size_t)pq * sxy;
+    UT* dst = raw + slot * CELLS;
 #pragma unroll
     for (int h = 0; h < CPT; ++h) {
       const int e = tid + h * RTHREADS;
-      if (h < CPT - 1 || e < CELLS) cp_async8(dst + e, src + off[h], (okm >> h) & 1u);
+      if (h < CPT - 1 || e < CELLS) cp_async<sizeof(UT)>(dst + e, src + off[h], (okm >> h) & 1u);
     }
     cp_commit();
   };
   auto convert = [&](int q, int slot, int fslot) {  // split logical plane q
     const uint32_t zs = q < 0 ? zsg_lo : (q >= nz ? zsg_hi : 0u);
-    const double* src = raw + slot * CELLS;
-    fxp* dst = fx + fslot * CELLS;
+    const UT* src = raw + slot * CELLS;
+    CT* dst = fx + fslot * CELLS;
 #pragma unroll
     for (int h = 0; h < CPT; ++h) {
       const int e = tid + h * RTHREADS;
-      if (h < CPT - 1 || e < CELLS)
-        dst[e] = to_fxp(flip_sign(src[e], (((negm >> h) & 1u) << 31) ^ zs), S, iS);
+      if (h < CPT - 1 || e < CELLS) {
+        const UT x = flip_sign(src[e], (((negm >> h) & 1u) << 31) ^ zs);
+        if constexpr (SPLIT3 && U32) dst[e] = to_fxp3(x, S, iS, S2, iS2);
+        else if constexpr (SPLIT3) dst[e] = to_fxp3(x, sc, iS, iS2);
+        else dst[e] = to_fxp(x, S, iS);
+      }
     }
   };
 
@@ -188,12 +269,22 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   // Interior tiles (every row and column in the domain) take a copy of the
   // march without the per-point domain tests.
   const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny);
-  const double* fcol = F + (size_t)jb * nx + i;  // this thread's column, row jb, plane 0
-  auto load_f = [&](int k, double* fv, auto full_tag) {
+  const size_t col = (size_t)jb * nx + i;  // this thread's column, row jb, plane 0
+  // the base of each point: f (FP64, split into hi + lo) or r_{m−1} = hi + lo
+  using base_t = typename std::conditional<DFBASE, float2, double>::type;
+  auto load_base = [&](int k, base_t* bv, auto full_tag) {
     constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-    for (int m = 0; m < RPT; ++m)
-      fv[m] = (FULL || in[m]) ? __ldg(fcol + (size_t)k * sxy + (size_t)m * nx) : 0.0;
+    for (int m = 0; m < RPT; ++m) {
+      const size_t g = (size_t)k * sxy + col + (size_t)m * nx;
+      const bool ld = FULL || in[m];
+      if constexpr (DFBASE) {
+        bv[m].x = ld ? __ldg(a.rh_in + g) : 0.f;
+        bv[m].y = ld ? __ldg(a.rl_in + g) : 0.f;
+      } else {
+        bv[m] = ld ? __ldg(a.f + g) : 0.0;
+      }
+    }
   };
 
   // prologue: planes k0−1 … k0+RDEPTH−2 in flight; split k0−1 and k0
@@ -202,15 +293,15 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     if (k0 - 1 + q <= k1) issue(k0 - 1 + q, q);
     else cp_commit();
   }
-  double fcur[RPT], fnext[RPT];
-  if (interior) load_f(k0, fcur, std::true_type{});
-  else load_f(k0, fcur, std::false_type{});
+  base_t bcur[RPT], bnext[RPT];
+  if (interior) load_base(k0, bcur, std::true_type{});
+  else load_base(k0, bcur, std::false_type{});
   cp_wait<RDEPTH - 2>();
   __syncthreads();
   convert(k0 - 1, 0, 0);
   convert(k0, 1, 1);
   __syncthreads();
-  fxp zm[RPT], zc[RPT], zp[RPT];
+  CT zm[RPT], zc[RPT], zp[RPT];
 #pragma unroll
   for (int m = 0; m < RPT; ++m) {
     zm[m] = fx[cidx[m]];
@@ -220,14 +311,14 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   float rmax = -INFINITY, rmin = INFINITY, fmax_ = -INFINITY, fmin_ = INFINITY;
   float wr = 0.f;
   df wf = {0.f, 0.f};
-  const df mu = SING ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
+  const df mu = SUBMU ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
   int islot = 0;                 // raw slot of plane k + RDEPTH − 1 (≡ k − k0 mod RDEPTH)
   int cslot = 2 % RDEPTH;        // raw slot of plane k + 1
   auto march = [&](auto full_tag) {
   constexpr bool FULL = decltype(full_tag)::value;
   for (int k = k0; k < k1; ++k) {
     const int par = (k - k0) & 1;  // split slot of plane k+1; plane k is in 1 − par
-    if (k + 1 < k1) load_f(k + 1, fnext, full_tag);
+    if (k + 1 < k1) load_base(k + 1, bnext, full_tag);
     // keep the ring full (an empty group keeps the wait count uniform)
     if (k + RDEPTH - 1 <= k1) issue(k + RDEPTH - 1, islot);
     else cp_commit();
@@ -237,21 +328,23 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     __syncthreads();
     islot = (islot + 1 == RDEPTH) ? 0 : islot + 1;
     cslot = (cslot + 1 == RDEPTH) ? 0 : cslot + 1;
-    const fxp* Fc = fx + (1 - par) * CELLS;
-    const fxp* Fn = fx + par * CELLS;
+    const CT* Fc = fx + (1 - par) * CELLS;
+    const CT* Fn = fx + par * CELLS;
 #pragma unroll
     for (int m = 0; m < RPT; ++m) zp[m] = Fn[cidx[m]];
     const float2 cl = __ldg(a.zlo + k), ch = __ldg(a.zhi + k);
     const float w = SING ? __ldg(a.wz + k) : 0.f;
-    float* rcol = a.r + (size_t)k * sxy + (size_t)jb * nx + i;
+    const size_t gk = (size_t)k * sxy + col;
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
-      const fxp pc = zc[m];
-      const fxp xm = Fc[cidx[m] - 1], xp = Fc[cidx[m] + 1];
-      const fxp ym = (m == 0) ? Fc[cidx[0] - W] : zc[m > 0 ? m - 1 : 0];
-      const fxp yp = (m == RPT - 1) ? Fc[cidx[RPT - 1] + W] : zc[m + 1 < RPT ? m + 1 : 0];
-      const fxp zmv = zm[m], zpv = zp[m];
-      const df fv = df_from_f64(fcur[m]);
+      const CT pc = zc[m];
+      const CT xm = Fc[cidx[m] - 1], xp = Fc[cidx[m] + 1];
+      const CT ym = (m == 0) ? Fc[cidx[0] - W] : zc[m > 0 ? m - 1 : 0];
+      const CT yp = (m == RPT - 1) ? Fc[cidx[RPT - 1] + W] : zc[m + 1 < RPT ? m + 1 : 0];
+      const CT zmv = zm[m], zpv = zp[m];
+      df bv;
+      if constexpr (DFBASE) bv = {bcur[m].x, bcur[m].y};
+      else bv = df_from_f64(bcur[m]);
       // exact high-part stencil sums (fixed-point grid), FP32 low parts
       const float sx = (xm.h + xp.h) - 2.f * pc.h, sy = (ym.h + yp.h) - 2.f * pc.h;
       const float dm = zmv.h - pc.h, dpz = zpv.h - pc.h;
@@ -261,30 +354,52 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
       const df t3 = prod(dm, df{cl.x, cl.y}), t4 = prod(dpz, df{ch.x, ch.y});
       const df s12 = two_sum(t1.h, t2.h);
       const df s123 = two_sum(s12.h, t3.h);
-      const df s1234 = two_sum(s123.h, t4.h);
-      const float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
+      df s1234 = two_sum(s123.h, t4.h);
+      float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
+      if constexpr (SPLIT3) {
+        // the middle level: exact sums on its grid, exact products, double-float sums
+        const float mx = (xm.m + xp.m) - 2.f * pc.m, my = (ym.m + yp.m) - 2.f * pc.m;
+        const df u1 = prod(mx, a.idx2), u2 = prod(my, a.idy2);
+        const df u3 = prod(zmv.m - pc.m, df{cl.x, cl.y}), u4 = prod(zpv.m - pc.m, df{ch.x, ch.y});
+        const df m12 = two_sum(u1.h, u2.h);
+        const df m123 = two_sum(m12.h, u3.h);
+        const df m1234 = two_sum(m123.h, u4.h);
+        const df hm = two_sum(s1234.h, m1234.h);
+        s1234 = {hm.h, 0.f};
+        ap_lo += ((m12.l + m123.l) + (m1234.l + u1.l)) + ((u2.l + u3.l) + (u4.l + hm.l));
+      }
       df r;
-      if (SING) {
-        const df d1 = two_sum(fv.h, -mu.h);
+      if constexpr (SUBMU) {
+        const df d1 = two_sum(bv.h, -mu.h);
         const df d2 = two_sum(d1.h, -s1234.h);
-        r = {d2.h, ((d1.l + d2.l) + (fv.l - mu.l)) - ap_lo};
+        r = {d2.h, ((d1.l + d2.l) + (bv.l - mu.l)) - ap_lo};
       } else {
-        const df d2 = two_sum(fv.h, -s1234.h);
-        r = {d2.h, (d2.l + fv.l) - ap_lo};
+        const df d2 = two_sum(bv.h, -s1234.h);
+        r = {d2.h, (d2.l + bv.l) - ap_lo};
       }
       const float rf = r.h + r.l;
       if (FULL || in[m]) {
-        rcol[(size_t)m * nx] = rf;
-        const float ff = fv.h + fv.l;
+        const size_t g = gk + (size_t)m * nx;
+        if constexpr (U32) {
+          if (a.rh_out) {
+            a.rh_out[g] = rf;
+            a.rl_out[g] = r.l - (rf - r.h);
+          }
+        } else {
+          a.r[g] = rf;
+        }
         rmax = fmaxf(rmax, rf);
         rmin = fminf(rmin, rf);
-        fmax_ = fmaxf(fmax_, ff);
-        fmin_ = fminf(fmin_, ff);
-        if (SING) {
+        if constexpr (FIRST) {
+          const float ff = bv.h + bv.l;
+          fmax_ = fmaxf(fmax_, ff);
+          fmin_ = fminf(fmin_, ff);
+        }
+        if constexpr (SING) {
           wr = fmaf(w, rf, wr);
-          if (FIRST) {  // Σ Δz^f·f in double-float (only the first pass needs μ_f)
-            wf = add_u(wf, prod(fv.h, df{w, 0.f}));
-            wf.l = fmaf(w, fv.l, wf.l);
+          if constexpr (FIRST) {  // Σ Δz^f·f in double-float (only pass 0 needs μ_f)
+            wf = add_u(wf, prod(bv.h, df{w, 0.f}));
+            wf.l = fmaf(w, bv.l, wf.l);
           }
         }
       }
@@ -293,7 +408,7 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     for (int m = 0; m < RPT; ++m) {
       zm[m] = zc[m];
       zc[m] = zp[m];
-      fcur[m] = fnext[m];
+      bcur[m] = bnext[m];
     }
   }
   };
@@ -330,20 +445,24 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     }
     atomicMax(&a.red[0], f32_key(rmax));
     atomicMin(&a.red[1], f32_key(rmin));
-    atomicMax(&a.red[2], f32_key(fmax_));
-    atomicMin(&a.red[3], f32_key(fmin_));
+    if (FIRST) {
+      atomicMax(&a.red[2], f32_key(fmax_));
+      atomicMin(&a.red[3], f32_key(fmin_));
+    }
     const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     reinterpret_cast<float4*>(a.partial)[bid] = make_float4(wrd.h, wrd.l, wf.h, wf.l);
   }
 }
 
-// Resets the reduction words before a residual pass.
-__global__ void reset_red_kernel(int* red, const int* skip) {
+// Resets the reduction words of r (and of f in pass 0) before a residual pass.
+__global__ void reset_red_kernel(int* red, const int* skip, int with_f) {
   if (skip && *skip) return;
   red[0] = f32_key(-INFINITY);
   red[1] = f32_key(INFINITY);
-  red[2] = f32_key(-INFINITY);
-  red[3] = f32_key(INFINITY);
+  if (with_f) {
+    red[2] = f32_key(-INFINITY);
+    red[3] = f32_key(INFINITY);
+  }
 }
 
 namespace {
@@ -352,9 +471,9 @@ struct ResidShape {
   int rpt, zchunk;
   dim3 grid;
 };
-ResidShape resid_shape(int nx, int ny, int nz) {
+ResidShape resid_shape(int nx, int ny, int nz, bool split3) {
   ResidShape s;
-  s.rpt = ny >= 4 * RWARPS ? 4 : 2;
+  s.rpt = (ny >= 4 * RWARPS && !split3) ? 4 : 2;  // three-level cells need the registers of two rows
   const int tiles = ((nx + RTX - 1) / RTX) * ((ny + RWARPS * s.rpt - 1) / (RWARPS * s.rpt));
   // about four waves of three CTAs per SM, 8 … 64 planes per CTA
   const long long want = 152LL * 3 * 4;
@@ -365,73 +484,131 @@ ResidShape resid_shape(int nx, int ny, int nz) {
                 (nz + s.zchunk - 1) / s.zchunk);
   return s;
 }
-template <int RPT, int MODE>
-cudaError_t launch_resid_mode(const ResidArgs& b, dim3 grid, cudaStream_t st) {
+template <int RPT, int KIND>
+cudaError_t launch_kind(const ResidArgs& b, dim3 grid, cudaStream_t st) {
+  constexpr size_t smem = resid_smem(RPT, (KIND & RK_U32) ? 4 : 8, (KIND & RK_SPLIT3) ? 16 : 8);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(residual_kernel<RPT, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)resid_smem(RPT));
+    cudaError_t e = cudaFuncSetAttribute(residual_kernel<RPT, KIND>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  residual_kernel<RPT, MODE><<<grid, dim3(RTX, RWARPS), resid_smem(RPT), st>>>(b);
+  residual_kernel<RPT, KIND><<<grid, dim3(RTX, RWARPS), smem, st>>>(b);
   return cudaGetLastError();
 }
 template <int RPT>
-cudaError_t launch_resid_rpt(const ResidArgs& b, dim3 grid, cudaStream_t st) {
-  if (!b.singular) return launch_resid_mode<RPT, 0>(b, grid, st);
-  return b.first ? launch_resid_mode<RPT, 2>(b, grid, st) : launch_resid_mode<RPT, 1>(b, grid, st);
+cudaError_t launch_rpt(const ResidArgs& b, int kind, dim3 grid, cudaStream_t st) {
+  if constexpr (RPT == 2) {  // the three-level passes run with two rows per thread only
+    switch (kind) {
+      case RK_SPLIT3: return launch_kind<RPT, RK_SPLIT3>(b, grid, st);
+      case RK_SPLIT3 | RK_SING | RK_SUBMU: return launch_kind<RPT, RK_SPLIT3 | RK_SING | RK_SUBMU>(b, grid, st);
+      case RK_SPLIT3 | RK_U32 | RK_FIRST: return launch_kind<RPT, RK_SPLIT3 | RK_U32 | RK_FIRST>(b, grid, st);
+      case RK_SPLIT3 | RK_U32 | RK_FIRST | RK_SING:
+        return launch_kind<RPT, RK_SPLIT3 | RK_U32 | RK_FIRST | RK_SING>(b, grid, st);
+      default: break;
+    }
+  }
+  switch (kind) {
+    case RK_U32 | RK_FIRST: return launch_kind<RPT, RK_U32 | RK_FIRST>(b, grid, st);
+    case RK_U32 | RK_FIRST | RK_SING: return launch_kind<RPT, RK_U32 | RK_FIRST | RK_SING>(b, grid, st);
+    case RK_U32 | RK_DFBASE: return launch_kind<RPT, RK_U32 | RK_DFBASE>(b, grid, st);
+    case RK_U32 | RK_DFBASE | RK_SING: return launch_kind<RPT, RK_U32 | RK_DFBASE | RK_SING>(b, grid, st);
+    case RK_U32 | RK_DFBASE | RK_SING | RK_SUBMU:
+      return launch_kind<RPT, RK_U32 | RK_DFBASE | RK_SING | RK_SUBMU>(b, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t launch_resid(const ResidArgs& b0, int kind, int reset_f, cudaStream_t st) {
+  reset_red_kernel<<<1, 1, 0, st>>>(b0.red, b0.skip, reset_f);
+  const ResidShape s = resid_shape(b0.nx, b0.ny, b0.nz, (kind & RK_SPLIT3) != 0);
+  ResidArgs b = b0;
+  b.zchunk = s.zchunk;
+  return s.rpt == 4 ? launch_rpt<4>(b, kind, s.grid, st) : launch_rpt<2>(b, kind, s.grid, st);
 }
 }  // namespace
 
-int residual_blocks(int nx, int ny, int nz) {
-  const ResidShape s = resid_shape(nx, ny, nz);
+int residual_blocks(int nx, int ny, int nz, int split3) {
+  const ResidShape s = resid_shape(nx, ny, nz, split3 != 0);
   return (int)(s.grid.x * s.grid.y * s.grid.z);
 }
 
-cudaError_t launch_residual(const ResidArgs& a, cudaStream_t st) {
-  if (!a.r) return cudaErrorInvalidValue;
-  reset_red_kernel<<<1, 1, 0, st>>>(a.red, a.skip);
-  const ResidShape s = resid_shape(a.nx, a.ny, a.nz);
-  ResidArgs b = a;
-  b.zchunk = s.zchunk;
-  return s.rpt == 4 ? launch_resid_rpt<4>(b, s.grid, st) : launch_resid_rpt<2>(b, s.grid, st);
+cudaError_t launch_residual_inc(const ResidArgs& a, int pass, int split3, cudaStream_t st) {
+  if (!a.u || (pass > 0 && (!a.rh_in || !a.rl_in)) || (!a.rh_out != !a.rl_out) || (split3 && pass))
+    return cudaErrorInvalidValue;
+  int kind = RK_U32;
+  if (pass == 0) kind |= RK_FIRST | (split3 ? RK_SPLIT3 : 0);
+  else kind |= RK_DFBASE;
+  if (a.singular) kind |= RK_SING;
+  if (a.singular && pass == 1) kind |= RK_SUBMU;
+  return launch_resid(a, kind, pass == 0, st);
 }
 
-// One CTA: weighted means (singular), norms, convergence test, info record.
-__global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* partial, int nblocks,
-                                                        double wsum_total, int singular, double rtol,
-                                                        int iteration, int last, ps_info* info) {
-  if (c->converged) return;
+cudaError_t launch_residual_exact(const ResidArgs& a, cudaStream_t st) {
+  if (!a.p || !a.r) return cudaErrorInvalidValue;
+  return launch_resid(a, RK_SPLIT3 | (a.singular ? (RK_SING | RK_SUBMU) : 0), 0, st);
+}
+
+namespace {
+// Σ over the per-block partials of (Δz^f·r, Δz^f·f) in double-float, one CTA;
+// thread 0 gets them in FP64.
+__device__ void sum_partials(const float* partial, int nblocks, double& sr_out, double& sf_out) {
   __shared__ df sr[32], sf[32];
-  if (singular) {
-    df ar = {0.f, 0.f}, af = {0.f, 0.f};
-    const float4* pv = reinterpret_cast<const float4*>(partial);
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      const float4 v = pv[b];
-      ar = add_u(ar, df{v.x, v.y});
-      af = add_u(af, df{v.z, v.w});
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      ar = add_u(ar, df{__shfl_xor_sync(0xffffffffu, ar.h, o), __shfl_xor_sync(0xffffffffu, ar.l, o)});
-      af = add_u(af, df{__shfl_xor_sync(0xffffffffu, af.h, o), __shfl_xor_sync(0xffffffffu, af.l, o)});
-    }
-    if ((threadIdx.x & 31) == 0) {
-      sr[threadIdx.x >> 5] = ar;
-      sf[threadIdx.x >> 5] = af;
-    }
+  df ar = {0.f, 0.f}, af = {0.f, 0.f};
+  const float4* pv = reinterpret_cast<const float4*>(partial);
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const float4 v = pv[b];
+    ar = add_u(ar, df{v.x, v.y});
+    af = add_u(af, df{v.z, v.w});
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar = add_u(ar, df{__shfl_xor_sync(0xffffffffu, ar.h, o), __shfl_xor_sync(0xffffffffu, ar.l, o)});
+    af = add_u(af, df{__shfl_xor_sync(0xffffffffu, af.h, o), __shfl_xor_sync(0xffffffffu, af.l, o)});
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = ar;
+    sf[threadIdx.x >> 5] = af;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double mr = 0.0, mf = 0.0;
-  if (singular) {
-    double s1 = 0.0, s2 = 0.0;
+  double s1 = 0.0, s2 = 0.0;
+  if (threadIdx.x == 0)
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       s1 += (double)sr[w].h + (double)sr[w].l;
       s2 += (double)sf[w].h + (double)sf[w].l;
     }
+  sr_out = s1;
+  sf_out = s2;
+}
+__device__ double bits_f64(unsigned long long b) { return __longlong_as_double((long long)b); }
+}  // namespace
+
+// One CTA after each pass of the refinement loop: weighted means (singular),
+// norms, the drift bound, the convergence test, the confirmation decision and
+// the info record.
+//
+// Pass 0 first runs with the two-level split, whose evaluation error is about
+// 2^-44·‖A‖∞·max|Φ_0| (bounded here by 2^-43·…). Every later residual inherits it,
+// so if that bound exceeds 5 % of rtol·‖f_c‖∞ this finalize (attempt 0) decides
+// nothing and asks for pass 0 again with the three-level split (attempt 1).
+//
+// Drift bound: pass m ≥ 1 evaluates r_{m−1} − A·e_{m−1} instead of f − A·Φ_m. It
+// differs from a fresh evaluation from the stored Φ_m by the evaluation error of
+// A·e_{m−1} (≤ 2^-43·‖A‖∞·max|e|) and by the FP64 rounding of Φ += e
+// (≤ 2^-52·‖A‖∞·max|Φ|). If the accumulated bound exceeds 5 % of rtol·‖f_c‖∞ when
+// the loop ends (converged or not), the exact pass at the end re-evaluates the
+// residual from the stored Φ and decides.
+__global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* partial, int nblocks,
+                                                        double wsum_total, int singular, double rtol,
+                                                        int iteration, int attempt, int last,
+                                                        double anorm, const int* skip, ps_info* info) {
+  if ((skip && *skip) || c->converged) return;
+  double s1 = 0.0, s2 = 0.0;
+  if (singular) sum_partials(partial, nblocks, s1, s2);
+  if (threadIdx.x != 0) return;
+  double mr = 0.0, mf = 0.0;
+  if (singular) {
     mr = s1 / wsum_total;
-    if (iteration == 0) {  // μ_f is measured once, on the first pass
+    if (iteration == 0) {  // μ_f is measured once, in pass 0
       mf = s2 / wsum_total;
       c->mf = mf;
       const float h = (float)mf;
@@ -441,17 +618,26 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
       mf = c->mf;
     }
   }
+  if (iteration > 0)
+    c->bnd += anorm * (ldexp(bits_f64(c->dmax), -43) + ldexp(bits_f64(c->pmax), -52));
+  c->dmax = 0;  // the next correction's x backward records max|e| here
   const double rmax = key_f32(c->red[0]), rmin = key_f32(c->red[1]);
   const double vfmax = key_f32(c->red[2]), vfmin = key_f32(c->red[3]);
   const double rn = fmax(rmax - mr, mr - rmin);
   const double fn = fmax(vfmax - mf, mf - vfmin);
   const double rel = fn > 0 ? rn / fn : (rn > 0 ? INFINITY : 0.0);
+  if (iteration == 0 && attempt == 0) {
+    const bool redo = ldexp(anorm * bits_f64(c->pmax), -43) > 0.05 * rtol * fn;
+    c->skip_redo = redo ? 0 : 1;
+    if (redo) return;
+  }
   c->rnorm = rn;
   c->fnorm = fn;
   c->rel = rel;
   c->iterations = iteration;
   const bool ok = rel <= rtol;
   if (ok) c->converged = 1;
+  if (ok || last) c->vskip = (c->bnd <= 0.05 * rtol * fn) ? 1 : 0;
   if (info && (ok || last)) {
     info->status = ok ? PS_OK : PS_NOT_CONVERGED;
     info->iterations = iteration;
@@ -461,11 +647,44 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
   }
 }
 
+// One CTA after the exact confirmation pass (which runs only when the drift
+// bound was not small): its residual decides the status.
+__global__ void __launch_bounds__(1024) finalize_exact_kernel(Ctrl* c, const float* partial, int nblocks,
+                                                              double wsum_total, int singular,
+                                                              double rtol, ps_info* info) {
+  if (c->vskip) return;
+  double s1 = 0.0, s2 = 0.0;
+  if (singular) sum_partials(partial, nblocks, s1, s2);
+  if (threadIdx.x != 0) return;
+  const double mr = singular ? s1 / wsum_total : 0.0, mf = singular ? c->mf : 0.0;
+  const double rmax = key_f32(c->red[0]), rmin = key_f32(c->red[1]);
+  const double vfmax = key_f32(c->red[2]), vfmin = key_f32(c->red[3]);
+  const double rn = fmax(rmax - mr, mr - rmin);
+  const double fn = fmax(vfmax - mf, mf - vfmin);
+  const double rel = fn > 0 ? rn / fn : (rn > 0 ? INFINITY : 0.0);
+  const bool ok = rel <= rtol;
+  c->rnorm = rn;
+  c->rel = rel;
+  if (info) {
+    info->status = ok ? PS_OK : PS_NOT_CONVERGED;
+    info->iterations = c->iterations;
+    info->rel_residual = rel;
+    info->r_norm = rn;
+    info->f_norm = fn;
+  }
+}
+
 cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
-                            int singular, double rtol, int iteration, int last, ps_info* info,
-                            cudaStream_t st) {
+                            int singular, double rtol, int iteration, int attempt, int last,
+                            double anorm, const int* skip, ps_info* info, cudaStream_t st) {
   finalize_kernel<<<1, 1024, 0, st>>>(ctrl, partial, nblocks, wsum_total, singular, rtol, iteration,
-                                      last, info);
+                                      attempt, last, anorm, skip, info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_exact(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
+                                  int singular, double rtol, ps_info* info, cudaStream_t st) {
+  finalize_exact_kernel<<<1, 1024, 0, st>>>(ctrl, partial, nblocks, wsum_total, singular, rtol, info);
   return cudaGetLastError();
 }
 

@@ -338,16 +338,13 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
     }
     T v = rO[l * ldr + e];
     if (!FWD && a.plane_scale) v *= a.plane_scale[z];
-    TO o;
-    if (a.accumulate) {
-      if constexpr (sizeof(TO) == 8) o = out[g] + st_cvt<TO, T>::f(v);
-      else o = out[g] + v;
-    } else {
-      o = st_cvt<TO, T>::f(v);
+    const TO x = st_cvt<TO, T>::f(v);
+    out[g] = a.accumulate ? out[g] + x : x;
+    if constexpr (sizeof(TO) == 8) {
+      amax = max(amax, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+      if constexpr (sizeof(T) == 4)
+        if (a.out2) a.out2[g] = v;
     }
-    out[g] = o;
-    if constexpr (sizeof(TO) == 8)
-      amax = max(amax, (unsigned long long)__double_as_longlong(o) & 0x7FFFFFFFFFFFFFFFull);
   }
   if constexpr (sizeof(TO) == 8) {
     if (a.amax) {

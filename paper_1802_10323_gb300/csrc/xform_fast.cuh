@@ -150,8 +150,9 @@ struct FastArgs {
   const T* plane_scale;
   int accumulate;
   const int* skip;
-  unsigned long long* amax;  // FP64 output: atomicMax of |value| bit patterns, or null
+  unsigned long long* amax;  // FP64 output: atomicMax of |transform output| bit patterns, or null
   int lpc;              // lines per CTA
+  float* out2;          // FP64 output (x lines): also store the FP32 transform output here, or null
 };
 
 template <class T, class TI, class TO, int M, bool FWD>

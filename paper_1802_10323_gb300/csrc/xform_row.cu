@@ -272,18 +272,26 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? 3 : 4
       __syncwarp();  // the last stage's buffer reads are done before the next line
       // ---- backward outputs straight from the last stage, as vectors ----
       // slot si = q·RL + r holds wavenumber k = t + q·TPL + r·(M/RL); k < M/2 iff r < RL/2
-      auto put = [&](int i0, const T* val, auto n_tag) {  // n consecutive outputs at i0
+      // n consecutive outputs at i0; an FP64 output may also keep its FP32 value in out2
+      // (the line's own input array: every input of the line is already in registers)
+      auto put = [&](int i0, const T* val, auto n_tag) {
         constexpr int NV = decltype(n_tag)::value;
         vec<TO, NV> o;
+        vec<T, NV> o2;
         if (a.accumulate) o = *reinterpret_cast<const vec<TO, NV>*>(dst + i0);
 #pragma unroll
         for (int u = 0; u < NV; ++u) {
-          const TO x = st_cvt<TO, T>::f(val[u] * s);
+          o2.v[u] = val[u] * s;
+          const TO x = st_cvt<TO, T>::f(o2.v[u]);
           o.v[u] = a.accumulate ? o.v[u] + x : x;
           if constexpr (sizeof(TO) == 8)
-            if (live) amax = max(amax, (unsigned long long)__double_as_longlong(o.v[u]) & 0x7FFFFFFFFFFFFFFFull);
+            if (live) amax = max(amax, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
         }
-        if (live) *reinterpret_cast<vec<TO, NV>*>(dst + i0) = o;
+        if (live) {
+          *reinterpret_cast<vec<TO, NV>*>(dst + i0) = o;
+          if constexpr (sizeof(TO) == 8 && sizeof(T) == 4)
+            if (a.out2) *reinterpret_cast<vec<T, NV>*>(a.out2 + base + i0) = o2;
+        }
       };
       using two = std::integral_constant<int, 2>;
       using four = std::integral_constant<int, 4>;
