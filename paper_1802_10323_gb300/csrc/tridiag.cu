@@ -15,26 +15,46 @@
 // singular z matrix. Its right-hand side loses its Δz^f-weighted mean, Φ̂_0 = 0
 // is pinned (row 0 dropped), and the solution's weighted mean is removed. A
 // separate one-CTA kernel does this column from shared memory.
+#include <type_traits>
+
 #include "tridiag_dev.cuh"
 
 namespace ps {
 
 // FP32, non-periodic columns: the forward sweep keeps the eliminated
 // (c'_k, d'_k) only at the end of every chunk of ZK planes (1/8 of the data
-// volume, in the scratch array); the backward sweep walks the chunks from the top, re-reads each
-// chunk's right-hand side, recomputes its (c', d') from the checkpoint in
-// registers (the same instructions on the same inputs, so bit-identical to the
-// forward sweep) and back-substitutes. HBM traffic: read f̂ twice (the second
-// read of a chunk usually hits L2), write Φ̂ once; loads of the next chunk are
-// issued before the current chunk is processed.
+// volume, in the scratch array); the backward sweep walks the chunks from the top,
+// re-reads each chunk's right-hand side, recomputes its (c', d') from the
+// checkpoint in registers (the same instructions on the same inputs, so
+// bit-identical to the forward sweep) and back-substitutes. HBM traffic: read f̂
+// twice (the second read of a chunk often hits L2), write Φ̂ once; loads of the
+// next chunk are issued before the current chunk is processed. The coefficients
+// (a_k, b_k, c_k), with a_0 = c_{n−1} = 0, sit in a shared table (one broadcast
+// load per row) and whole chunks run without per-row bound tests.
 template <class T>
 cudaError_t launch_zsolve(ZArgs<T> a, cudaStream_t st);
 
 constexpr int ZK = 16;
-constexpr int ZB = 128;  // columns (threads) per CTA
+constexpr int ZB = 128;            // columns (threads) per CTA
+constexpr int ZTAB_MAX = 4096;     // planes whose coefficient table fits in shared memory
 
+template <bool TAB>
 __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
   if (a.skip && *a.skip) return;
+  extern __shared__ float4 ztab[];  // [nz] (a_k, b_k, c_k, ·) when TAB
+  const int nz = a.nz;
+  auto coef = [&](int k) -> float4 {
+    if constexpr (TAB) {
+      return ztab[k];
+    } else {
+      return make_float4(k > 0 ? __ldg(a.za + k) : 0.f, __ldg(a.zb + k), k < nz - 1 ? __ldg(a.zc + k) : 0.f, 0.f);
+    }
+  };
+  if constexpr (TAB) {
+    for (int k = threadIdx.x; k < nz; k += ZB)
+      ztab[k] = make_float4(k > 0 ? a.za[k] : 0.f, a.zb[k], k < nz - 1 ? a.zc[k] : 0.f, 0.f);
+    __syncthreads();
+  }
   const int ncol = a.nx * a.ny;
   float2* __restrict__ ck = reinterpret_cast<float2*>(a.scr_c);  // [nchunk][ncol]
   const int col = blockIdx.x * ZB + threadIdx.x;
@@ -43,80 +63,69 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
   const int i = colc % a.nx, j = colc / a.nx;
   const float lam = a.lamx[i] + a.lamy[j];
   const size_t st = (size_t)ncol;
-  const int nz = a.nz;
-  const int nch = (nz + ZK - 1) / ZK;
+  const int nch = (nz + ZK - 1) / ZK, nfull = nz / ZK;
   float* __restrict__ d = a.data + colc;
-  const float* __restrict__ za = a.za;
-  const float* __restrict__ zb = a.zb;
-  const float* __restrict__ zc = a.zc;
 
-  float cur[ZK], nxt[ZK];
-#pragma unroll
-  for (int u = 0; u < ZK; ++u) cur[u] = (u < nz) ? d[(size_t)u * st] : 0.f;
-  float cp = 0.f, dp = 0.f;
-  for (int c = 0; c < nch; ++c) {
-    const int k0 = c * ZK;
-    if (c + 1 < nch) {
-#pragma unroll
-      for (int u = 0; u < ZK; ++u) {
-        const int k = k0 + ZK + u;
-        nxt[u] = (k < nz) ? d[(size_t)k * st] : 0.f;
-      }
-    }
+  // one chunk of the elimination: rows k0 … k0+ZK−1 (all present when FULL)
+  auto eliminate = [&](int k0, const float* cur, float& cp, float& dp, float* cpa, float* dpa,
+                       auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
     for (int u = 0; u < ZK; ++u) {
       const int k = k0 + u;
-      if (k < nz) {
-        const float ak = (k > 0) ? za[k] : 0.f;
-        const float ckk = (k < nz - 1) ? zc[k] : 0.f;
-        const float mk = __fdividef(1.f, zb[k] + lam - ak * cp);
-        cp = ckk * mk;
-        dp = (cur[u] - ak * dp) * mk;
+      if (FULL || k < nz) {
+        const float4 q = coef(k);
+        const float mk = __fdividef(1.f, q.y + lam - q.x * cp);
+        cp = q.z * mk;
+        dp = (cur[u] - q.x * dp) * mk;
+      }
+      if (cpa) {
+        cpa[u] = cp;
+        dpa[u] = dp;
       }
     }
+  };
+  auto load = [&](int k0, float* buf, auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    const float* src = d + (size_t)k0 * st;
+#pragma unroll
+    for (int u = 0; u < ZK; ++u) buf[u] = (FULL || k0 + u < nz) ? src[(size_t)u * st] : 0.f;
+  };
+
+  float cur[ZK], nxt[ZK];
+  if (nfull > 0) load(0, cur, std::true_type{});
+  else load(0, cur, std::false_type{});
+  float cp = 0.f, dp = 0.f;
+  for (int c = 0; c < nch; ++c) {
+    const int k0 = c * ZK;
+    if (c + 1 < nfull) load(k0 + ZK, nxt, std::true_type{});
+    else if (c + 1 < nch) load(k0 + ZK, nxt, std::false_type{});
+    if (c < nfull) eliminate(k0, cur, cp, dp, nullptr, nullptr, std::true_type{});
+    else eliminate(k0, cur, cp, dp, nullptr, nullptr, std::false_type{});
     ck[(size_t)c * ncol + colc] = make_float2(cp, dp);
 #pragma unroll
     for (int u = 0; u < ZK; ++u) cur[u] = nxt[u];
   }
   // backward: chunks from the top; prefetch the chunk below
-  {
-    const int k0 = (nch - 1) * ZK;
-#pragma unroll
-    for (int u = 0; u < ZK; ++u) {
-      const int k = k0 + u;
-      cur[u] = (k < nz) ? d[(size_t)k * st] : 0.f;
-    }
-  }
+  if (nch - 1 < nfull) load((nch - 1) * ZK, cur, std::true_type{});
+  else load((nch - 1) * ZK, cur, std::false_type{});
   float x = 0.f;
   for (int c = nch - 1; c >= 0; --c) {
     const int k0 = c * ZK;
-    if (c > 0) {
-#pragma unroll
-      for (int u = 0; u < ZK; ++u) nxt[u] = d[(size_t)(k0 - ZK + u) * st];
-    }
-    float2 prev = (c > 0) ? ck[(size_t)(c - 1) * ncol + colc] : make_float2(0.f, 0.f);
+    if (c > 0) load(k0 - ZK, nxt, std::true_type{});  // every chunk below the last is full
+    const float2 prev = (c > 0) ? ck[(size_t)(c - 1) * ncol + colc] : make_float2(0.f, 0.f);
     float cpa[ZK], dpa[ZK];
     cp = prev.x;
     dp = prev.y;
-#pragma unroll
-    for (int u = 0; u < ZK; ++u) {
-      const int k = k0 + u;
-      if (k < nz) {
-        const float ak = (k > 0) ? za[k] : 0.f;
-        const float ckk = (k < nz - 1) ? zc[k] : 0.f;
-        const float mk = __fdividef(1.f, zb[k] + lam - ak * cp);
-        cp = ckk * mk;
-        dp = (cur[u] - ak * dp) * mk;
-      }
-      cpa[u] = cp;
-      dpa[u] = dp;
-    }
+    if (c < nfull) eliminate(k0, cur, cp, dp, cpa, dpa, std::true_type{});
+    else eliminate(k0, cur, cp, dp, cpa, dpa, std::false_type{});
+    float* dst = d + (size_t)k0 * st;
 #pragma unroll
     for (int u = ZK - 1; u >= 0; --u) {
       const int k = k0 + u;
-      if (k < nz) {
+      if (c < nfull || k < nz) {
         x = dpa[u] - ((k < nz - 1) ? cpa[u] : 0.f) * x;
-        if (act) d[(size_t)k * st] = x;
+        if (act) dst[(size_t)u * st] = x;
       }
     }
 #pragma unroll
@@ -126,7 +135,20 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
 
 cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st) {
   const int ncol = a.nx * a.ny;
-  zsolve_ckpt_kernel<<<(ncol + ZB - 1) / ZB, ZB, 0, st>>>(a);
+  const int grid = (ncol + ZB - 1) / ZB;
+  if (a.nz <= ZTAB_MAX) {
+    const size_t smem = (size_t)a.nz * sizeof(float4);
+    static size_t smem_set = 0;
+    if (smem > smem_set) {
+      cudaError_t e = cudaFuncSetAttribute(zsolve_ckpt_kernel<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZTAB_MAX * 16);
+      if (e != cudaSuccess) return e;
+      smem_set = (size_t)ZTAB_MAX * 16;
+    }
+    zsolve_ckpt_kernel<true><<<grid, ZB, smem, st>>>(a);
+  } else {
+    zsolve_ckpt_kernel<false><<<grid, ZB, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
