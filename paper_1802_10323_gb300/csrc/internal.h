@@ -54,6 +54,11 @@ struct ZArgs {
   int periodic;
   int singular;             // column (0,0) is singular: handled by the fix-up kernel
   const int* skip;
+  // FP32 path, non-periodic z: the columns q_x < lowx, q_y < lowy (the worst-conditioned,
+  // see tridiag.cu) are solved in FP64 by extra CTAs of the same launch (0: none).
+  int lowx, lowy;
+  const double *lamx64, *lamy64, *za64, *zb64, *zc64, *dzf64;
+  double* scr64;            // 2·nz·lowx·lowy doubles
 };
 
 template <class T>

@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include <type_traits>
@@ -137,6 +139,7 @@ struct ps_plan {
   float2 *zlo, *zhi;
   double wsum;  // Σ Δz^f (the per-plane weights of the singular mean, times nx·ny)
   double anorm; // an upper bound of ‖A‖∞ (the drift bound of the incremental residual)
+  int lowx, lowy;  // FP32 non-periodic z: rectangle of columns solved in FP64 (tridiag.cu)
   df idx2, idy2;
   void* dev;    // one allocation for all of the above
   int resid_blocks;     // CTAs of a residual pass (max over the two shapes: partials size)
@@ -162,7 +165,7 @@ ps_status cuda_fail(ps_plan* p, cudaError_t e, const char* where) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t ctrl, partial, info, w, rh, rl, scr_c, scr_u, total;
+  size_t ctrl, partial, info, w, rh, rl, scr_c, scr_u, zlow, total;
 };
 
 WsLayout ws_layout(const ps_plan* p) {
@@ -189,6 +192,8 @@ WsLayout ws_layout(const ps_plan* p) {
   off += align256(p->N * tz);
   L.scr_u = off;
   if (p->periodic_z) off += align256(p->N * tz);
+  L.zlow = off;
+  off += align256((size_t)2 * p->nz * p->lowx * p->lowy * sizeof(double));
   L.total = off;
   return L;
 }
@@ -238,6 +243,17 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
   a.periodic = p->periodic_z;
   a.singular = p->singular;
   a.skip = skip;
+  if constexpr (sizeof(T) == 4) {
+    a.lowx = p->lowx;
+    a.lowy = p->lowy;
+    a.lamx64 = p->ax.lam64;
+    a.lamy64 = p->ay.lam64;
+    a.za64 = p->za64;
+    a.zb64 = p->zb64;
+    a.zc64 = p->zc64;
+    a.dzf64 = p->dzf64;
+    a.scr64 = reinterpret_cast<double*>(w + L.zlow);
+  }
   return a;
 }
 
@@ -336,7 +352,8 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
          return launch_zsolve<T>(za, st);
        })) != cudaSuccess)
     return cuda_fail(pl, e, "z solve");
-  if (pl->singular && (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
+  if (pl->singular && !(sizeof(T) == 4 && !pl->periodic_z && pl->lowx > 0) &&
+      (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z singular column");
   if ((e = run(pl, K_YB, st, [&] { return line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "y backward");
@@ -377,7 +394,8 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
            return pl->periodic_z ? launch_zsolve<float>(zw, st) : launch_zsolve_ckpt(zw, st);
          })) != cudaSuccess)
       return r;
-    if (pl->singular && (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
+    if (pl->singular && (pl->periodic_z || pl->lowx == 0) &&
+        (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
     if ((r = run(pl, K_YB, st, [&] { return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
     return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] {
       return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, first ? 0 : 1, skip, st,
@@ -600,6 +618,28 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
   }
   p->dev = dev;
   size_t off = 0;
+  {
+    // FP32 paths with a non-periodic z: columns whose z system has κ ≈ ‖T_z‖/|λ| > 10^4
+    // are solved in FP64 (tridiag.cu). λ grows with q along each axis, so they lie in
+    // the rectangle q_x < lowx, q_y < lowy; at most 1/8 of the columns.
+    p->lowx = p->lowy = 0;
+    if (prec != PS_FP64 && bcz != PS_BC_PERIODIC) {
+      double zmax = 0.0;
+      for (int k = 0; k < nz; ++k)
+        zmax = std::max(zmax, std::fabs(za[k]) + std::fabs(zb[k]) + std::fabs(zc[k]));
+      const double thr = zmax / 1e4;
+      const std::vector<double> lx = eig_scaled(bcx, nx, dx), ly = eig_scaled(bcy, ny, dy);
+      int qx = 0, qy = 0;
+      while (qx < nx && std::fabs(lx[qx]) < thr) ++qx;
+      while (qy < ny && std::fabs(ly[qy]) < thr) ++qy;
+      while ((size_t)qx * qy * 8 > (size_t)nx * ny && qy > 1) --qy;
+      while ((size_t)qx * qy * 8 > (size_t)nx * ny && qx > 1) --qx;
+      if ((size_t)qx * qy * 8 <= (size_t)nx * ny && qx > 0 && qy > 0) {
+        p->lowx = qx;
+        p->lowy = qy;
+      }
+    }
+  }
   auto take = [&](size_t nbytes) { char* q = dev + off; off += align256(nbytes); return q; };
   std::vector<char> host(bytes, 0);
   auto hput = [&](void* devp, const void* src, size_t nbytes) {

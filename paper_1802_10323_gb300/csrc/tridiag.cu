@@ -38,9 +38,63 @@ constexpr int ZK = 16;
 constexpr int ZB = 128;            // columns (threads) per CTA
 constexpr int ZTAB_MAX = 4096;     // planes whose coefficient table fits in shared memory
 
+// The FP32 elimination of a column with a small |λ| (low wavenumbers) errs by about
+// ε_32·κ, κ ≈ ‖T_z‖/|λ| up to ~10^7 on the stretched channel grid, and that error
+// is smooth in z with a large amplitude: exactly what an FP32 correction solve
+// removes worst (its own transform rounding, amplified by ‖A‖, scales with the
+// correction's size). Those few columns — a rectangle q_x < lowx, q_y < lowy chosen
+// at plan creation from κ — are solved here in FP64 (Thomas with c' and d' in FP64
+// scratch; the singular column (0,0) with its weighted-mean pinning), by CTAs of
+// the same launch as the FP32 columns, so they overlap them. Output rounded to FP32.
+__device__ void zlow_column(const ZArgs<float>& a, int t) {
+  const int nrect = a.lowx * a.lowy;
+  if (t >= nrect) return;
+  const int i = t % a.lowx, j = t / a.lowx;
+  const int col = j * a.nx + i;
+  const size_t st = (size_t)a.nx * a.ny;
+  const int nz = a.nz;
+  float* d = a.data + col;
+  double* cs = a.scr64 + t;                       // [k][nrect]
+  double* ds = a.scr64 + (size_t)nz * nrect + t;  // [k][nrect]
+  const bool sing = a.singular && col == 0;
+  const double lam = a.lamx64[i] + a.lamy64[j];
+  double mean = 0.0, wsum = 0.0;
+  if (sing) {  // remove the Δz^f-weighted mean of the right-hand side; Φ̂_0 = 0 pinned
+    for (int k = 0; k < nz; ++k) {
+      mean += a.dzf64[k] * (double)d[k * st];
+      wsum += a.dzf64[k];
+    }
+    mean /= wsum;
+  }
+  const int kb = sing ? 1 : 0;
+  double cp = 0.0, dp = 0.0;
+  for (int k = kb; k < nz; ++k) {
+    const double ak = (k > kb) ? a.za64[k] : 0.0;
+    const double ck = (k < nz - 1) ? a.zc64[k] : 0.0;
+    const double mk = 1.0 / (a.zb64[k] + (sing ? 0.0 : lam) - ak * cp);
+    cp = ck * mk;
+    dp = (((double)d[k * st] - mean) - ak * dp) * mk;
+    cs[(size_t)k * nrect] = cp;
+    ds[(size_t)k * nrect] = dp;
+  }
+  double x = 0.0, xs = 0.0;
+  for (int k = nz - 1; k >= kb; --k) {
+    x = ds[(size_t)k * nrect] - ((k < nz - 1) ? cs[(size_t)k * nrect] : 0.0) * x;
+    ds[(size_t)k * nrect] = x;
+    if (sing) xs += a.dzf64[k] * x;
+  }
+  const double mx = sing ? xs / wsum : 0.0;  // the singular column keeps zero weighted mean
+  if (sing) d[0] = (float)(-mx);
+  for (int k = kb; k < nz; ++k) d[k * st] = (float)(ds[(size_t)k * nrect] - mx);
+}
+
 template <bool TAB>
-__global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
+__global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlowb) {
   if (a.skip && *a.skip) return;
+  if ((int)blockIdx.x < nlowb) {  // FP64 rectangle of low wavenumbers
+    zlow_column(a, blockIdx.x * ZB + threadIdx.x);
+    return;
+  }
   extern __shared__ float4 ztab[];  // [nz] (a_k, b_k, c_k, ·) when TAB
   const int nz = a.nz;
   auto coef = [&](int k) -> float4 {
@@ -57,10 +111,10 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
   }
   const int ncol = a.nx * a.ny;
   float2* __restrict__ ck = reinterpret_cast<float2*>(a.scr_c);  // [nchunk][ncol]
-  const int col = blockIdx.x * ZB + threadIdx.x;
-  const bool act = col < ncol && !(a.singular && col == 0);
+  const int col = (blockIdx.x - nlowb) * ZB + threadIdx.x;
   const int colc = col < ncol ? col : ncol - 1;
   const int i = colc % a.nx, j = colc / a.nx;
+  const bool act = col < ncol && !(a.singular && col == 0) && !(i < a.lowx && j < a.lowy);
   const float lam = a.lamx[i] + a.lamy[j];
   const size_t st = (size_t)ncol;
   const int nch = (nz + ZK - 1) / ZK, nfull = nz / ZK;
@@ -135,7 +189,8 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a) {
 
 cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st) {
   const int ncol = a.nx * a.ny;
-  const int grid = (ncol + ZB - 1) / ZB;
+  const int nlowb = (a.lowx * a.lowy + ZB - 1) / ZB;  // FP64 CTAs first (they run longest)
+  const int grid = nlowb + (ncol + ZB - 1) / ZB;
   if (a.nz <= ZTAB_MAX) {
     const size_t smem = (size_t)a.nz * sizeof(float4);
     static size_t smem_set = 0;
@@ -145,9 +200,9 @@ cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st) {
       if (e != cudaSuccess) return e;
       smem_set = (size_t)ZTAB_MAX * 16;
     }
-    zsolve_ckpt_kernel<true><<<grid, ZB, smem, st>>>(a);
+    zsolve_ckpt_kernel<true><<<grid, ZB, smem, st>>>(a, nlowb);
   } else {
-    zsolve_ckpt_kernel<false><<<grid, ZB, 0, st>>>(a);
+    zsolve_ckpt_kernel<false><<<grid, ZB, 0, st>>>(a, nlowb);
   }
   return cudaGetLastError();
 }
