@@ -46,6 +46,8 @@ constexpr int ZTAB_MAX = 4096;     // planes whose coefficient table fits in sha
 // at plan creation from κ — are solved here in FP64 (Thomas with c' and d' in FP64
 // scratch; the singular column (0,0) with its weighted-mean pinning), by CTAs of
 // the same launch as the FP32 columns, so they overlap them. Output rounded to FP32.
+constexpr int ZL = 4;  // rows in flight per FP64 column (keeps the kernel's registers at the FP32 path's)
+
 __device__ void zlow_column(const ZArgs<float>& a, int t) {
   const int nrect = a.lowx * a.lowy;
   if (t >= nrect) return;
@@ -67,32 +69,84 @@ __device__ void zlow_column(const ZArgs<float>& a, int t) {
     mean /= wsum;
   }
   const int kb = sing ? 1 : 0;
+  // forward sweep over chunks of ZL rows, the next chunk's right-hand side in flight
+  float cur[ZL], nxt[ZL];
+  auto load = [&](int k0, float* buf) {
+#pragma unroll
+    for (int u = 0; u < ZL; ++u) buf[u] = (k0 + u < nz) ? d[(size_t)(k0 + u) * st] : 0.f;
+  };
+  load(0, cur);
   double cp = 0.0, dp = 0.0;
-  for (int k = kb; k < nz; ++k) {
-    const double ak = (k > kb) ? a.za64[k] : 0.0;
-    const double ck = (k < nz - 1) ? a.zc64[k] : 0.0;
-    const double mk = 1.0 / (a.zb64[k] + (sing ? 0.0 : lam) - ak * cp);
-    cp = ck * mk;
-    dp = (((double)d[k * st] - mean) - ak * dp) * mk;
-    cs[(size_t)k * nrect] = cp;
-    ds[(size_t)k * nrect] = dp;
+  for (int k0 = 0; k0 < nz; k0 += ZL) {
+    if (k0 + ZL < nz) load(k0 + ZL, nxt);
+#pragma unroll
+    for (int u = 0; u < ZL; ++u) {
+      const int k = k0 + u;
+      if (k >= kb && k < nz) {
+        const double ak = (k > kb) ? __ldg(a.za64 + k) : 0.0;
+        const double ck = (k < nz - 1) ? __ldg(a.zc64 + k) : 0.0;
+        const double mk = 1.0 / (__ldg(a.zb64 + k) + (sing ? 0.0 : lam) - ak * cp);
+        cp = ck * mk;
+        dp = (((double)cur[u] - mean) - ak * dp) * mk;
+        cs[(size_t)k * nrect] = cp;
+        ds[(size_t)k * nrect] = dp;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < ZL; ++u) cur[u] = nxt[u];
   }
+  // backward sweep, chunks of (c', d') from the top with the chunk below in flight
+  double cb[ZL], db[ZL], cn[ZL], dn[ZL];
+  const int klast = ((nz - 1) / ZL) * ZL;
+  auto loadb = [&](int k0, double* c_, double* d_) {
+#pragma unroll
+    for (int u = 0; u < ZL; ++u) {
+      const int k = k0 + u;
+      c_[u] = (k < nz) ? cs[(size_t)k * nrect] : 0.0;
+      d_[u] = (k < nz) ? ds[(size_t)k * nrect] : 0.0;
+    }
+  };
+  loadb(klast, cb, db);
   double x = 0.0, xs = 0.0;
-  for (int k = nz - 1; k >= kb; --k) {
-    x = ds[(size_t)k * nrect] - ((k < nz - 1) ? cs[(size_t)k * nrect] : 0.0) * x;
-    ds[(size_t)k * nrect] = x;
-    if (sing) xs += a.dzf64[k] * x;
+  for (int k0 = klast; k0 >= 0; k0 -= ZL) {
+    if (k0 > 0) loadb(k0 - ZL, cn, dn);
+#pragma unroll
+    for (int u = ZL - 1; u >= 0; --u) {
+      const int k = k0 + u;
+      if (k >= kb && k < nz) {
+        x = db[u] - ((k < nz - 1) ? cb[u] : 0.0) * x;
+        db[u] = x;
+        if (sing) xs += a.dzf64[k] * x;
+      }
+    }
+    if (!sing) {
+#pragma unroll
+      for (int u = 0; u < ZL; ++u)
+        if (k0 + u < nz) d[(size_t)(k0 + u) * st] = (float)db[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < ZL; ++u)
+        if (k0 + u >= kb && k0 + u < nz) ds[(size_t)(k0 + u) * nrect] = db[u];
+    }
+#pragma unroll
+    for (int u = 0; u < ZL; ++u) {
+      cb[u] = cn[u];
+      db[u] = dn[u];
+    }
   }
-  const double mx = sing ? xs / wsum : 0.0;  // the singular column keeps zero weighted mean
-  if (sing) d[0] = (float)(-mx);
-  for (int k = kb; k < nz; ++k) d[k * st] = (float)(ds[(size_t)k * nrect] - mx);
+  if (sing) {  // the singular column keeps zero weighted mean
+    const double mx = xs / wsum;
+    d[0] = (float)(-mx);
+    for (int k = 1; k < nz; ++k) d[(size_t)k * st] = (float)(ds[(size_t)k * nrect] - mx);
+  }
 }
 
 template <bool TAB>
 __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlowb) {
   if (a.skip && *a.skip) return;
-  if ((int)blockIdx.x < nlowb) {  // FP64 rectangle of low wavenumbers
-    zlow_column(a, blockIdx.x * ZB + threadIdx.x);
+  if ((int)blockIdx.x < nlowb) {  // FP64 rectangle of low wavenumbers: one warp per CTA,
+    // so that the FP64 work (2 ops per clock per SM) spreads over many SMs
+    if (threadIdx.x < 32) zlow_column(a, blockIdx.x * 32 + threadIdx.x);
     return;
   }
   extern __shared__ float4 ztab[];  // [nz] (a_k, b_k, c_k, ·) when TAB
@@ -189,7 +243,7 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlo
 
 cudaError_t launch_zsolve_ckpt(ZArgs<float> a, cudaStream_t st) {
   const int ncol = a.nx * a.ny;
-  const int nlowb = (a.lowx * a.lowy + ZB - 1) / ZB;  // FP64 CTAs first (they run longest)
+  const int nlowb = (a.lowx * a.lowy + 31) / 32;  // FP64 CTAs first (they run longest)
   const int grid = nlowb + (ncol + ZB - 1) / ZB;
   if (a.nz <= ZTAB_MAX) {
     const size_t smem = (size_t)a.nz * sizeof(float4);
