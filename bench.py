@@ -45,8 +45,11 @@ BYTES_PER_POINT = {
     # the FP32 values for the next residual pass; residual pass 0 reads f (FP64)
     # and Φ_0 (FP32), later passes r = rh + rl and the correction, and both write
     # rh + rl (the check pass writes nothing); the exact pass reads p and f.
+    # The first x backward keeps only the FP32 Φ_0; the first correction writes
+    # p = Φ_0 + e (and e in FP32), later ones add into p.
     "refine": {"x_fwd_f64in": 8 + 4, "x_fwd": 4 + 4, "y_fwd": 4 + 4, "z_solve": 4 + 4,
-               "y_bwd": 4 + 4, "x_bwd_f64store": 4 + 8 + 4, "x_bwd_f64acc": 4 + 8 + 8 + 4,
+               "y_bwd": 4 + 4, "x_bwd_f64store": 4 + 4, "x_bwd_f64base": 4 + 4 + 8 + 4,
+               "x_bwd_f64acc": 4 + 8 + 8 + 4, "materialize": 4 + 8,
                "residual_first": 8 + 4 + 8, "residual_first3": 8 + 4 + 8, "residual": 8 + 4 + 8,
                "residual_check": 8 + 4, "residual_exact": 8 + 8 + 4},
     "fp64": {"x_fwd": 16, "y_fwd": 16, "z_solve": 16, "y_bwd": 16, "x_bwd": 16},

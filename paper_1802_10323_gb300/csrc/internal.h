@@ -33,6 +33,7 @@ struct XformArgs {
   const int* skip;          // if non-null and *skip != 0 the kernel returns at once
   unsigned long long* amax; // FP64 output: atomicMax of |transform output| bit patterns, or null
   float* out2;              // FP64 output: also store the FP32 transform output here, or null
+  const float* base32;      // FP64 output: out = widen(base32) + v instead of (out +) v, or null
 };
 
 template <class T, class TI, class TO, bool FWD>
@@ -114,12 +115,14 @@ struct Ctrl {
   unsigned long long dmax;  // bit pattern of max|e| of the last correction
   double bnd;               // accumulated drift bound of the incremental residual
   int skip_redo;            // 0: pass 0 is repeated with the three-level split
-  int pad1;
+  int nomat0;               // 0: the loop ended at pass 0, p is written from Φ_0
 };
 
 cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
                             int singular, double rtol, int iteration, int attempt, int last,
                             double anorm, const int* skip, ps_info* info, cudaStream_t st);
+// p = Φ_0 (widened exactly) unless *skip.
+cudaError_t launch_widen(const float* u, double* p, size_t n, const int* skip, cudaStream_t st);
 cudaError_t launch_finalize_exact(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
                                   int singular, double rtol, ps_info* info, cudaStream_t st);
 cudaError_t launch_info_plain(ps_info* info, cudaStream_t st);

@@ -108,11 +108,12 @@ void split_df(double d, float2* out) {
 // per grid point (the FP32 refinement path has separate kinds for its FP64-input
 // x pass, its storing and accumulating x passes and its check-only residual).
 enum Kind { K_XF = 0, K_XF64IN, K_YF, K_Z, K_ZS, K_YB, K_XB, K_XB64ST, K_XB64ACC, K_RES, K_CHK,
-            K_CTL, K_VER, K_RES0, K_RES3, K_NKINDS };
+            K_CTL, K_VER, K_RES0, K_RES3, K_XB64BASE, K_MAT, K_NKINDS };
 static const char* kKindName[K_NKINDS] = {"x_fwd", "x_fwd_f64in", "y_fwd", "z_solve",
                                           "z_singular", "y_bwd", "x_bwd", "x_bwd_f64store",
                                           "x_bwd_f64acc", "residual", "residual_check", "control",
-                                          "residual_exact", "residual_first", "residual_first3"};
+                                          "residual_exact", "residual_first", "residual_first3",
+                                          "x_bwd_f64base", "materialize"};
 constexpr int kProfMax = 4096;
 
 struct Prof {
@@ -165,7 +166,7 @@ ps_status cuda_fail(ps_plan* p, cudaError_t e, const char* where) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t ctrl, partial, info, w, rh, rl, scr_c, scr_u, zlow, total;
+  size_t ctrl, partial, info, w, rh, rl, u0, scr_c, scr_u, zlow, total;
 };
 
 WsLayout ws_layout(const ps_plan* p) {
@@ -186,6 +187,8 @@ WsLayout ws_layout(const ps_plan* p) {
     L.rh = off;  // the residual r = rh + rl of the refinement (double-float)
     off += align256(p->N * sizeof(float));
     L.rl = off;
+    off += align256(p->N * sizeof(float));
+    L.u0 = off;  // Φ_0, the FP32 solve (operand of residual pass 0, base of the first correction)
     off += align256(p->N * sizeof(float));
   }
   L.scr_c = off;
@@ -262,7 +265,8 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
 template <class T, class TI, class TO, bool FWD>
 cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, const T* scale,
                        int accumulate, const int* skip, cudaStream_t st,
-                       unsigned long long* amax = nullptr, float* out2 = nullptr) {
+                       unsigned long long* amax = nullptr, float* out2 = nullptr,
+                       const float* base32 = nullptr) {
   const AxisTab& t = axis == 0 ? p->ax : p->ay;
   const int lpc_y = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
   const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) &&
@@ -284,8 +288,9 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
     a.skip = skip;
     a.amax = amax;
     a.out2 = out2;
+    a.base32 = base32;
     if (axis == 1 && std::is_same<TI, T>::value && std::is_same<TO, T>::value && p->nx % 16 == 0 &&
-        !accumulate && !amax && !out2) {
+        !accumulate && !amax && !out2 && !base32) {
       switch (t.m) {
         case 64: return launch_xform_col<T, 64, FWD>(a, st);
         case 128: return launch_xform_col<T, 128, FWD>(a, st);
@@ -311,6 +316,7 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
   XformArgs<T> ga = xargs<T>(p, axis, in, out, scale, accumulate, skip);
   ga.amax = amax;
   ga.out2 = out2;
+  ga.base32 = base32;
   return launch_xform<T, TI, TO, FWD>(ga, st);
 }
 
@@ -377,12 +383,15 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   if ((e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return cuda_fail(pl, e, "reset");
   float* rh = reinterpret_cast<float*>(wb + L.rh);
   float* rl = reinterpret_cast<float*>(wb + L.rl);
+  float* u0 = reinterpret_cast<float*>(wb + L.u0);
   const ZArgs<float> zw = zargs<float>(pl, w, ws, L, skip);
-  // One FP32 solve of w (the right-hand side in, in place); the first reads f, later
-  // ones r = rh. The x backward stores Φ_0 (first) or adds e (later) into the FP64 p
-  // and keeps the FP32 values in w, the operand of the next residual pass, with
-  // max|Φ_0| or max|e| in ctrl.
-  auto correction = [&](bool first) -> cudaError_t {
+  // One FP32 solve (c = 0: of f; c ≥ 1: of r = rh, the c-th correction) through w.
+  // The x backward writes Φ_0 to u0 only (c = 0; the FP64 p is written by the first
+  // correction as Φ_0 + e, or from Φ_0 alone if the loop ends at pass 0), then
+  // p = Φ_0 + e (c = 1) or p += e (c ≥ 2), keeping e in w for the next residual
+  // pass; max|Φ_0| or max|e| go to ctrl.
+  auto correction = [&](int c) -> cudaError_t {
+    const bool first = (c == 0);
     cudaError_t r;
     if (first)
       r = run(pl, K_XF64IN, st, [&] { return line_xform<float, double, float, true>(pl, 0, f, w, nullptr, 0, skip, st); });
@@ -397,15 +406,18 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
     if (pl->singular && (pl->periodic_z || pl->lowx == 0) &&
         (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
     if ((r = run(pl, K_YB, st, [&] { return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
-    return run(pl, first ? K_XB64ST : K_XB64ACC, st, [&] {
-      return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, first ? 0 : 1, skip, st,
-                                                     first ? &ctrl->pmax : &ctrl->dmax, w);
+    if (first)
+      return run(pl, K_XB64ST, st, [&] {
+        return line_xform<float, float, double, false>(pl, 0, w, nullptr, nullptr, 0, skip, st, &ctrl->pmax, u0);
+      });
+    return run(pl, c == 1 ? K_XB64BASE : K_XB64ACC, st, [&] {
+      return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, c == 1 ? 0 : 1, skip, st, &ctrl->dmax,
+                                                     w, c == 1 ? u0 : nullptr);
     });
   };
   ResidArgs ra{};
   ra.p = p;
   ra.f = f;
-  ra.u = w;
   ra.rh_in = rh;
   ra.rl_in = rl;
   ra.nx = pl->nx;
@@ -426,12 +438,13 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   ra.nblocks = pl->resid_blocks;  // (informational; each launch sizes its own grid)
   ra.skip = skip;
   const double wsum_total = pl->wsum * pl->nx * pl->ny;
-  if ((e = correction(true)) != cudaSuccess) return cuda_fail(pl, e, "initial solve");
+  if ((e = correction(0)) != cudaSuccess) return cuda_fail(pl, e, "initial solve");
   for (int it = 0; it <= pl->max_iter; ++it) {
     const bool last = (it == pl->max_iter);
     ra.rh_out = last ? nullptr : rh;  // the last pass only checks
     ra.rl_out = last ? nullptr : rl;
     ra.pmax_bits = it == 0 ? &ctrl->pmax : &ctrl->dmax;
+    ra.u = it == 0 ? u0 : w;
     ra.skip = skip;
     if ((e = run(pl, last ? K_CHK : (it == 0 ? K_RES0 : K_RES), st,
                  [&] { return launch_residual_inc(ra, it, 0, st); })) != cudaSuccess)
@@ -452,8 +465,11 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
                                     pl->rtol, 0, 1, last ? 1 : 0, pl->anorm, &ctrl->skip_redo, info, st);
            })) != cudaSuccess)
         return cuda_fail(pl, e, "finalize");
+      // the loop ended at pass 0 (converged or max_iter = 0): p = Φ_0
+      if ((e = run(pl, K_MAT, st, [&] { return launch_widen(u0, p, pl->N, &ctrl->nomat0, st); })) != cudaSuccess)
+        return cuda_fail(pl, e, "store");
     }
-    if (!last && (e = correction(false)) != cudaSuccess) return cuda_fail(pl, e, "correction");
+    if (!last && (e = correction(it + 1)) != cudaSuccess) return cuda_fail(pl, e, "correction");
   }
   // Exact confirmation from the stored p, only when the drift bound of the
   // incremental passes was not small (both kernels return at once otherwise).

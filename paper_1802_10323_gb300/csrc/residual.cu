@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
   if (iteration == 0 && attempt == 0) {
     const bool redo = ldexp(anorm * bits_f64(c->pmax), -43) > 0.05 * rtol * fn;
     c->skip_redo = redo ? 0 : 1;
+    c->nomat0 = 1;
     if (redo) return;
   }
   c->rnorm = rn;
@@ -638,6 +639,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
   const bool ok = rel <= rtol;
   if (ok) c->converged = 1;
   if (ok || last) c->vskip = (c->bnd <= 0.05 * rtol * fn) ? 1 : 0;
+  if (iteration == 0) c->nomat0 = (ok || last) ? 0 : 1;
   if (info && (ok || last)) {
     info->status = ok ? PS_OK : PS_NOT_CONVERGED;
     info->iterations = iteration;
@@ -685,6 +687,17 @@ cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, doubl
 cudaError_t launch_finalize_exact(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,
                                   int singular, double rtol, ps_info* info, cudaStream_t st) {
   finalize_exact_kernel<<<1, 1024, 0, st>>>(ctrl, partial, nblocks, wsum_total, singular, rtol, info);
+  return cudaGetLastError();
+}
+
+__global__ void widen_kernel(const float* __restrict__ u, double* __restrict__ p, size_t n, const int* skip) {
+  if (*skip) return;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < n; g += (size_t)gridDim.x * blockDim.x)
+    p[g] = widen_f32(u[g]);
+}
+
+cudaError_t launch_widen(const float* u, double* p, size_t n, const int* skip, cudaStream_t st) {
+  widen_kernel<<<152 * 8, 256, 0, st>>>(u, p, n, skip);
   return cudaGetLastError();
 }
 

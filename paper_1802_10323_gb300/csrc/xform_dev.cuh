@@ -339,11 +339,20 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
     T v = rO[l * ldr + e];
     if (!FWD && a.plane_scale) v *= a.plane_scale[z];
     const TO x = st_cvt<TO, T>::f(v);
-    out[g] = a.accumulate ? out[g] + x : x;
     if constexpr (sizeof(TO) == 8) {
+      if (out) {
+        if constexpr (sizeof(T) == 4) {
+          if (a.base32) out[g] = widen_f32(a.base32[g]) + x;
+          else out[g] = a.accumulate ? out[g] + x : x;
+        } else {
+          out[g] = a.accumulate ? out[g] + x : x;
+        }
+      }
       amax = max(amax, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
       if constexpr (sizeof(T) == 4)
         if (a.out2) a.out2[g] = v;
+    } else {
+      out[g] = a.accumulate ? out[g] + x : x;
     }
   }
   if constexpr (sizeof(TO) == 8) {

@@ -153,6 +153,7 @@ struct FastArgs {
   unsigned long long* amax;  // FP64 output: atomicMax of |transform output| bit patterns, or null
   int lpc;              // lines per CTA
   float* out2;          // FP64 output (x lines): also store the FP32 transform output here, or null
+  const float* base32;  // FP64 output (x lines): out = widen(base32) + v instead of (out +) v, or null
 };
 
 template <class T, class TI, class TO, int M, bool FWD>

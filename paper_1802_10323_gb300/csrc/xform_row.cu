@@ -36,8 +36,14 @@ constexpr int WARPS = 8;  // warps per CTA
 template <class TC, class TI>
 __device__ __forceinline__ TC in_cvt(TI x) { return ld_cvt<TC, TI>::f(x); }
 
-template <class T, class TI, class TO, int M, bool FWD>
-__global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? 3 : 4) : 2) xform_row_kernel(FastArgs<T> a) {
+// Output modes of the backward transform (compile-time, so that no mode pays for
+// another's registers): store; accumulate (out += v); base (out = widen(base32) + v);
+// none (no FP64 output: only the FP32 copy and the max).
+enum { OM_STORE = 0, OM_ACC = 1, OM_BASE = 2, OM_NONE = 3 };
+
+template <class T, class TI, class TO, int M, bool FWD, int OM>
+__global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? (OM == OM_NONE ? 2 : 3) : 4) : 2)
+    xform_row_kernel(FastArgs<T> a) {
   if (a.skip && *a.skip) return;
   using S = Shape<M>;
   constexpr int N = 2 * M, E = S::E, TPL = S::TPL, LPW = 32 / TPL;
@@ -276,20 +282,27 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? 3 : 4
       // (the line's own input array: every input of the line is already in registers)
       auto put = [&](int i0, const T* val, auto n_tag) {
         constexpr int NV = decltype(n_tag)::value;
+        constexpr bool F64OUT = sizeof(TO) == 8 && sizeof(T) == 4;
         vec<TO, NV> o;
         vec<T, NV> o2;
-        if (a.accumulate) o = *reinterpret_cast<const vec<TO, NV>*>(dst + i0);
+        if constexpr (OM == OM_ACC) o = *reinterpret_cast<const vec<TO, NV>*>(dst + i0);
+        if constexpr (F64OUT && OM == OM_BASE) {
+          const vec<float, NV> b32 = *reinterpret_cast<const vec<float, NV>*>(a.base32 + base + i0);
+#pragma unroll
+          for (int u = 0; u < NV; ++u) o.v[u] = widen_f32(b32.v[u]);
+        }
 #pragma unroll
         for (int u = 0; u < NV; ++u) {
           o2.v[u] = val[u] * s;
           const TO x = st_cvt<TO, T>::f(o2.v[u]);
-          o.v[u] = a.accumulate ? o.v[u] + x : x;
+          if constexpr (OM == OM_ACC || (F64OUT && OM == OM_BASE)) o.v[u] = o.v[u] + x;
+          else o.v[u] = x;
           if constexpr (sizeof(TO) == 8)
             if (live) amax = max(amax, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
         }
         if (live) {
-          *reinterpret_cast<vec<TO, NV>*>(dst + i0) = o;
-          if constexpr (sizeof(TO) == 8 && sizeof(T) == 4)
+          if constexpr (OM != OM_NONE) *reinterpret_cast<vec<TO, NV>*>(dst + i0) = o;
+          if constexpr (F64OUT)
             if (a.out2) *reinterpret_cast<vec<T, NV>*>(a.out2 + base + i0) = o2;
         }
       };
@@ -348,13 +361,13 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? 3 : 4
 
 }  // namespace row
 
-template <class T, class TI, class TO, int M, bool FWD>
-cudaError_t launch_xform_row(FastArgs<T> a, cudaStream_t st) {
+namespace {
+template <class T, class TI, class TO, int M, bool FWD, int OM>
+cudaError_t launch_row_mode(FastArgs<T> a, cudaStream_t st) {
   using S = fast::Shape<M>;
-  if (a.axis != 0 || a.nx != 2 * M) return cudaErrorInvalidValue;
   constexpr int LPW = 32 / S::TPL;
   constexpr size_t LB = M + M / 8;
-  auto k = row::xform_row_kernel<T, TI, TO, M, FWD>;
+  auto k = row::xform_row_kernel<T, TI, TO, M, FWD, OM>;
   const size_t smem = fast_table_bytes<T, M>(a.bc) + (size_t)row::WARPS * LPW * LB * sizeof(cplx<T>);
   static int smem_set = 0;
   static int blocks_per_sm[2] = {};
@@ -379,6 +392,18 @@ cudaError_t launch_xform_row(FastArgs<T> a, cudaStream_t st) {
   (void)cudaGetLastError();  // a stale error from elsewhere must not be blamed here
   k<<<grid, 32 * row::WARPS, smem, st>>>(a);
   return cudaGetLastError();
+}
+}  // namespace
+
+template <class T, class TI, class TO, int M, bool FWD>
+cudaError_t launch_xform_row(FastArgs<T> a, cudaStream_t st) {
+  if (a.axis != 0 || a.nx != 2 * M) return cudaErrorInvalidValue;
+  if constexpr (!FWD && sizeof(TO) == 8 && sizeof(T) == 4) {
+    if (a.base32) return launch_row_mode<T, TI, TO, M, FWD, row::OM_BASE>(a, st);
+    if (!a.out) return launch_row_mode<T, TI, TO, M, FWD, row::OM_NONE>(a, st);
+  }
+  if (a.accumulate) return launch_row_mode<T, TI, TO, M, FWD, row::OM_ACC>(a, st);
+  return launch_row_mode<T, TI, TO, M, FWD, row::OM_STORE>(a, st);
 }
 
 #define PS_ROW_INST(M)                                                                                   \
