@@ -21,9 +21,7 @@
 namespace ps {
 namespace col {
 
-constexpr int CW = 16;  // x columns per CTA
-
-template <int M>
+template <int M, int CW>  // CW: x columns per CTA (16 or 8)
 struct CShape {
   static constexpr int TPL = (M >= 128) ? 32 : 16;  // threads per column
   static constexpr int E = M / TPL;                 // complex points per thread
@@ -83,10 +81,10 @@ __device__ __forceinline__ void dft(cplx<T>* v) {
 // Stages STAGE… of the M-point FFT of this thread's column. On entry
 // v[q·R + r] = x[b_q + r·M/R] with b_q = b + q·TPL; on return v holds the last
 // stage's outputs, v[q·R + r] at position b_q + r·(M/R_last).
-template <class T, int M, bool INV, int STAGE, int NS>
-__device__ __forceinline__ void fft_col(cplx<T> (&v)[CShape<M>::E], cplx<T>* buf, const cplx<T>* stw,
+template <class T, int M, int CW, bool INV, int STAGE, int NS>
+__device__ __forceinline__ void fft_col(cplx<T> (&v)[CShape<M, CW>::E], cplx<T>* buf, const cplx<T>* stw,
                                         int b, int c) {
-  using S = CShape<M>;
+  using S = CShape<M, CW>;
   constexpr int E = S::E, TPL = S::TPL;
   constexpr int R = S::radix(STAGE);
 #pragma unroll
@@ -120,19 +118,20 @@ __device__ __forceinline__ void fft_col(cplx<T> (&v)[CShape<M>::E], cplx<T>* buf
 #pragma unroll
       for (int r = 0; r < R2; ++r) v[q * R2 + r] = buf[(bq + r * (M / R2)) * CW + c];
     }
-    fft_col<T, M, INV, STAGE + 1, NS * R>(v, buf, stw, b, c);
+    fft_col<T, M, CW, INV, STAGE + 1, NS * R>(v, buf, stw, b, c);
   }
 }
 
-template <class T, int M>
+template <class T, int M, int CW>
 __host__ __device__ constexpr size_t col_smem(int bc) {
   return fast_table_bytes<T, M>(bc) + (size_t)M * CW * sizeof(cplx<T>);
 }
 
-template <class T, int M, bool FWD>
-__global__ void __launch_bounds__(CShape<M>::NT, sizeof(T) == 4 ? 2 : 1) xform_col_kernel(FastArgs<T> a) {
+template <class T, int M, bool FWD, int CW>
+__global__ void __launch_bounds__(CShape<M, CW>::NT, sizeof(T) == 4 ? 1024 / CShape<M, CW>::NT : 1)
+    xform_col_kernel(FastArgs<T> a) {
   if (a.skip && *a.skip) return;
-  using S = CShape<M>;
+  using S = CShape<M, CW>;
   constexpr int N = 2 * M, E = S::E, TPL = S::TPL;
   static_assert(S::radix(0) == E, "the first stage takes all of a thread's points");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(CShape<M>::NT, sizeof(T) == 4 ? 2 : 1) xform_c
         }
         v[r] = cscale(z, s);
       }
-      fft_col<T, M, false, 0, 1>(v, buf, stw, b, c);
+      fft_col<T, M, CW, false, 0, 1>(v, buf, stw, b, c);
       // ---- post-processing: pair k with M − k through the buffer, rows out ----
       __syncthreads();
 #pragma unroll
@@ -312,8 +311,8 @@ __global__ void __launch_bounds__(CShape<M>::NT, sizeof(T) == 4 ? 2 : 1) xform_c
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < E; ++r) v[r] = buf[(b + r * TPL) * CW + c];
-      if (bc == BC_ND) fft_col<T, M, false, 0, 1>(v, buf, stw, b, c);
-      else fft_col<T, M, true, 0, 1>(v, buf, stw, b, c);
+      if (bc == BC_ND) fft_col<T, M, CW, false, 0, 1>(v, buf, stw, b, c);
+      else fft_col<T, M, CW, true, 0, 1>(v, buf, stw, b, c);
       // ---- backward post-processing straight from the last stage to the rows ----
       const T inv_m = (T)1 / (T)M;
 #pragma unroll
@@ -349,18 +348,17 @@ __global__ void __launch_bounds__(CShape<M>::NT, sizeof(T) == 4 ? 2 : 1) xform_c
 
 }  // namespace col
 
-template <class T, int M, bool FWD>
-cudaError_t launch_xform_col(FastArgs<T> a, cudaStream_t st) {
-  using S = col::CShape<M>;
-  if (a.axis != 1 || a.ny != 2 * M || a.nx % col::CW != 0 || a.accumulate || a.amax)
-    return cudaErrorInvalidValue;
-  auto k = col::xform_col_kernel<T, M, FWD>;
-  const size_t smem = col::col_smem<T, M>(a.bc);
+namespace {
+template <class T, int M, bool FWD, int CW>
+cudaError_t launch_col_cw(FastArgs<T> a, cudaStream_t st) {
+  using S = col::CShape<M, CW>;
+  auto k = col::xform_col_kernel<T, M, FWD, CW>;
+  const size_t smem = col::col_smem<T, M, CW>(a.bc);
   static int smem_set = 0;
   static int blocks_per_sm[2] = {};  // [bc != P]
   if (!smem_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)col::col_smem<T, M>(1));
+                                         (int)col::col_smem<T, M, CW>(1));
     if (e != cudaSuccess) return e;
     smem_set = 1;
   }
@@ -373,11 +371,21 @@ cudaError_t launch_xform_col(FastArgs<T> a, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int ntiles = a.nz * (a.nx / col::CW);
+  const int ntiles = a.nz * (a.nx / CW);
   const int grid = ntiles < sms * bps ? ntiles : sms * bps;
   (void)cudaGetLastError();  // a stale error from elsewhere must not be blamed here
   k<<<grid, S::NT, smem, st>>>(a);
   return cudaGetLastError();
+}
+}  // namespace
+
+// Tiles of 16 columns: 64-byte rows in FP32, 128-byte rows in FP64.
+template <class T, int M, bool FWD>
+cudaError_t launch_xform_col(FastArgs<T> a, cudaStream_t st) {
+  constexpr int CW = 16;  // (measured at 1024^3: 8 and 32 columns are slower)
+  if (a.axis != 1 || a.ny != 2 * M || a.nx % CW != 0 || a.accumulate || a.amax)
+    return cudaErrorInvalidValue;
+  return launch_col_cw<T, M, FWD, CW>(a, st);
 }
 
 #define PS_COL_INST(M)                                                                              \
