@@ -170,6 +170,49 @@ def cpu_oracle_rate(nz_sample=None, target_s=15.0):
                       f"threads={cores}"}
 
 
+class Ranks:
+    """The replica world of a multi-GPU run: one process per GPU, each solving its own
+    copy of the workload (weak scaling, no collective on the data path). Only the
+    timing uses the process group: a barrier around the timed region and the
+    maximum of the per-rank times. The backend is NCCL on GPUs; the same code runs
+    over gloo on the CPU (tests)."""
+
+    def __init__(self, backend="nccl", device=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.device = device
+        if self.world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group(backend, device_id=device)
+            else:
+                dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+def job_rate(world, points_per_rank, ms_max):
+    """Whole-job Mpts/s: the points all ranks solved over the slowest rank's time."""
+    return world * points_per_rank / (ms_max * 1e-3) / 1e6
+
+
 def bench_reference(args):
     """The FP64 CPU oracle, as it stands, on a bounded slab of the workload per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -199,27 +242,12 @@ def bench_ours(args):
     import torch
     from paper_1802_10323_gb300 import binding as lib
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl", dev)
+    world, rank = ranks.world, ranks.rank
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     n = (args.n, args.n, args.n)
     N = n[0] * n[1] * n[2]
@@ -256,7 +284,7 @@ def bench_ours(args):
     prof = plan.profile_read()
     plan.profile(False)
     inf = lib.read_info(info)
-    value = world * N / (ms_max * 1e-3) / 1e6
+    value = job_rate(world, N, ms_max)
 
     # dominant kernel and its roofline
     bpp = BYTES_PER_POINT["refine"]
@@ -306,7 +334,7 @@ def bench_ours(args):
         for _ in range(k_e2e):
             ie = plan.solve_host(fh, ph, f, p)
         t_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e)
-        e2e = {"value": world * N / t_e2e / 1e6, "unit": "Mpts/s",
+        e2e = {"value": job_rate(world, N, t_e2e * 1e3), "unit": "Mpts/s",
                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8 + 32,
                "ms_per_step": t_e2e * 1e3, "status": ie.status}
         del fh, ph
@@ -368,7 +396,7 @@ def bench_ours(args):
                        "parallelism": f"replicas x{world}"},
             "refine": {"iterations": inf.iterations, "rel_residual": inf.rel_residual,
                        "status": inf.status},
-            "fp64_solve": {"value": world * N / (ms64 * 1e-3) / 1e6, "unit": "Mpts/s",
+            "fp64_solve": {"value": job_rate(world, N, ms64), "unit": "Mpts/s",
                            "ms_per_step": ms64, "max_rel_diff_vs_refined": diff,
                            "kernels": {k: v[3] / k64 for k, v in prof64.items() if v[0]}},
             "speedup_vs_fp64": ms64 / ms_max,
@@ -385,9 +413,7 @@ def bench_ours(args):
         }
         print(json.dumps(line))
     plan.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
