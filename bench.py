@@ -51,7 +51,7 @@ BYTES_PER_POINT = {
                "y_bwd": 4 + 4, "x_bwd_f64store": 4 + 4, "x_bwd_f64base": 4 + 4 + 8 + 4,
                "x_bwd_f64acc": 4 + 8 + 8 + 4, "materialize": 4 + 8,
                "residual_first": 8 + 4 + 8, "residual_first3": 8 + 4 + 8, "residual": 8 + 4 + 8,
-               "residual_check": 8 + 4, "residual_exact": 8 + 8 + 4},
+               "residual_check": 8 + 4, "residual_out": 8 + 4 + 8, "residual_exact": 8 + 8 + 4},
     "fp64": {"x_fwd": 16, "y_fwd": 16, "z_solve": 16, "y_bwd": 16, "x_bwd": 16},
 }
 
@@ -299,7 +299,7 @@ def bench_ours(args):
     peak, peak_src = peaks()
     gpu_launches = sum(v[0] for v in prof.values()) + sum(
         prof.get(k, (0,))[0] for k in ("residual_first", "residual_first3", "residual", "residual_check",
-                                       "residual_exact"))
+                                       "residual_out", "residual_exact"))
     kernels = {k: {"launches": v[0], "active": v[1], "active_ms_per_step": v[3] / args.steps,
                    "share": v[3] / max(sum(x[3] for x in prof.values()), 1e-9)}
                for k, v in prof.items() if v[0]}

@@ -116,6 +116,9 @@ struct Ctrl {
   double bnd;               // accumulated drift bound of the incremental residual
   int skip_redo;            // 0: pass 0 is repeated with the three-level split
   int nomat0;               // 0: the loop ended at pass 0, p is written from Φ_0
+  int skip_out;             // 0: a pass m ≥ 1 found no convergence; it is repeated with its output
+  int pad2;
+  unsigned long long dmax_prev;  // max|e| of the correction the current pass used
 };
 
 cudaError_t launch_finalize(Ctrl* ctrl, const float* partial, int nblocks, double wsum_total,

@@ -108,12 +108,12 @@ void split_df(double d, float2* out) {
 // per grid point (the FP32 refinement path has separate kinds for its FP64-input
 // x pass, its storing and accumulating x passes and its check-only residual).
 enum Kind { K_XF = 0, K_XF64IN, K_YF, K_Z, K_ZS, K_YB, K_XB, K_XB64ST, K_XB64ACC, K_RES, K_CHK,
-            K_CTL, K_VER, K_RES0, K_RES3, K_XB64BASE, K_MAT, K_NKINDS };
+            K_CTL, K_VER, K_RES0, K_RES3, K_XB64BASE, K_MAT, K_RESOUT, K_NKINDS };
 static const char* kKindName[K_NKINDS] = {"x_fwd", "x_fwd_f64in", "y_fwd", "z_solve",
                                           "z_singular", "y_bwd", "x_bwd", "x_bwd_f64store",
                                           "x_bwd_f64acc", "residual", "residual_check", "control",
                                           "residual_exact", "residual_first", "residual_first3",
-                                          "x_bwd_f64base", "materialize"};
+                                          "x_bwd_f64base", "materialize", "residual_out"};
 constexpr int kProfMax = 4096;
 
 struct Prof {
@@ -439,14 +439,17 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   ra.skip = skip;
   const double wsum_total = pl->wsum * pl->nx * pl->ny;
   if ((e = correction(0)) != cudaSuccess) return cuda_fail(pl, e, "initial solve");
+  // Passes m ≥ 1 first only check (no output: the loop usually ends there); if
+  // their finalize finds no convergence, the pass is repeated to store r_m for the
+  // next correction. Pass 0 stores r_0 at once (it almost never converges).
   for (int it = 0; it <= pl->max_iter; ++it) {
     const bool last = (it == pl->max_iter);
-    ra.rh_out = last ? nullptr : rh;  // the last pass only checks
-    ra.rl_out = last ? nullptr : rl;
+    ra.rh_out = (last || it > 0) ? nullptr : rh;
+    ra.rl_out = (last || it > 0) ? nullptr : rl;
     ra.pmax_bits = it == 0 ? &ctrl->pmax : &ctrl->dmax;
     ra.u = it == 0 ? u0 : w;
     ra.skip = skip;
-    if ((e = run(pl, last ? K_CHK : (it == 0 ? K_RES0 : K_RES), st,
+    if ((e = run(pl, (last || it > 0) ? K_CHK : K_RES0, st,
                  [&] { return launch_residual_inc(ra, it, 0, st); })) != cudaSuccess)
       return cuda_fail(pl, e, "residual");
     if ((e = run(pl, K_CTL, st, [&] {
@@ -468,6 +471,15 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       // the loop ended at pass 0 (converged or max_iter = 0): p = Φ_0
       if ((e = run(pl, K_MAT, st, [&] { return launch_widen(u0, p, pl->N, &ctrl->nomat0, st); })) != cudaSuccess)
         return cuda_fail(pl, e, "store");
+    }
+    if (it > 0 && !last) {  // the output repeat of pass it, only if it did not converge
+      ResidArgs ro = ra;
+      ro.rh_out = rh;
+      ro.rl_out = rl;
+      ro.pmax_bits = &ctrl->dmax_prev;
+      ro.skip = &ctrl->skip_out;
+      if ((e = run(pl, K_RESOUT, st, [&] { return launch_residual_inc(ro, it, 0, st); })) != cudaSuccess)
+        return cuda_fail(pl, e, "residual");
     }
     if (!last && (e = correction(it + 1)) != cudaSuccess) return cuda_fail(pl, e, "correction");
   }

@@ -620,7 +620,8 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
   }
   if (iteration > 0)
     c->bnd += anorm * (ldexp(bits_f64(c->dmax), -43) + ldexp(bits_f64(c->pmax), -52));
-  c->dmax = 0;  // the next correction's x backward records max|e| here
+  c->dmax_prev = c->dmax;  // the scale of the output repeat of this pass
+  c->dmax = 0;             // the next correction's x backward records max|e| here
   const double rmax = key_f32(c->red[0]), rmin = key_f32(c->red[1]);
   const double vfmax = key_f32(c->red[2]), vfmin = key_f32(c->red[3]);
   const double rn = fmax(rmax - mr, mr - rmin);
@@ -640,6 +641,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
   if (ok) c->converged = 1;
   if (ok || last) c->vskip = (c->bnd <= 0.05 * rtol * fn) ? 1 : 0;
   if (iteration == 0) c->nomat0 = (ok || last) ? 0 : 1;
+  c->skip_out = (ok || last) ? 1 : 0;
   if (info && (ok || last)) {
     info->status = ok ? PS_OK : PS_NOT_CONVERGED;
     info->iterations = iteration;
