@@ -42,7 +42,7 @@ __device__ __forceinline__ TC in_cvt(TI x) { return ld_cvt<TC, TI>::f(x); }
 enum { OM_STORE = 0, OM_ACC = 1, OM_BASE = 2, OM_NONE = 3 };
 
 template <class T, class TI, class TO, int M, bool FWD, int OM>
-__global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? (OM == OM_NONE ? 2 : 3) : 4) : 2)
+__global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? 3 : 4) : 2)
     xform_row_kernel(FastArgs<T> a) {
   if (a.skip && *a.skip) return;
   using S = Shape<M>;
@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? (OM =
   TO* out = static_cast<TO*>(a.out);
   const int ny = a.ny, nlines = a.nlines;
   const unsigned full = 0xffffffffu;
-  unsigned long long amax = 0;
+  // max |transform output| of FP64 outputs, tracked on the values before widening
+  // (exact) so that no 64-bit work per value reaches the FP64 pipe
+  T tmax = (T)0;
 
   const int wstride = gridDim.x * WARPS * LPW;
   for (int l0 = (blockIdx.x * WARPS + warp) * LPW; l0 < nlines; l0 += wstride) {
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? (OM =
           if constexpr (OM == OM_ACC || (F64OUT && OM == OM_BASE)) o.v[u] = o.v[u] + x;
           else o.v[u] = x;
           if constexpr (sizeof(TO) == 8)
-            if (live) amax = max(amax, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+            if (live) tmax = fmax(tmax, fabs(o2.v[u]));
         }
         if (live) {
           if constexpr (OM != OM_NONE) *reinterpret_cast<vec<TO, NV>*>(dst + i0) = o;
@@ -353,7 +355,9 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(T) == 4 ? (M >= 512 ? (OM =
   }
   if constexpr (sizeof(TO) == 8) {
     if (a.amax) {
-      for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(full, amax, o));
+      for (int o = 16; o > 0; o >>= 1) tmax = fmax(tmax, __shfl_xor_sync(full, tmax, o));
+      const unsigned long long amax =
+          (unsigned long long)__double_as_longlong(st_cvt<double, T>::f(tmax));  // ≥ 0: the bits order as the values
       if (lane == 0 && amax) atomicMax(a.amax, amax);
     }
   }
