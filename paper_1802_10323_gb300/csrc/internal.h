@@ -84,6 +84,9 @@ struct ResidArgs {
   df idx2, idy2;            // 1/Δx², 1/Δy²
   const float2* zlo;        // coefficient of (Φ_{k−1} − Φ_k), ghost rules folded in
   const float2* zhi;        // coefficient of (Φ_{k+1} − Φ_k)
+  const float2* zres;       // passes m ≥ 1: per plane (a_k, c_k, w_c) in double-float, the
+                            // Dirichlet ghost sign folded into a_0 / c_{n−1} (see residual.cu)
+  double asum;              // max over planes of Σ_j |w_j| (the 7 coefficients of a row)
   const float* wz;          // Δz^f_k (weights of the mean, singular problems)
   const float* mu;          // double-float volume-weighted mean of f (singular)
   const unsigned long long* pmax_bits;  // bit pattern of max|operand| (sets the fixed-point scale)

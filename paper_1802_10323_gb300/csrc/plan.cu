@@ -138,6 +138,8 @@ struct ps_plan {
   double *za64, *zb64, *zc64, *dzf64, *idzf64, *idzc64;
   float *za32, *zb32, *zc32, *dzf32, *idzf32, *idzc32;
   float2 *zlo, *zhi;
+  float2* zres;  // residual passes m ≥ 1: (a_k, c_k, w_c) per plane, Dirichlet ghost sign folded in
+  double asum;   // max over rows of Σ_j |w_j| (those passes' accumulator binade)
   double wsum;  // Σ Δz^f (the per-plane weights of the singular mean, times nx·ny)
   double anorm; // an upper bound of ‖A‖∞ (the drift bound of the incremental residual)
   int lowx, lowy;  // FP32 non-periodic z: rectangle of columns solved in FP64 (tridiag.cu)
@@ -430,6 +432,8 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   ra.idy2 = pl->idy2;
   ra.zlo = pl->zlo;
   ra.zhi = pl->zhi;
+  ra.zres = pl->zres;
+  ra.asum = pl->asum;
   ra.wz = pl->dzf32;
   ra.mu = ctrl->mu;
   ra.singular = pl->singular;
@@ -622,6 +626,27 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
     }
     p->anorm = 8.0 / (dx * dx) + 8.0 / (dy * dy) + zmax;
   }
+  // Sum form of a row for the residual passes m ≥ 1: A·e = Σ_j w_j·e_j over x±1,
+  // y±1, z±1 and the centre (w_c = −Σ of the others). The ghost plane at a
+  // Dirichlet z end is loaded as a copy of the boundary plane, so its coefficient
+  // carries the ghost's sign (ghost = −Φ).
+  std::vector<float2> zres(3 * (size_t)nz);
+  {
+    const double ix2 = 1.0 / (dx * dx), iy2 = 1.0 / (dy * dy);
+    const bool dlo = (bcz == PS_BC_DIRICHLET_DIRICHLET);
+    const bool dhi = (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_NEUMANN_DIRICHLET);
+    double asum = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      const double cl = (k == 0 && dlo) ? -lo[k] : lo[k];
+      const double ch = (k == nz - 1 && dhi) ? -hi[k] : hi[k];
+      split_df(cl, &zres[3 * (size_t)k]);
+      split_df(ch, &zres[3 * (size_t)k + 1]);
+      split_df(-(2.0 * ix2 + 2.0 * iy2 + lo[k] + hi[k]), &zres[3 * (size_t)k + 2]);
+      const double rs = 4.0 * ix2 + 4.0 * iy2 + 2.0 * (lo[k] + hi[k]);
+      asum = rs > asum ? rs : asum;
+    }
+    p->asum = asum;
+  }
 
   // ---- axis tables ----
   AxisTab* axes[2] = {&p->ax, &p->ay};
@@ -635,7 +660,7 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
     bytes += align256(n * sizeof(double)) + align256(n * sizeof(float));
   }
   bytes += 6 * align256(nz * sizeof(double)) + 6 * align256(nz * sizeof(float)) +
-           2 * align256(nz * sizeof(float2));
+           2 * align256(nz * sizeof(float2)) + align256(3 * nz * sizeof(float2));
   char* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, bytes);
   if (e != cudaSuccess) {
@@ -715,8 +740,10 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
   }
   p->zlo = reinterpret_cast<float2*>(take(nz * sizeof(float2)));
   p->zhi = reinterpret_cast<float2*>(take(nz * sizeof(float2)));
+  p->zres = reinterpret_cast<float2*>(take(3 * nz * sizeof(float2)));
   hput(p->zlo, zlo.data(), nz * sizeof(float2));
   hput(p->zhi, zhi.data(), nz * sizeof(float2));
+  hput(p->zres, zres.data(), 3 * nz * sizeof(float2));
   e = cudaMemcpy(dev, host.data(), bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(dev);

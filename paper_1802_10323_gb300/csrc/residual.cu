@@ -3,18 +3,20 @@
 // FP64 arithmetic and f64<->f32 conversions issue at ~1/64 of the FP32 rate on
 // this part, so the 7-point stencil is evaluated in FP32 with error-free
 // transformations (TwoSum, FMA products; "double-float", ~48 significant bits).
-// Two kinds of pass share one kernel template:
-//   * incremental (every pass of the refinement loop): the stencil operand U is
-//     an FP32 field — the FP32 solve Φ_0 in pass 0 (its FP64 widening is the
-//     stored Φ, exactly), the last correction e in later passes — and
+// The refinement loop evaluates
 //       pass 0:  r_0 = f − A·Φ_0                 (f FP64, split on its bit pattern)
 //       pass m:  r_m = r_{m−1} − c_m − A·e_{m−1}  (r_{m−1} stored as FP32 hi + lo)
-//     with c_1 = μ_f (singular problems) and c_m = 0 otherwise. The result is
-//     stored as hi + lo (the hi part is the right-hand side of the next FP32
-//     correction solve). Since e is small, A·e is evaluated to ~2^-44 of |e|, not
-//     of |Φ|, so later passes are more accurate than a fresh evaluation;
-//   * exact (an optional confirmation at the end): r = f − μ_f − A·Φ from the
-//     stored FP64 Φ, split on its bit pattern.
+// with Φ_0 the FP32 solve (its FP64 widening is the stored Φ, exactly), e the last
+// FP32 correction, c_1 = μ_f (singular problems) and c_m = 0 otherwise; r is stored
+// as hi + lo (the hi part is the right-hand side of the next FP32 correction solve).
+// Since e is small, A·e needs accuracy relative to |e| only, not to |Φ|, so later
+// passes are more accurate than a fresh evaluation. Two kernels:
+//   * residual_kernel (pass 0, and an optional exact confirmation at the end,
+//     r = f − μ_f − A·Φ from the stored FP64 Φ): the operand is split on a
+//     fixed-point grid (below) and the stencil evaluated in double-float,
+//     ~2^-44·‖A‖·max|U|, three levels when that is not enough;
+//   * residual_acc_kernel (passes m ≥ 1): the sum-form stencil accumulated in a
+//     single FP32 word offset into a fixed binade (see there), ~2^-39·‖A‖·max|e|.
 //
 // Splitting the operand: U = ph + pl with ph on a fixed-point grid 2^−s common to
 // the whole field (s from max|U|, so |ph|·2^s < 2^20): the stencil sums of ph are
@@ -62,7 +64,6 @@ enum : int {
   RK_FIRST = 2,   // pass 0: max/min of f, and (singular) the weighted sum of f
   RK_SUBMU = 4,   // subtract μ_f (double-float) from the base
   RK_U32 = 8,     // operand U is FP32 (else FP64)
-  RK_DFBASE = 16, // base is r_{m−1} = hi + lo (else f, FP64)
   RK_SPLIT3 = 32  // three-level split of U (pass 0 and the exact pass; see below)
 };
 
@@ -167,10 +168,54 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// Block reductions of one pass (warp shuffles, then one thread over the warps):
+// max and min of r (and of f when FIRST) into the reduction words, and the
+// per-block double-float weighted sums into the partials.
+template <bool FIRST>
+__device__ __forceinline__ void resid_reduce(const ResidArgs& a, float rmax, float rmin, float fmax_,
+                                             float fmin_, float wr, df wf) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const unsigned full = 0xffffffffu;
+  df wrd = {wr, 0.f};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(full, rmax, o));
+    rmin = fminf(rmin, __shfl_xor_sync(full, rmin, o));
+    fmax_ = fmaxf(fmax_, __shfl_xor_sync(full, fmax_, o));
+    fmin_ = fminf(fmin_, __shfl_xor_sync(full, fmin_, o));
+    wrd = add_u(wrd, df{__shfl_xor_sync(full, wrd.h, o), __shfl_xor_sync(full, wrd.l, o)});
+    wf = add_u(wf, df{__shfl_xor_sync(full, wf.h, o), __shfl_xor_sync(full, wf.l, o)});
+  }
+  __shared__ float red[RWARPS][8];
+  if (tx == 0) {
+    red[ty][0] = rmax; red[ty][1] = rmin; red[ty][2] = fmax_; red[ty][3] = fmin_;
+    red[ty][4] = wrd.h; red[ty][5] = wrd.l; red[ty][6] = wf.h; red[ty][7] = wf.l;
+  }
+  __syncthreads();
+  if (ty == 0 && tx == 0) {
+    for (int w = 1; w < RWARPS; ++w) {
+      rmax = fmaxf(rmax, red[w][0]);
+      rmin = fminf(rmin, red[w][1]);
+      fmax_ = fmaxf(fmax_, red[w][2]);
+      fmin_ = fminf(fmin_, red[w][3]);
+      wrd = add_u(wrd, df{red[w][4], red[w][5]});
+      wf = add_u(wf, df{red[w][6], red[w][7]});
+    }
+    atomicMax(&a.red[0], f32_key(rmax));
+    atomicMin(&a.red[1], f32_key(rmin));
+    if (FIRST) {
+      atomicMax(&a.red[2], f32_key(fmax_));
+      atomicMin(&a.red[3], f32_key(fmin_));
+    }
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    reinterpret_cast<float4*>(a.partial)[bid] = make_float4(wrd.h, wrd.l, wf.h, wf.l);
+  }
+}
+
 template <int RPT, int KIND>
 __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(ResidArgs a) {
   constexpr bool SING = KIND & RK_SING, FIRST = KIND & RK_FIRST, SUBMU = KIND & RK_SUBMU;
-  constexpr bool U32 = KIND & RK_U32, DFBASE = KIND & RK_DFBASE, SPLIT3 = KIND & RK_SPLIT3;
+  constexpr bool U32 = KIND & RK_U32, SPLIT3 = KIND & RK_SPLIT3;
   using UT = typename std::conditional<U32, float, double>::type;
   using CT = typename std::conditional<SPLIT3, fxp3, fxp>::type;  // a split cell
   constexpr int TY = RWARPS * RPT, W = RTX + 2, CELLS = resid_cells(RPT);
@@ -270,20 +315,15 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   // march without the per-point domain tests.
   const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny);
   const size_t col = (size_t)jb * nx + i;  // this thread's column, row jb, plane 0
-  // the base of each point: f (FP64, split into hi + lo) or r_{m−1} = hi + lo
-  using base_t = typename std::conditional<DFBASE, float2, double>::type;
+  // the base of each point: f (FP64, split into hi + lo)
+  using base_t = double;
   auto load_base = [&](int k, base_t* bv, auto full_tag) {
     constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
       const size_t g = (size_t)k * sxy + col + (size_t)m * nx;
       const bool ld = FULL || in[m];
-      if constexpr (DFBASE) {
-        bv[m].x = ld ? __ldg(a.rh_in + g) : 0.f;
-        bv[m].y = ld ? __ldg(a.rl_in + g) : 0.f;
-      } else {
-        bv[m] = ld ? __ldg(a.f + g) : 0.0;
-      }
+      bv[m] = ld ? __ldg(a.f + g) : 0.0;
     }
   };
 
@@ -342,9 +382,7 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
       const CT ym = (m == 0) ? Fc[cidx[0] - W] : zc[m > 0 ? m - 1 : 0];
       const CT yp = (m == RPT - 1) ? Fc[cidx[RPT - 1] + W] : zc[m + 1 < RPT ? m + 1 : 0];
       const CT zmv = zm[m], zpv = zp[m];
-      df bv;
-      if constexpr (DFBASE) bv = {bcur[m].x, bcur[m].y};
-      else bv = df_from_f64(bcur[m]);
+      const df bv = df_from_f64(bcur[m]);
       // exact high-part stencil sums (fixed-point grid), FP32 low parts
       const float sx = (xm.h + xp.h) - 2.f * pc.h, sy = (ym.h + yp.h) - 2.f * pc.h;
       const float dm = zmv.h - pc.h, dpz = zpv.h - pc.h;
@@ -416,42 +454,304 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   else march(std::false_type{});
   cp_wait<0>();
 
-  // block reductions: warp shuffles, then one thread over the warps
-  const unsigned full = 0xffffffffu;
-  df wrd = {wr, 0.f};
+  resid_reduce<FIRST>(a, rmax, rmin, fmax_, fmin_, wr, wf);
+}
+
+// ---------------------------------------------------------------------------
+// Passes m ≥ 1 in one accumulator word.
+//
+// The operand is the last correction e (FP32), about 10^-7 of Φ, so A·e needs
+// absolute accuracy ~2^-39·‖A‖∞·max|e| only (that error enters the drift bound
+// and is far below the FP64 rounding of Φ). The stencil is taken in sum form,
+//   A·e = Σ_j w_j·e_j over the cells x±1, y±1, z±1 and the centre,
+// with double-float coefficients (the centre's w_c = −(2/Δx² + 2/Δy² + a_k + c_k))
+// and accumulated in ONE FP32 word offset by σ = 1.5·2^G, where 2^(G−1) exceeds
+// Σ_j |w_j|·max|e| and so every partial sum: the word stays in σ's binade, where
+// every FMA acc' = fma(e_j, w_j.h, acc) rounds onto the fixed grid 2^(G−23), the
+// difference acc − acc' is exact, and fma(e_j, w_j.h, acc − acc') is the rounding
+// error itself (to 2^-24 of it). Those errors and the e_j·w_j.l terms go into a
+// second word. Five FP32 operations per term instead of the split, the exact
+// products and the TwoSum chain of the general kernel; the evaluation error is at
+// most ~2^(G−41) ≤ 2^-39·Σ_j|w_j|·max|e|.
+//
+// The raw planes of e stream into a shared ring with cp.async (16-byte copies of
+// each row's 32 interior cells when n_x is a multiple of 4) and are read in
+// place: no split pass, one barrier per plane. The ghost rules of Table 1 are the
+// general kernel's, with two changes: a Dirichlet z end keeps the clamped copy of
+// the boundary plane and carries the sign in its coefficient (the per-plane table
+// zres holds a_k, c_k and w_c with that sign folded in), and Dirichlet x/y halo
+// cells are negated in shared memory by the thread that copied them, after the
+// copy lands and before the barrier that publishes the plane.
+enum : int {
+  AK_SING = 1,   // singular problem: weighted sum of r
+  AK_SUBMU = 2,  // subtract μ_f from the base (pass 1 of a singular problem)
+  AK_OUT = 4,    // store r_m = hi + lo (else norms only)
+  AK_VEC = 8     // n_x % 4 == 0: 16-byte row copies
+};
+constexpr int AW = 40;     // shared row pitch: halo at column 3, interior 4 … 35, halo at 36
+constexpr int ADEPTH = 5;  // raw-plane ring: k, k+1 read; k+2 … k+4 in flight
+__host__ __device__ constexpr int acc_cells(int rpt) { return AW * (RWARPS * rpt + 2); }
+
+template <int RPT, int KIND>
+__global__ void __launch_bounds__(RTHREADS, 3) residual_acc_kernel(ResidArgs a) {
+  constexpr bool SING = KIND & AK_SING, SUBMU = KIND & AK_SUBMU, OUT = KIND & AK_OUT, VEC = KIND & AK_VEC;
+  constexpr int TY = RWARPS * RPT, ROWS = TY + 2, CELLS = acc_cells(RPT);
+  constexpr int NC16 = VEC ? (8 * ROWS + RTHREADS - 1) / RTHREADS : 1;           // 16-byte copies
+  constexpr int NC4 = VEC ? 1 : ((RTX + 2) * ROWS + RTHREADS - 1) / RTHREADS;    // 4-byte copies
+  if (a.skip && *a.skip) return;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const size_t sxy = (size_t)nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RTX + tx;
+  const int x0 = blockIdx.x * RTX, y0 = blockIdx.y * TY;
+  const int i = x0 + tx, jb = y0 + ty * RPT;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(nz, k0 + a.zchunk);
+  const bool perz = (a.bcz == BC_P);
+  float sig;  // σ = 1.5·2^G, 2^(G−2) ≤ 1.001·Σ|w|·max|e| < 2^(G−1)
+  {
+    const double B = 1.001 * a.asum * __longlong_as_double((long long)*a.pmax_bits);
+    const int eb = (int)(((unsigned long long)__double_as_longlong(B) >> 52) & 0x7FF);
+    const int G = max(-100, min(120, eb == 0 ? -100 : eb - 1023 + 2));
+    sig = 1.5f * __uint_as_float((uint32_t)(G + 127) << 23);
+  }
+  extern __shared__ __align__(16) float ring[];  // [ADEPTH][ROWS][AW]
+
+  // Copies of this thread: shared offset, in-plane source offset, and bits
+  // "exists", "source valid" (else zero fill) and "negate" (Dirichlet ghost).
+  int s16[NC16], g16[NC16], s4[NC4], g4[NC4];
+  uint32_t has16 = 0, ok16 = 0, neg16 = 0, has4 = 0, ok4 = 0, neg4 = 0;
+  {
+    const int xl = end_lo(a.bcx), xh = end_hi(a.bcx), yl = end_lo(a.bcy), yh = end_hi(a.bcy);
+    // row rr of the tile → source row (wrap or clamp), validity, sign
+    auto map_y = [&](int rr, int& gj, bool& ok, bool& neg) {
+      gj = y0 - 1 + rr;
+      ok = true;
+      neg = false;
+      if (gj < 0) {
+        if (a.bcy == BC_P) gj = ny - 1; else { gj = 0; neg = (yl == END_D); }
+      } else if (gj == ny) {
+        if (a.bcy == BC_P) gj = 0; else { gj = ny - 1; neg = (yh == END_D); }
+      } else if (gj > ny) {
+        ok = false;
+      }
+    };
+    // column cc ∈ [0, 34) of the tile (cc = 0 and 33 are the halo) → source column
+    auto map_x = [&](int cc, int& gi, bool& ok, bool& neg) {
+      gi = x0 - 1 + cc;
+      ok = true;
+      neg = false;
+      if (gi < 0) {
+        if (a.bcx == BC_P) gi = nx - 1; else { gi = 0; neg = (xl == END_D); }
+      } else if (gi == nx) {
+        if (a.bcx == BC_P) gi = 0; else { gi = nx - 1; neg = (xh == END_D); }
+      } else if (gi > nx) {
+        ok = false;
+      }
+    };
+    auto cell = [&](int rr, int cc, int& so, int& go, bool& ok, bool& neg) {
+      int gj, gi;
+      bool oky, negy, okx, negx;
+      map_y(rr, gj, oky, negy);
+      map_x(cc, gi, okx, negx);
+      const int oj = y0 - 1 + rr, oi = x0 - 1 + cc;
+      ok = oky && okx && !((oi < 0 || oi >= nx) && (oj < 0 || oj >= ny));  // corners unused
+      neg = negx ^ negy;
+      so = rr * AW + 3 + cc;
+      go = ok ? gj * nx + gi : 0;
+    };
+    if constexpr (VEC) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmaxf(rmax, __shfl_xor_sync(full, rmax, o));
-    rmin = fminf(rmin, __shfl_xor_sync(full, rmin, o));
-    fmax_ = fmaxf(fmax_, __shfl_xor_sync(full, fmax_, o));
-    fmin_ = fminf(fmin_, __shfl_xor_sync(full, fmin_, o));
-    wrd = add_u(wrd, df{__shfl_xor_sync(full, wrd.h, o), __shfl_xor_sync(full, wrd.l, o)});
-    wf = add_u(wf, df{__shfl_xor_sync(full, wf.h, o), __shfl_xor_sync(full, wf.l, o)});
+      for (int h = 0; h < NC16; ++h) {
+        const int e = tid + h * RTHREADS;
+        const int rr = e >> 3, q = e & 7;
+        int gj;
+        bool oky, negy;
+        map_y(rr < ROWS ? rr : 0, gj, oky, negy);
+        // chunks wholly beyond n_x are not copied (their cells are never read;
+        // the right ghost of a ragged tile sits in the first of them)
+        const bool ex = e < 8 * ROWS && x0 + 4 * q < nx;
+        s16[h] = rr * AW + 4 + 4 * q;
+        g16[h] = (ex && oky) ? gj * nx + x0 + 4 * q : 0;
+        has16 |= (ex ? 1u : 0u) << h;
+        ok16 |= (ex && oky ? 1u : 0u) << h;
+        neg16 |= (ex && negy ? 1u : 0u) << h;
+      }
+      {  // the two x-halo cells of each row: x0 − 1 and min(x0 + 32, n_x)
+        const int e = tid;
+        const int rr = e >> 1, cc = (e & 1) ? min(RTX, nx - x0) + 1 : 0;
+        bool ok, neg;
+        cell(rr < ROWS ? rr : 0, cc, s4[0], g4[0], ok, neg);
+        has4 = (e < 2 * ROWS) ? 1u : 0u;
+        ok4 = (ok && has4) ? 1u : 0u;
+        neg4 = (neg && has4) ? 1u : 0u;
+      }
+    } else {
+      s16[0] = g16[0] = 0;
+#pragma unroll
+      for (int h = 0; h < NC4; ++h) {
+        const int e = tid + h * RTHREADS;
+        const int rr = e / (RTX + 2), cc = e - rr * (RTX + 2);
+        bool ok, neg;
+        cell(rr < ROWS ? rr : 0, cc, s4[h], g4[h], ok, neg);
+        const bool ex = e < (RTX + 2) * ROWS;
+        has4 |= (ex ? 1u : 0u) << h;
+        ok4 |= (ok && ex ? 1u : 0u) << h;
+        neg4 |= (neg && ex ? 1u : 0u) << h;
+      }
+    }
   }
-  __shared__ float red[RWARPS][8];
-  if (tx == 0) {
-    red[ty][0] = rmax; red[ty][1] = rmin; red[ty][2] = fmax_; red[ty][3] = fmin_;
-    red[ty][4] = wrd.h; red[ty][5] = wrd.l; red[ty][6] = wf.h; red[ty][7] = wf.l;
+  const bool doneg = (neg16 | neg4) != 0;
+  const float* __restrict__ U = a.u;
+  auto issue = [&](int q, int slot) {  // raw copies of logical plane q (wrap or clamp in z)
+    const int pq = q < 0 ? (perz ? q + nz : 0) : (q >= nz ? (perz ? q - nz : nz - 1) : q);
+    const float* src = U + (size_t)pq * sxy;
+    float* dst = ring + slot * CELLS;
+    if constexpr (VEC) {
+#pragma unroll
+      for (int h = 0; h < NC16; ++h)
+        if ((has16 >> h) & 1u) {
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + s16[h]);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src + g16[h]),
+                       "r"(((ok16 >> h) & 1u) ? 16 : 0));
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < NC4; ++h)
+      if ((has4 >> h) & 1u) cp_async<4>(dst + s4[h], src + g4[h], (ok4 >> h) & 1u);
+    cp_commit();
+  };
+  auto negate = [&](int slot) {  // Dirichlet ghosts of a landed plane (own copies only)
+    float* dst = ring + slot * CELLS;
+    if constexpr (VEC) {
+#pragma unroll
+      for (int h = 0; h < NC16; ++h)
+        if ((neg16 >> h) & 1u) {
+          float4* c4 = reinterpret_cast<float4*>(dst + s16[h]);
+          float4 v = *c4;
+          v.x = -v.x; v.y = -v.y; v.z = -v.z; v.w = -v.w;
+          *c4 = v;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < NC4; ++h)
+      if ((neg4 >> h) & 1u) dst[s4[h]] = -dst[s4[h]];
+  };
+
+  int cidx[RPT];
+  bool in[RPT];
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    cidx[m] = (ty * RPT + m + 1) * AW + 4 + tx;
+    in[m] = (i < nx) && (jb + m < ny);
   }
+  const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny);
+  const size_t col = (size_t)jb * nx + i;
+  auto load_base = [&](int k, float2* bv, auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      const size_t g = (size_t)k * sxy + col + (size_t)m * nx;
+      const bool ld = FULL || in[m];
+      bv[m].x = ld ? __ldg(a.rh_in + g) : 0.f;
+      bv[m].y = ld ? __ldg(a.rl_in + g) : 0.f;
+    }
+  };
+
+  // prologue: planes k0−1 … k0+ADEPTH−2 in flight; wait for k0−1 and k0
+#pragma unroll
+  for (int q = 0; q < ADEPTH; ++q) {
+    if (k0 - 1 + q <= k1) issue(k0 - 1 + q, q);
+    else cp_commit();
+  }
+  float2 bcur[RPT], bnext[RPT];
+  if (interior) load_base(k0, bcur, std::true_type{});
+  else load_base(k0, bcur, std::false_type{});
+  cp_wait<ADEPTH - 2>();
+  if (doneg) negate(1);
   __syncthreads();
-  if (ty == 0 && tx == 0) {
-    for (int w = 1; w < RWARPS; ++w) {
-      rmax = fmaxf(rmax, red[w][0]);
-      rmin = fminf(rmin, red[w][1]);
-      fmax_ = fmaxf(fmax_, red[w][2]);
-      fmin_ = fminf(fmin_, red[w][3]);
-      wrd = add_u(wrd, df{red[w][4], red[w][5]});
-      wf = add_u(wf, df{red[w][6], red[w][7]});
-    }
-    atomicMax(&a.red[0], f32_key(rmax));
-    atomicMin(&a.red[1], f32_key(rmin));
-    if (FIRST) {
-      atomicMax(&a.red[2], f32_key(fmax_));
-      atomicMin(&a.red[3], f32_key(fmin_));
-    }
-    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    reinterpret_cast<float4*>(a.partial)[bid] = make_float4(wrd.h, wrd.l, wf.h, wf.l);
+  float zm[RPT], zc[RPT], zp[RPT];
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    zm[m] = ring[cidx[m]];
+    zc[m] = ring[CELLS + cidx[m]];
   }
+  float rmax = -INFINITY, rmin = INFINITY, wr = 0.f;
+  const df mu = SUBMU ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
+  const df wx = a.idx2, wy = a.idy2;
+  int islot = 0;  // slot of plane k−1 (refilled with plane k+ADEPTH−1)
+  int cslot = 1;  // plane k
+  int nslot = 2;  // plane k+1
+  auto march = [&](auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    for (int k = k0; k < k1; ++k) {
+      if (k + 1 < k1) load_base(k + 1, bnext, full_tag);
+      cp_wait<ADEPTH - 3>();  // plane k+1 has landed
+      if (doneg) negate(nslot);
+      __syncthreads();        // … for every thread; plane k−1 is no longer read
+      if (k + ADEPTH - 1 <= k1) issue(k + ADEPTH - 1, islot);
+      else cp_commit();
+      const float* Rc = ring + cslot * CELLS;
+      const float* Rn = ring + nslot * CELLS;
+      islot = cslot;  // plane k's slot is the free one next time
+      cslot = nslot;
+      nslot = (nslot + 1 == ADEPTH) ? 0 : nslot + 1;
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) zp[m] = Rn[cidx[m]];
+      const float2 c0 = __ldg(a.zres + 3 * k), c1 = __ldg(a.zres + 3 * k + 1), c2 = __ldg(a.zres + 3 * k + 2);
+      const df cl = {c0.x, c0.y}, ch = {c1.x, c1.y}, cd = {c2.x, c2.y};
+      const float w = SING ? __ldg(a.wz + k) : 0.f;
+      const size_t gk = (size_t)k * sxy + col;
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        const int ci = cidx[m];
+        const float xm = Rc[ci - 1], xp = Rc[ci + 1];
+        const float ym = (m == 0) ? Rc[ci - AW] : zc[m > 0 ? m - 1 : 0];
+        const float yp = (m == RPT - 1) ? Rc[ci + AW] : zc[m + 1 < RPT ? m + 1 : 0];
+        float acc = sig, lo = 0.f;
+        auto term = [&](float u, df wt) {
+          const float a2 = __fmaf_rn(u, wt.h, acc);
+          lo = __fadd_rn(lo, __fmaf_rn(u, wt.h, __fsub_rn(acc, a2)));
+          lo = __fmaf_rn(u, wt.l, lo);
+          acc = a2;
+        };
+        term(zc[m], cd);
+        term(zm[m], cl);
+        term(zp[m], ch);
+        term(xm, wx);
+        term(xp, wx);
+        term(ym, wy);
+        term(yp, wy);
+        const float H = __fsub_rn(acc, sig);  // exact: Σ_j w_j·e_j − lo
+        df bv = {bcur[m].x, bcur[m].y};
+        if constexpr (SUBMU) {
+          const df d1 = two_sum(bv.h, -mu.h);
+          bv = {d1.h, __fadd_rn(d1.l, __fsub_rn(bv.l, mu.l))};
+        }
+        const df d2 = two_sum(bv.h, -H);
+        const float rl = __fsub_rn(__fadd_rn(d2.l, bv.l), lo);
+        const float rf = __fadd_rn(d2.h, rl);
+        if (FULL || in[m]) {
+          if constexpr (OUT) {
+            const size_t g = gk + (size_t)m * nx;
+            a.rh_out[g] = rf;
+            a.rl_out[g] = __fsub_rn(rl, __fsub_rn(rf, d2.h));
+          }
+          rmax = fmaxf(rmax, rf);
+          rmin = fminf(rmin, rf);
+          if constexpr (SING) wr = fmaf(w, rf, wr);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        zm[m] = zc[m];
+        zc[m] = zp[m];
+        bcur[m] = bnext[m];
+      }
+    }
+  };
+  if (interior) march(std::true_type{});
+  else march(std::false_type{});
+  cp_wait<0>();
+  resid_reduce<false>(a, rmax, rmin, -INFINITY, INFINITY, wr, df{0.f, 0.f});
 }
 
 // Resets the reduction words of r (and of f in pass 0) before a residual pass.
@@ -512,12 +812,39 @@ cudaError_t launch_rpt(const ResidArgs& b, int kind, dim3 grid, cudaStream_t st)
   switch (kind) {
     case RK_U32 | RK_FIRST: return launch_kind<RPT, RK_U32 | RK_FIRST>(b, grid, st);
     case RK_U32 | RK_FIRST | RK_SING: return launch_kind<RPT, RK_U32 | RK_FIRST | RK_SING>(b, grid, st);
-    case RK_U32 | RK_DFBASE: return launch_kind<RPT, RK_U32 | RK_DFBASE>(b, grid, st);
-    case RK_U32 | RK_DFBASE | RK_SING: return launch_kind<RPT, RK_U32 | RK_DFBASE | RK_SING>(b, grid, st);
-    case RK_U32 | RK_DFBASE | RK_SING | RK_SUBMU:
-      return launch_kind<RPT, RK_U32 | RK_DFBASE | RK_SING | RK_SUBMU>(b, grid, st);
     default: return cudaErrorInvalidValue;
   }
+}
+template <int RPT, int KIND>
+cudaError_t launch_acc_kind(const ResidArgs& b, dim3 grid, cudaStream_t st) {
+  constexpr size_t smem = (size_t)ADEPTH * acc_cells(RPT) * sizeof(float);
+  residual_acc_kernel<RPT, KIND><<<grid, dim3(RTX, RWARPS), smem, st>>>(b);
+  return cudaGetLastError();
+}
+template <int RPT, int K>
+cudaError_t launch_acc_out(const ResidArgs& b, bool out, bool vec, dim3 grid, cudaStream_t st) {
+  if (out) return vec ? launch_acc_kind<RPT, K | AK_OUT | AK_VEC>(b, grid, st) : launch_acc_kind<RPT, K | AK_OUT>(b, grid, st);
+  return vec ? launch_acc_kind<RPT, K | AK_VEC>(b, grid, st) : launch_acc_kind<RPT, K>(b, grid, st);
+}
+template <int RPT>
+cudaError_t launch_acc_rpt(const ResidArgs& b, int kind, bool out, bool vec, dim3 grid, cudaStream_t st) {
+  switch (kind) {
+    case 0: return launch_acc_out<RPT, 0>(b, out, vec, grid, st);
+    case AK_SING: return launch_acc_out<RPT, AK_SING>(b, out, vec, grid, st);
+    case AK_SING | AK_SUBMU: return launch_acc_out<RPT, AK_SING | AK_SUBMU>(b, out, vec, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+// Passes m ≥ 1: same grid as the two-level passes (the finalize sums that many partials).
+cudaError_t launch_resid_acc(const ResidArgs& b0, int pass, cudaStream_t st) {
+  reset_red_kernel<<<1, 1, 0, st>>>(b0.red, b0.skip, 0);
+  const ResidShape s = resid_shape(b0.nx, b0.ny, b0.nz, false);
+  ResidArgs b = b0;
+  b.zchunk = s.zchunk;
+  const int kind = b.singular ? (AK_SING | (pass == 1 ? AK_SUBMU : 0)) : 0;
+  const bool out = b.rh_out != nullptr, vec = (b.nx % 4) == 0;
+  return s.rpt == 4 ? launch_acc_rpt<4>(b, kind, out, vec, s.grid, st)
+                    : launch_acc_rpt<2>(b, kind, out, vec, s.grid, st);
 }
 cudaError_t launch_resid(const ResidArgs& b0, int kind, int reset_f, cudaStream_t st) {
   reset_red_kernel<<<1, 1, 0, st>>>(b0.red, b0.skip, reset_f);
@@ -536,9 +863,11 @@ int residual_blocks(int nx, int ny, int nz, int split3) {
 cudaError_t launch_residual_inc(const ResidArgs& a, int pass, int split3, cudaStream_t st) {
   if (!a.u || (pass > 0 && (!a.rh_in || !a.rl_in)) || (!a.rh_out != !a.rl_out) || (split3 && pass))
     return cudaErrorInvalidValue;
-  int kind = RK_U32;
-  if (pass == 0) kind |= RK_FIRST | (split3 ? RK_SPLIT3 : 0);
-  else kind |= RK_DFBASE;
+  if (pass > 0) {
+    if (!a.zres) return cudaErrorInvalidValue;
+    return launch_resid_acc(a, pass, st);
+  }
+  int kind = RK_U32 | RK_FIRST | (split3 ? RK_SPLIT3 : 0);
   if (a.singular) kind |= RK_SING;
   if (a.singular && pass == 1) kind |= RK_SUBMU;
   return launch_resid(a, kind, pass == 0, st);
@@ -593,7 +922,7 @@ __device__ double bits_f64(unsigned long long b) { return __longlong_as_double((
 //
 // Drift bound: pass m ≥ 1 evaluates r_{m−1} − A·e_{m−1} instead of f − A·Φ_m. It
 // differs from a fresh evaluation from the stored Φ_m by the evaluation error of
-// A·e_{m−1} (≤ 2^-43·‖A‖∞·max|e|) and by the FP64 rounding of Φ += e
+// A·e_{m−1} (≤ 2^-39·‖A‖∞·max|e|, the single-word accumulation) and by the FP64 rounding of Φ += e
 // (≤ 2^-52·‖A‖∞·max|Φ|). If the accumulated bound exceeds 5 % of rtol·‖f_c‖∞ when
 // the loop ends (converged or not), the exact pass at the end re-evaluates the
 // residual from the stored Φ and decides.
@@ -619,7 +948,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Ctrl* c, const float* pa
     }
   }
   if (iteration > 0)
-    c->bnd += anorm * (ldexp(bits_f64(c->dmax), -43) + ldexp(bits_f64(c->pmax), -52));
+    c->bnd += anorm * (ldexp(bits_f64(c->dmax), -39) + ldexp(bits_f64(c->pmax), -52));
   c->dmax_prev = c->dmax;  // the scale of the output repeat of this pass
   c->dmax = 0;             // the next correction's x backward records max|e| here
   const double rmax = key_f32(c->red[0]), rmin = key_f32(c->red[1]);

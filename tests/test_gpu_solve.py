@@ -164,6 +164,41 @@ def test_refine_register_resident_sizes(lib, bcs):
     assert O.relative_residual(p, f, 6.0 / nx, 3.0 / ny, zf, *bcs) <= 1e-10
 
 
+# Refinement on sizes that reach the scalar-copy path of the later residual
+# passes (n_x not a multiple of 4), a ragged last x tile under the 16-byte copies
+# (n_x = 72), and two rows per thread (n_y < 32); Dirichlet ends on every axis.
+ODD = [(10, 12, 18), (12, 24, 54), (16, 24, 72), (6, 36, 6)]
+
+
+@pytest.mark.parametrize("shape", ODD, ids=["x".join(map(str, s)) for s in ODD])
+@pytest.mark.parametrize("bcs", [("DD", "DD", "DD"), ("ND", "P", "NN"), ("P", "ND", "DD")])
+def test_refine_unaligned_and_ragged_sizes(lib, shape, bcs):
+    nz, ny, nx = shape
+    lx, ly = 2.0, 3.0
+    zf = synth.tanh_faces(nz, 1.0, 1.5)
+    f = np.random.default_rng(nx * 5 + ny).uniform(-1, 1, shape)
+    p, info = _run(lib, f, lx / nx, ly / ny, zf, bcs, precision="fp32_refine", rtol=1e-10, max_iter=6)
+    assert info.status == 0 and info.rel_residual <= 1e-10, (info.status, info.rel_residual)
+    rr = O.relative_residual(p, f, lx / nx, ly / ny, zf, *bcs)
+    assert rr <= 1e-10 and abs(info.rel_residual - rr) <= 1e-11, (info.rel_residual, rr)
+    q = S.solve(f, lx / nx, ly / ny, zf, *bcs)
+    assert _relerr(p, q) <= 1e-8
+
+
+@pytest.mark.parametrize("shape,bcs", [((16, 24, 24), ("P", "P", "NN")), ((12, 16, 18), ("DD", "NN", "ND"))])
+def test_refine_several_corrections(lib, shape, bcs):
+    """A tolerance near the FP64 floor takes more than one correction, so the stored
+    residuals of the later passes (the output repeats) feed the next corrections."""
+    nz, ny, nx = shape
+    zf = synth.tanh_faces(nz, 1.0, 1.5)
+    f = np.random.default_rng(13).uniform(-1, 1, shape)
+    p, info = _run(lib, f, 1.0 / nx, 1.0 / ny, zf, bcs, precision="fp32_refine", rtol=1e-13, max_iter=8)
+    rr = O.relative_residual(p, f, 1.0 / nx, 1.0 / ny, zf, *bcs)
+    assert info.iterations >= 2, info.iterations
+    assert info.status == 0 and info.rel_residual <= 1e-13, (info.status, info.rel_residual, rr)
+    assert rr <= 1.5e-13 and abs(info.rel_residual - rr) <= 2e-14, (info.rel_residual, rr)
+
+
 REPORTED = [
     ("rough", (32, 48, 64), ("P", "P", "NN")),
     ("rough", (24, 32, 32), ("DD", "ND", "DD")),
