@@ -186,9 +186,9 @@ class Plan:
 
     def profile_read(self):
         """Per-kernel-kind timing since the last read: {name: (launches, active, total_ms, active_ms)}."""
-        arr = (PsKernelStat * 16)()
+        arr = (PsKernelStat * 32)()
         n = ctypes.c_int()
-        _check(_lib.ps_profile_read(self.handle, arr, 16, ctypes.byref(n)), self.handle)
+        _check(_lib.ps_profile_read(self.handle, arr, 32, ctypes.byref(n)), self.handle)
         return {arr[i].name.decode(): (arr[i].launches, arr[i].active_launches, arr[i].total_ms,
                                        arr[i].active_ms) for i in range(n.value)}
 

@@ -77,17 +77,6 @@ struct BatchArgs {
   int inject;              // test hook: one dependency that is never satisfied
 };
 
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ XformArgs<float> bx_args(const BGrid& G, int axis, const void* in, void* out, int acc,
                                     unsigned long long* amax) {
   XformArgs<float> a{};

@@ -117,6 +117,19 @@ __device__ __forceinline__ df df_from_f64(double d) {
 }
 __device__ __forceinline__ float df_to_f32(df a) { return __fadd_rn(a.h, a.l); }
 
+// Wall clock (ns) and an acquire load at GPU scope, for the bounded waits of the
+// persistent kernels (a consumer waits on a completion counter of earlier tasks).
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Order-preserving int key of a float (for atomicMax/atomicMin on signed values).
 __device__ __forceinline__ int f32_key(float f) {
   int i = __float_as_int(f);

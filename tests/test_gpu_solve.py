@@ -199,6 +199,26 @@ def test_refine_several_corrections(lib, shape, bcs):
     assert rr <= 1.5e-13 and abs(info.rel_residual - rr) <= 2e-14, (info.rel_residual, rr)
 
 
+# Refinement with the line lengths of the 1024^3 workload's kernels (n_x, n_y ∈
+# {512, 1024}: the M = 256 and M = 512 row and column transforms), few planes.
+LONG = [((6, 512, 512), ("P", "P", "NN")), ((4, 1024, 512), ("DD", "ND", "DD")),
+        ((5, 512, 1024), ("NN", "P", "P"))]
+
+
+@pytest.mark.parametrize("shape,bcs", LONG, ids=["x".join(map(str, s)) + "-" + "-".join(b) for s, b in LONG])
+def test_refine_long_lines(lib, shape, bcs):
+    nz, ny, nx = shape
+    lx, ly = 6.0, 3.0
+    zf = synth.tanh_faces(nz, 1.0, 1.5) if bcs[2] != "P" else synth.uniform_faces(nz, 1.0)
+    f = np.random.default_rng(nx + nz).uniform(-1, 1, shape)
+    p, info = _run(lib, f, lx / nx, ly / ny, zf, bcs, precision="fp32_refine", rtol=1e-10, max_iter=6)
+    assert info.status == 0 and info.rel_residual <= 1e-10, (info.status, info.rel_residual)
+    rr = O.relative_residual(p, f, lx / nx, ly / ny, zf, *bcs)
+    assert rr <= 1e-10 and abs(info.rel_residual - rr) <= 1e-11, (info.rel_residual, rr)
+    q = S.solve(f, lx / nx, ly / ny, zf, *bcs)
+    assert _relerr(p, q) <= 1e-8
+
+
 REPORTED = [
     ("rough", (32, 48, 64), ("P", "P", "NN")),
     ("rough", (24, 32, 32), ("DD", "ND", "DD")),
