@@ -249,7 +249,7 @@ def bench_ours(args):
     world, rank = ranks.world, ranks.rank
     barrier, max_over_ranks = ranks.barrier, ranks.max
 
-    n = (args.n, args.n, args.n)
+    n = (args.n, args.n, args.nz or args.n)
     N = n[0] * n[1] * n[2]
     f, zf, dx, dy = make_input(n, GRID["seed"], dev)
     plan = lib.Plan(n[0], n[1], n[2], dx, dy, zf=zf, bcs=BCS, precision="fp32_refine",
@@ -424,6 +424,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024, help="cells per axis (default: the 1024^3 workload)")
+    ap.add_argument("--nz", type=int, default=0,
+                    help="cells along z if not --n (an n x n x nz slab of the workload, e.g. for profiling)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
