@@ -200,12 +200,22 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlo
     for (int u = 0; u < ZK; ++u) buf[u] = (FULL || k0 + u < nz) ? src[(size_t)u * st] : 0.f;
   };
 
+  // L2 prefetch of the chunk after next (both sweeps), so that more of the column
+  // is in flight than the registers of the next chunk allow
+  auto prefetch = [&](int c2) {
+    if (c2 >= 0 && c2 < nfull) {
+      const float* src = d + (size_t)c2 * ZK * st;
+#pragma unroll
+      for (int u = 0; u < ZK; ++u) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (size_t)u * st));
+    }
+  };
   float cur[ZK], nxt[ZK];
   if (nfull > 0) load(0, cur, std::true_type{});
   else load(0, cur, std::false_type{});
   float cp = 0.f, dp = 0.f;
   for (int c = 0; c < nch; ++c) {
     const int k0 = c * ZK;
+    prefetch(c + 2);
     if (c + 1 < nfull) load(k0 + ZK, nxt, std::true_type{});
     else if (c + 1 < nch) load(k0 + ZK, nxt, std::false_type{});
     if (c < nfull) eliminate(k0, cur, cp, dp, nullptr, nullptr, std::true_type{});
@@ -220,6 +230,7 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlo
   float x = 0.f;
   for (int c = nch - 1; c >= 0; --c) {
     const int k0 = c * ZK;
+    prefetch(c - 2);
     if (c > 0) load(k0 - ZK, nxt, std::true_type{});  // every chunk below the last is full
     const float2 prev = (c > 0) ? ck[(size_t)(c - 1) * ncol + colc] : make_float2(0.f, 0.f);
     float cpa[ZK], dpa[ZK];

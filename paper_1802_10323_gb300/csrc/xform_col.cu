@@ -33,7 +33,19 @@ __global__ void __launch_bounds__(CShape<M, CW>::NT, sizeof(T) == 4 ? 1024 / CSh
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + fast_table_bytes<T, M>(a.bc));  // [M][CW]
   load_line_tables<T, M>(a.tw, a.bc, stw);
   const int ntiles = a.nz * (a.nx / CW);
-  for (int g = blockIdx.x; g < ntiles; g += gridDim.x) col_tile<T, M, FWD, CW>(a, stw, ptw, xtw, buf, g);
+  const int tpz = a.nx / CW;
+  for (int g = blockIdx.x; g < ntiles; g += gridDim.x) {
+    // forward: ask L2 for the rows of this CTA's next tile, so that its loads do not
+    // wait on HBM (measured at 1024³: −5 % forward; the backward tiles gain nothing)
+    const int gn = g + gridDim.x;
+    if (FWD && gn < ntiles) {
+      const int zb = gn / tpz, x0 = (gn - zb * tpz) * CW;
+      const T* nb = static_cast<const T*>(a.in) + (size_t)zb * a.ny * a.nx + x0;
+      for (int q = threadIdx.x; q < a.ny; q += blockDim.x)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + (size_t)q * a.nx));
+    }
+    col_tile<T, M, FWD, CW>(a, stw, ptw, xtw, buf, g);
+  }
 }
 
 }  // namespace col

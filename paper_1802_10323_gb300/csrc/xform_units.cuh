@@ -190,6 +190,18 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
     }
     __syncwarp();  // buffer reads done before the next line overwrites it
   } else {
+    // The FP64 output modes read the line's base (FP32 Φ_0) or its accumulator (FP64
+    // p) only when the outputs are written; ask L2 for them now, one 128-byte
+    // segment per lane, so that those loads do not wait on HBM after the transform.
+    if constexpr (sizeof(TO) == 8 && sizeof(T) == 4 && (OM == OM_BASE || OM == OM_ACC)) {
+      if (live) {
+        const char* pf = (OM == OM_BASE) ? reinterpret_cast<const char*>(a.base32 + base)
+                                         : reinterpret_cast<const char*>(dst);
+        constexpr int SEG = (OM == OM_BASE ? N * 4 : N * 8) / 128;  // 128-byte segments of the line
+#pragma unroll
+        for (int j = t; j < SEG; j += TPL) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf + 128 * j));
+      }
+    }
     // ---- backward pre-processing: pairs (k, M−k) from the line into the buffer ----
     auto X = [&](int i) { return in_cvt<T>(src[i]); };
     if (bc == BC_ND) {
