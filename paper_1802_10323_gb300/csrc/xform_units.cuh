@@ -50,6 +50,29 @@ __device__ __forceinline__ TC in_cvt(TI x) { return ld_cvt<TC, TI>::f(x); }
 // none (no FP64 output: only the FP32 copy and the max).
 enum { OM_STORE = 0, OM_ACC = 1, OM_BASE = 2, OM_NONE = 3 };
 
+// Slots of a 32-lane line (M ≥ 128): lane t holds wavenumbers k = t + 32·j, j < E.
+// After the last FFT stage slot si holds j = jout(si); the first stage takes slot si
+// at j = jin(si). The partner M − k of k is held by lane (32 − t) mod 32 at
+// j' = E − 1 − j (lane 0: j' = E − j, and k = 0 pairs with itself).
+template <int M>
+struct LaneSlots {
+  static constexpr int E = Shape<M>::E, R0 = Shape<M>::radix(0), RL = Shape<M>::radix(Shape<M>::NST - 1);
+  __host__ __device__ static constexpr int jin(int si) { return si / R0 + (si % R0) * (M / R0 / 32); }
+  __host__ __device__ static constexpr int jout(int si) { return si / RL + (si % RL) * (M / RL / 32); }
+  __host__ __device__ static constexpr int sin_(int j) {
+    int r = 0;
+    for (int s = 0; s < E; ++s)
+      if (jin(s) == j) r = s;
+    return r;
+  }
+  __host__ __device__ static constexpr int sout(int j) {
+    int r = 0;
+    for (int s = 0; s < E; ++s)
+      if (jout(s) == j) r = s;
+    return r;
+  }
+};
+
 // One line (two for M = 64, half a warp each) of the x transform: the warp's
 // exchange buffers at bufs, tables in shared memory, the first line index l0.
 // tmax accumulates max |FP64 output| (before widening) for the caller's reduction.
@@ -128,51 +151,48 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
       }
     }
     fast::fft_stages<T, M, false, 0, 1>(v, lc, stw, t);
-    // ---- post-processing: pairs (k, M−k) through the exchange buffer, scalar stores ----
-    __syncwarp();
+    if constexpr (TPL == 32) {
+      // ---- post-processing in registers: pairs (k, M−k), Z_{M−k} from the partner lane ----
+      // Lane t takes its slots j < E/2 (k = t + 32j) and writes the outputs of k and of
+      // M − k, whose Z arrives by shuffle from slot E−1−j of lane (32 − t) mod 32; every
+      // slot is read once. Lane 0's partners are its own slots E − j: the value it
+      // shuffled to itself one iteration earlier (k = 0 pairs with itself), and after the
+      // loop, the one of k = M/2.
+      using LS = LaneSlots<M>;
+      auto Y = [&](int i, T val) {
+        if (live) dst[i] = st_cvt<TO, T>::f(val);
+      };
+      if (bc == BC_ND) {
 #pragma unroll
-    for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-      for (int r = 0; r < RL; ++r) lc[cpad(t + q * TPL + r * (M / RL))] = v[q * RL + r];
-    __syncwarp();
-    auto Y = [&](int i, T val) {
-      if (live) dst[i] = st_cvt<TO, T>::f(val);
-    };
-    if (bc == BC_ND) {
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int k = t + i * TPL;
-        const cplx<T> c = cmul(xtw[M + k], lc[cpad(k)]);
-        Y(2 * k, (T)2 * c.x);
-        Y(N - 1 - 2 * k, (T)-2 * c.y);
-      }
-    } else {
-      constexpr int NP = (M / 2) / TPL + 1;
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const int k = t + i * TPL;
-        if (k > M / 2) break;
-        const cplx<T> Zk = lc[cpad(k)], Zmk = lc[cpad(k == 0 ? 0 : M - k)];
-        const cplx<T> Ek = cscale(cadd(Zk, conj_(Zmk)), (T)0.5);
-        const cplx<T> Ok = cscale(mul_mi(csub(Zk, conj_(Zmk))), (T)0.5);
-        const cplx<T> B = cmul(ptw[k], Ok);
-        const cplx<T> Vk = cadd(Ek, B), Vmk = conj_(csub(Ek, B));
-        if (bc == BC_P) {
-          if (k == 0) {
-            Y(0, Vk.x);
-            Y(N - 1, Vmk.x);
-          } else {
-            Y(2 * k - 1, Vk.x);
-            Y(2 * k, -Vk.y);
-            if (2 * k != M) {
-              Y(2 * (M - k) - 1, Vmk.x);
-              Y(2 * (M - k), -Vmk.y);
+        for (int j = 0; j < E; ++j) {
+          const int k = t + 32 * j;
+          const cplx<T> c = cmul(xtw[M + k], v[LS::sout(j)]);
+          Y(2 * k, (T)2 * c.x);
+          Y(N - 1 - 2 * k, (T)-2 * c.y);
+        }
+      } else {
+        const int pl = (32 - t) & 31;
+        const bool rev = (bc == BC_DD);
+        auto OUTQ = [&](int q, T val) { Y(rev ? (N - 1 - q) : q, val); };
+        // outputs of k (and of M − k unless k = 0 or 2k = M) from Z_k and Z_{M−k}
+        auto pair_out = [&](int k, cplx<T> Zk, cplx<T> Zmk) {
+          const cplx<T> Ek = cscale(cadd(Zk, conj_(Zmk)), (T)0.5);
+          const cplx<T> Ok = cscale(mul_mi(csub(Zk, conj_(Zmk))), (T)0.5);
+          const cplx<T> B = cmul(ptw[k], Ok);
+          const cplx<T> Vk = cadd(Ek, B), Vmk = conj_(csub(Ek, B));
+          if (bc == BC_P) {
+            if (k == 0) {
+              Y(0, Vk.x);
+              Y(N - 1, Vmk.x);
+            } else {
+              Y(2 * k - 1, Vk.x);
+              Y(2 * k, -Vk.y);
+              if (2 * k != M) {
+                Y(2 * (M - k) - 1, Vmk.x);
+                Y(2 * (M - k), -Vmk.y);
+              }
             }
-          }
-        } else {
-          const bool rev = (bc == BC_DD);
-          auto OUTQ = [&](int q, T val) { Y(rev ? (N - 1 - q) : q, val); };
-          if (k == 0) {
+          } else if (k == 0) {
             OUTQ(0, (T)2 * Vk.x);
             OUTQ(M, (T)1.41421356237309504880 * Vmk.x);
           } else {
@@ -185,10 +205,82 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
               OUTQ(M + k, (T)-2 * c2.y);
             }
           }
+        };
+        cplx<T> prev = {(T)0, (T)0};
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) {
+          const cplx<T> Zk = v[LS::sout(j)];
+          const cplx<T> recv = {__shfl_sync(full, v[LS::sout(E - 1 - j)].x, pl),
+                                __shfl_sync(full, v[LS::sout(E - 1 - j)].y, pl)};
+          const cplx<T> Zmk = (t != 0) ? recv : (j == 0 ? Zk : prev);
+          prev = recv;
+          pair_out(t + 32 * j, Zk, Zmk);
+        }
+        if (t == 0) pair_out(M / 2, prev, prev);  // k = M/2 pairs with itself
+      }
+    } else {
+      // ---- post-processing: pairs (k, M−k) through the exchange buffer, scalar stores ----
+      __syncwarp();
+  #pragma unroll
+      for (int q = 0; q < E / RL; ++q)
+  #pragma unroll
+        for (int r = 0; r < RL; ++r) lc[cpad(t + q * TPL + r * (M / RL))] = v[q * RL + r];
+      __syncwarp();
+      auto Y = [&](int i, T val) {
+        if (live) dst[i] = st_cvt<TO, T>::f(val);
+      };
+      if (bc == BC_ND) {
+  #pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int k = t + i * TPL;
+          const cplx<T> c = cmul(xtw[M + k], lc[cpad(k)]);
+          Y(2 * k, (T)2 * c.x);
+          Y(N - 1 - 2 * k, (T)-2 * c.y);
+        }
+      } else {
+        constexpr int NP = (M / 2) / TPL + 1;
+  #pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const int k = t + i * TPL;
+          if (k > M / 2) break;
+          const cplx<T> Zk = lc[cpad(k)], Zmk = lc[cpad(k == 0 ? 0 : M - k)];
+          const cplx<T> Ek = cscale(cadd(Zk, conj_(Zmk)), (T)0.5);
+          const cplx<T> Ok = cscale(mul_mi(csub(Zk, conj_(Zmk))), (T)0.5);
+          const cplx<T> B = cmul(ptw[k], Ok);
+          const cplx<T> Vk = cadd(Ek, B), Vmk = conj_(csub(Ek, B));
+          if (bc == BC_P) {
+            if (k == 0) {
+              Y(0, Vk.x);
+              Y(N - 1, Vmk.x);
+            } else {
+              Y(2 * k - 1, Vk.x);
+              Y(2 * k, -Vk.y);
+              if (2 * k != M) {
+                Y(2 * (M - k) - 1, Vmk.x);
+                Y(2 * (M - k), -Vmk.y);
+              }
+            }
+          } else {
+            const bool rev = (bc == BC_DD);
+            auto OUTQ = [&](int q, T val) { Y(rev ? (N - 1 - q) : q, val); };
+            if (k == 0) {
+              OUTQ(0, (T)2 * Vk.x);
+              OUTQ(M, (T)1.41421356237309504880 * Vmk.x);
+            } else {
+              const cplx<T> c1 = cmul(xtw[k], Vk);
+              OUTQ(k, (T)2 * c1.x);
+              OUTQ(N - k, (T)-2 * c1.y);
+              if (2 * k != M) {
+                const cplx<T> c2 = cmul(xtw[M - k], Vmk);
+                OUTQ(M - k, (T)2 * c2.x);
+                OUTQ(M + k, (T)-2 * c2.y);
+              }
+            }
+          }
         }
       }
+      __syncwarp();  // buffer reads done before the next line overwrites it
     }
-    __syncwarp();  // buffer reads done before the next line overwrites it
   } else {
     // The FP64 output modes read the line's base (FP32 Φ_0) or its accumulator (FP64
     // p) only when the outputs are written; ask L2 for them now, one 128-byte
@@ -202,78 +294,135 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
         for (int j = t; j < SEG; j += TPL) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf + 128 * j));
       }
     }
-    // ---- backward pre-processing: pairs (k, M−k) from the line into the buffer ----
     auto X = [&](int i) { return in_cvt<T>(src[i]); };
-    if (bc == BC_ND) {
-      // (x_{2k}, x_{n−1−2k})·e^{−iπk/n}; x_{n−1−2k} = x_{2k'+1} of k' = M−1−k
+    if constexpr (TPL == 32) {
+      // ---- backward pre-processing in registers: own V_k, V_{M−k} from the partner lane,
+      // Z_k straight into its first-stage slot ----
+      using LS = LaneSlots<M>;
+      if (bc == BC_ND) {
+        // (x_{2k}, x_{n−1−2k})·e^{−iπk/n}; x_{n−1−2k} = x_{2k'+1} of k' = M−1−k (mirrored lane)
+        cplx<T> z[E];
 #pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int k = t + i * TPL;
-        const vec<TI, 2> x = *reinterpret_cast<const vec<TI, 2>*>(src + 2 * k);
-        v[i].x = in_cvt<T>(x.v[0]);
-        v[E - 1 - i].y = __shfl_sync(full, in_cvt<T>(x.v[1]), mate);
-      }
+        for (int i = 0; i < E; ++i) {
+          const int k = t + i * TPL;
+          const vec<TI, 2> x = *reinterpret_cast<const vec<TI, 2>*>(src + 2 * k);
+          z[i].x = in_cvt<T>(x.v[0]);
+          z[E - 1 - i].y = __shfl_sync(full, in_cvt<T>(x.v[1]), mate);
+        }
 #pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int k = t + i * TPL;
-        lc[cpad(k)] = cmul(v[i], xtw[k]);
-      }
-    } else {
-      constexpr int NP = (M / 2) / TPL + 1;
-      T xv[NP][4];
+        for (int j = 0; j < E; ++j) v[LS::sin_(j)] = cmul(z[j], xtw[t + 32 * j]);
+      } else {
+        const bool rev = (bc == BC_DD);
+        auto qx = [&](int q) { return rev ? (N - 1 - q) : q; };
+        cplx<T> Vv[E];
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const int k = t + i * TPL;
-        const bool ok = (i < NP - 1) || (k <= M / 2);
-        int q[4];
-        bool use[4] = {ok, ok, ok, ok};
-        if (bc == BC_P) {
-          q[0] = k == 0 ? 0 : 2 * k - 1;
-          q[1] = 2 * k;
-          q[2] = k == 0 ? N - 1 : 2 * (M - k) - 1;
-          q[3] = 2 * (M - k);
-          use[1] = use[3] = ok && k != 0;
-        } else {
-          const bool rev = (bc == BC_DD);
-          const int qq[4] = {k, N - k, M - k, N - M + k};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            q[u] = rev ? (N - 1 - qq[u]) : qq[u];
-            use[u] = ok && qq[u] < N;
+        for (int j = 0; j < E; ++j) {
+          const int k = t + 32 * j;
+          if (bc == BC_P) {
+            Vv[j] = (k == 0) ? cplx<T>{X(0), (T)0} : cplx<T>{X(2 * k - 1), -X(2 * k)};
+          } else {
+            const T x0 = X(qx(k)), x1 = (k == 0) ? (T)0 : X(qx(N - k));
+            cplx<T> w = xtw[k];
+            w.y = -w.y;
+            Vv[j] = cscale(cmul(w, cplx<T>{x0, -x1}), (T)0.5);
           }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) xv[i][u] = use[u] ? X(q[u]) : (T)0;
-      }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const int k = t + i * TPL;
-        if (i == NP - 1 && k > M / 2) break;
-        cplx<T> Vk, Vm;
+        // V_M, the partner of k = 0 (lane 0)
+        cplx<T> VM;
         if (bc == BC_P) {
-          Vk = {xv[i][0], -xv[i][1]};
-          Vm = {xv[i][2], -xv[i][3]};
+          VM = {X(N - 1), (T)0};
         } else {
-          cplx<T> w = xtw[k];
+          const T xm = X(qx(M));
+          cplx<T> w = xtw[M];
           w.y = -w.y;
-          Vk = cscale(cmul(w, cplx<T>{xv[i][0], -xv[i][1]}), (T)0.5);
-          cplx<T> w2 = xtw[M - k];
-          w2.y = -w2.y;
-          Vm = cscale(cmul(w2, cplx<T>{xv[i][2], -xv[i][3]}), (T)0.5);
+          VM = cscale(cmul(w, cplx<T>{xm, -xm}), (T)0.5);
         }
-        const cplx<T> Ek = cscale(cadd(Vk, conj_(Vm)), (T)0.5);
-        cplx<T> wn = ptw[k];
-        wn.y = -wn.y;
-        const cplx<T> Ok = cscale(cmul(csub(Vk, conj_(Vm)), wn), (T)0.5);
-        if (k < M) lc[cpad(k)] = cadd(Ek, mul_i(Ok));
-        if (k != 0 && 2 * k != M) lc[cpad(M - k)] = cadd(conj_(Ek), mul_i(conj_(Ok)));
+        const int pl = (32 - t) & 31;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int k = t + 32 * j;
+          cplx<T> Vm = {__shfl_sync(full, Vv[E - 1 - j].x, pl), __shfl_sync(full, Vv[E - 1 - j].y, pl)};
+          if (t == 0) Vm = (j == 0) ? VM : Vv[(E - j) % E];
+          const cplx<T> Ek = cscale(cadd(Vv[j], conj_(Vm)), (T)0.5);
+          cplx<T> wn = ptw[k];
+          wn.y = -wn.y;
+          const cplx<T> Ok = cscale(cmul(csub(Vv[j], conj_(Vm)), wn), (T)0.5);
+          v[LS::sin_(j)] = cadd(Ek, mul_i(Ok));
+        }
       }
+    } else {
+      // ---- backward pre-processing: pairs (k, M−k) from the line into the buffer ----
+      if (bc == BC_ND) {
+        // (x_{2k}, x_{n−1−2k})·e^{−iπk/n}; x_{n−1−2k} = x_{2k'+1} of k' = M−1−k
+  #pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int k = t + i * TPL;
+          const vec<TI, 2> x = *reinterpret_cast<const vec<TI, 2>*>(src + 2 * k);
+          v[i].x = in_cvt<T>(x.v[0]);
+          v[E - 1 - i].y = __shfl_sync(full, in_cvt<T>(x.v[1]), mate);
+        }
+  #pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int k = t + i * TPL;
+          lc[cpad(k)] = cmul(v[i], xtw[k]);
+        }
+      } else {
+        constexpr int NP = (M / 2) / TPL + 1;
+        T xv[NP][4];
+  #pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const int k = t + i * TPL;
+          const bool ok = (i < NP - 1) || (k <= M / 2);
+          int q[4];
+          bool use[4] = {ok, ok, ok, ok};
+          if (bc == BC_P) {
+            q[0] = k == 0 ? 0 : 2 * k - 1;
+            q[1] = 2 * k;
+            q[2] = k == 0 ? N - 1 : 2 * (M - k) - 1;
+            q[3] = 2 * (M - k);
+            use[1] = use[3] = ok && k != 0;
+          } else {
+            const bool rev = (bc == BC_DD);
+            const int qq[4] = {k, N - k, M - k, N - M + k};
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              q[u] = rev ? (N - 1 - qq[u]) : qq[u];
+              use[u] = ok && qq[u] < N;
+            }
+          }
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) xv[i][u] = use[u] ? X(q[u]) : (T)0;
+        }
+  #pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const int k = t + i * TPL;
+          if (i == NP - 1 && k > M / 2) break;
+          cplx<T> Vk, Vm;
+          if (bc == BC_P) {
+            Vk = {xv[i][0], -xv[i][1]};
+            Vm = {xv[i][2], -xv[i][3]};
+          } else {
+            cplx<T> w = xtw[k];
+            w.y = -w.y;
+            Vk = cscale(cmul(w, cplx<T>{xv[i][0], -xv[i][1]}), (T)0.5);
+            cplx<T> w2 = xtw[M - k];
+            w2.y = -w2.y;
+            Vm = cscale(cmul(w2, cplx<T>{xv[i][2], -xv[i][3]}), (T)0.5);
+          }
+          const cplx<T> Ek = cscale(cadd(Vk, conj_(Vm)), (T)0.5);
+          cplx<T> wn = ptw[k];
+          wn.y = -wn.y;
+          const cplx<T> Ok = cscale(cmul(csub(Vk, conj_(Vm)), wn), (T)0.5);
+          if (k < M) lc[cpad(k)] = cadd(Ek, mul_i(Ok));
+          if (k != 0 && 2 * k != M) lc[cpad(M - k)] = cadd(conj_(Ek), mul_i(conj_(Ok)));
+        }
+      }
+      __syncwarp();
+  #pragma unroll
+      for (int q = 0; q < E / R0; ++q)
+  #pragma unroll
+        for (int r = 0; r < R0; ++r) v[q * R0 + r] = lc[cpad(t + q * TPL + r * (M / R0))];
     }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < E / R0; ++q)
-#pragma unroll
-      for (int r = 0; r < R0; ++r) v[q * R0 + r] = lc[cpad(t + q * TPL + r * (M / R0))];
     if (bc == BC_ND) fast::fft_stages<T, M, false, 0, 1>(v, lc, stw, t);
     else fast::fft_stages<T, M, true, 0, 1>(v, lc, stw, t);
     __syncwarp();  // the last stage's buffer reads are done before the next line
