@@ -141,6 +141,14 @@ __device__ void zlow_column(const ZArgs<float>& a, int t) {
   }
 }
 
+// 1/x by the hardware approximation (`rcp.approx.ftz.f32`, about 1 ulp): the pivots
+// here are normal FP32 numbers far from the overflow range.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <bool TAB>
 __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlowb) {
   if (a.skip && *a.skip) return;
@@ -183,7 +191,7 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlo
       const int k = k0 + u;
       if (FULL || k < nz) {
         const float4 q = coef(k);
-        const float mk = __fdividef(1.f, q.y + lam - q.x * cp);
+        const float mk = rcp_approx(q.y + lam - q.x * cp);
         cp = q.z * mk;
         dp = (cur[u] - q.x * dp) * mk;
       }
@@ -243,7 +251,7 @@ __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlo
     for (int u = ZK - 1; u >= 0; --u) {
       const int k = k0 + u;
       if (c < nfull || k < nz) {
-        x = dpa[u] - ((k < nz - 1) ? cpa[u] : 0.f) * x;
+        x = dpa[u] - cpa[u] * x;  // c'_{n−1} = 0: the table holds c_{n−1} = 0
         if (act) dst[(size_t)u * st] = x;
       }
     }
