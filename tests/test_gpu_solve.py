@@ -219,6 +219,31 @@ def test_refine_long_lines(lib, shape, bcs):
     assert _relerr(p, q) <= 1e-8
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-8)])
+def test_solve_from_host_buffers(lib, precision, tol):
+    """ps_solve_host: the copies in and out inside the call, the same bits as the
+    device-buffer call, the oracle's solution."""
+    import torch
+    nz, ny, nx = 12, 24, 32
+    bcs = ("P", "NN", "DD")
+    zf = synth.tanh_faces(nz, 1.0, 1.5)
+    f = np.random.default_rng(21).uniform(-1, 1, (nz, ny, nx))
+    plan = lib.Plan(nx, ny, nz, 1.0 / nx, 1.0 / ny, zf=zf, bcs=bcs, precision=precision,
+                    rtol=1e-10, max_iter=6)
+    fh = torch.from_numpy(f.copy()).pin_memory()
+    ph = torch.zeros_like(fh).pin_memory()
+    fd = torch.empty(f.shape, dtype=torch.float64, device="cuda")
+    pd = torch.empty_like(fd)
+    info = plan.solve_host(fh, ph, fd, pd)
+    assert info.status == 0, info.status
+    p_dev = plan.solve(torch.as_tensor(f, device="cuda").contiguous())
+    torch.cuda.synchronize()
+    plan.close()
+    assert np.array_equal(ph.numpy(), p_dev.cpu().numpy())
+    q = S.solve(f, 1.0 / nx, 1.0 / ny, zf, *bcs)
+    assert _relerr(ph.numpy(), q) <= tol
+
+
 REPORTED = [
     ("rough", (32, 48, 64), ("P", "P", "NN")),
     ("rough", (24, 32, 32), ("DD", "ND", "DD")),
