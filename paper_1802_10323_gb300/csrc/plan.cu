@@ -123,8 +123,21 @@ struct Prof {
   std::vector<int> kind;
 };
 
+// ps_solve_host with refinement: the copy of f overlaps the first solve's x and y
+// passes (per chunk of planes), the copy of p the passes after the first correction.
+constexpr int kPipeMax = 8;
+struct HostPipe {
+  int nch = 0;
+  int z[kPipeMax + 1] = {};
+  cudaEvent_t in[kPipeMax] = {};   // chunk c of f is on the device
+  cudaEvent_t out[kPipeMax] = {};  // chunk c of p = Φ_0 + e written by the first correction
+  bool p_recorded = false;
+};
+
 struct ps_plan {
   Prof prof;
+  cudaStream_t copy_stream = nullptr;          // ps_solve_host: host <-> device copies
+  cudaEvent_t pipe_ev[2 * kPipeMax + 1] = {};  // chunks of f in, chunks of p ready, call start
   int nx, ny, nz;
   double dx, dy;
   int bcx, bcy, bcz;
@@ -268,7 +281,7 @@ template <class T, class TI, class TO, bool FWD>
 cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, const T* scale,
                        int accumulate, const int* skip, cudaStream_t st,
                        unsigned long long* amax = nullptr, float* out2 = nullptr,
-                       const float* base32 = nullptr) {
+                       const float* base32 = nullptr, int zn = 0) {
   const AxisTab& t = axis == 0 ? p->ax : p->ay;
   const int lpc_y = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
   const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) &&
@@ -283,6 +296,10 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
     a.nz = p->nz;
     a.bc = t.bc;
     a.nlines = (axis == 0) ? p->ny * p->nz : p->nx * p->nz;
+    if (zn > 0) {  // the planes at in/out only (the caller offsets the pointers)
+      a.nz = zn;
+      a.nlines = (axis == 0) ? p->ny * zn : p->nx * zn;
+    }
     if constexpr (sizeof(T) == 8) a.tw = reinterpret_cast<const cplx<T>*>(t.tw64);
     else a.tw = reinterpret_cast<const cplx<T>*>(t.tw32);
     a.plane_scale = scale;
@@ -374,7 +391,7 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
 
 // FP32 bulk solve with FP64 iterative refinement (residual in double-float).
 ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaStream_t st,
-                       ps_info* info) {
+                       ps_info* info, HostPipe* hp = nullptr) {
   const WsLayout L = ws_layout(pl);
   char* wb = static_cast<char*>(ws);
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(wb + L.ctrl);
@@ -395,12 +412,30 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   auto correction = [&](int c) -> cudaError_t {
     const bool first = (c == 0);
     cudaError_t r;
-    if (first)
-      r = run(pl, K_XF64IN, st, [&] { return line_xform<float, double, float, true>(pl, 0, f, w, nullptr, 0, skip, st); });
-    else
-      r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, rh, w, nullptr, 0, skip, st); });
-    if (r != cudaSuccess) return r;
-    if ((r = run(pl, K_YF, st, [&] { return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
+    if (first && hp) {  // f arrives in chunks of planes: x and y of each chunk as it lands
+      for (int ch = 0; ch < hp->nch; ++ch) {
+        const int zn = hp->z[ch + 1] - hp->z[ch];
+        const size_t off = (size_t)hp->z[ch] * pl->nx * pl->ny;
+        if ((r = cudaStreamWaitEvent(st, hp->in[ch], 0)) != cudaSuccess) return r;
+        if ((r = run(pl, K_XF64IN, st, [&] {
+               return line_xform<float, double, float, true>(pl, 0, f + off, w + off, nullptr, 0, skip, st,
+                                                             nullptr, nullptr, nullptr, zn);
+             })) != cudaSuccess)
+          return r;
+        if ((r = run(pl, K_YF, st, [&] {
+               return line_xform<float, float, float, true>(pl, 1, w + off, w + off, nullptr, 0, skip, st,
+                                                            nullptr, nullptr, nullptr, zn);
+             })) != cudaSuccess)
+          return r;
+      }
+    } else {
+      if (first)
+        r = run(pl, K_XF64IN, st, [&] { return line_xform<float, double, float, true>(pl, 0, f, w, nullptr, 0, skip, st); });
+      else
+        r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, rh, w, nullptr, 0, skip, st); });
+      if (r != cudaSuccess) return r;
+      if ((r = run(pl, K_YF, st, [&] { return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
+    }
     if ((r = run(pl, K_Z, st, [&] {
            return pl->periodic_z ? launch_zsolve<float>(zw, st) : launch_zsolve_ckpt(zw, st);
          })) != cudaSuccess)
@@ -412,6 +447,20 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       return run(pl, K_XB64ST, st, [&] {
         return line_xform<float, float, double, false>(pl, 0, w, nullptr, nullptr, 0, skip, st, &ctrl->pmax, u0);
       });
+    if (hp && c == 1) {  // p is final here unless a later correction runs: chunk by chunk
+      for (int ch = 0; ch < hp->nch; ++ch) {
+        const int zn = hp->z[ch + 1] - hp->z[ch];
+        const size_t off = (size_t)hp->z[ch] * pl->nx * pl->ny;
+        if ((r = run(pl, K_XB64BASE, st, [&] {
+               return line_xform<float, float, double, false>(pl, 0, w + off, p + off, nullptr, 0, skip, st,
+                                                              &ctrl->dmax, w + off, u0 + off, zn);
+             })) != cudaSuccess)
+          return r;
+        if ((r = cudaEventRecord(hp->out[ch], st)) != cudaSuccess) return r;
+      }
+      hp->p_recorded = true;
+      return cudaSuccess;
+    }
     return run(pl, c == 1 ? K_XB64BASE : K_XB64ACC, st, [&] {
       return line_xform<float, float, double, false>(pl, 0, w, p, nullptr, c == 1 ? 0 : 1, skip, st, &ctrl->dmax,
                                                      w, c == 1 ? u0 : nullptr);
@@ -805,7 +854,71 @@ ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, dou
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = plan->N * sizeof(double);
   ps_info* info_dev = reinterpret_cast<ps_info*>(static_cast<char*>(ws) + ws_layout(plan).info);
-  cudaError_t e = cudaMemcpyAsync(f_dev, f_host, bytes, cudaMemcpyHostToDevice, st);
+  cudaError_t e;
+  // Refinement with the register-resident x and y kernels: the copy of f in chunks
+  // of planes on a side stream, each chunk's first x and y passes as it lands; the
+  // copy of each chunk of p as soon as the first correction's x pass has written it
+  // (overlapping the rest of that pass and of the loop), and p again after the loop
+  // if a later correction changed it.
+  const bool pipe = plan->prec == PS_FP32_REFINE && f_dev != p_dev && plan->nz >= 2 &&
+                    plan->nx % 16 == 0 && (plan->ax.m >= 64 && plan->ax.m <= 512) &&
+                    (plan->ay.m >= 64 && plan->ay.m <= 512) && !(plan->ax.m & (plan->ax.m - 1)) &&
+                    !(plan->ay.m & (plan->ay.m - 1));
+  if (pipe) {
+    if (!plan->copy_stream) {
+      if ((e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(plan, e, "copy stream");
+      for (auto& ev : plan->pipe_ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(plan, e, "copy events");
+    }
+    cudaStream_t cs = plan->copy_stream;
+    HostPipe hp;
+    hp.nch = plan->nz < kPipeMax ? plan->nz : kPipeMax;
+    for (int c = 0; c <= hp.nch; ++c) hp.z[c] = (int)((long long)plan->nz * c / hp.nch);
+    for (int c = 0; c < hp.nch; ++c) {
+      hp.in[c] = plan->pipe_ev[c];
+      hp.out[c] = plan->pipe_ev[kPipeMax + c];
+    }
+    cudaEvent_t start = plan->pipe_ev[2 * kPipeMax];
+    // the copies wait for the caller's earlier work on its stream (which may use f_dev)
+    if ((e = cudaEventRecord(start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, start, 0)) != cudaSuccess)
+      return cuda_fail(plan, e, "copy stream order");
+    const size_t plane = (size_t)plan->nx * plan->ny;
+    for (int c = 0; c < hp.nch; ++c) {
+      const size_t off = (size_t)hp.z[c] * plane, n = (size_t)(hp.z[c + 1] - hp.z[c]) * plane;
+      if ((e = cudaMemcpyAsync(f_dev + off, f_host + off, n * sizeof(double), cudaMemcpyHostToDevice, cs)) !=
+              cudaSuccess ||
+          (e = cudaEventRecord(hp.in[c], cs)) != cudaSuccess)
+        return cuda_fail(plan, e, "host to device copy");
+    }
+    s = solve_refine(plan, f_dev, p_dev, ws, st, info_dev, &hp);
+    if (s != PS_OK) {
+      cudaStreamSynchronize(cs);
+      return s;
+    }
+    for (int c = 0; hp.p_recorded && c < hp.nch; ++c) {
+      const size_t off = (size_t)hp.z[c] * plane, n = (size_t)(hp.z[c + 1] - hp.z[c]) * plane;
+      if ((e = cudaStreamWaitEvent(cs, hp.out[c], 0)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(p_host + off, p_dev + off, n * sizeof(double), cudaMemcpyDeviceToHost, cs)) !=
+              cudaSuccess)
+        return cuda_fail(plan, e, "device to host copy");
+    }
+    ps_info rec{};
+    if ((e = cudaMemcpyAsync(&rec, info_dev, sizeof(ps_info), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(plan, e, "info copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess || (e = cudaStreamSynchronize(cs)) != cudaSuccess)
+      return cuda_fail(plan, e, "stream synchronize");
+    // p changed after the early copy unless the loop stopped at the first correction
+    if (!hp.p_recorded || rec.iterations != 1) {
+      if ((e = cudaMemcpyAsync(p_host, p_dev, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(plan, e, "device to host copy");
+    }
+    if (info_host) *info_host = rec;
+    return PS_OK;
+  }
+  e = cudaMemcpyAsync(f_dev, f_host, bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(plan, e, "host to device copy");
   s = ps_solve(plan, f_dev, p_dev, ws, stream, info_dev);
   if (s != PS_OK) return s;
@@ -917,6 +1030,9 @@ ps_status ps_div_adjoint_correct(ps_plan* plan, const void* g, const void* s, vo
 ps_status ps_plan_destroy(ps_plan* plan) {
   if (!plan) return PS_OK;
   for (auto& ev : plan->prof.ev) cudaEventDestroy(ev);
+  for (auto& ev : plan->pipe_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (plan->copy_stream) cudaStreamDestroy(plan->copy_stream);
   if (plan->dev) cudaFree(plan->dev);
   delete plan;
   return PS_OK;

@@ -219,29 +219,43 @@ def test_refine_long_lines(lib, shape, bcs):
     assert _relerr(p, q) <= 1e-8
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-8)])
-def test_solve_from_host_buffers(lib, precision, tol):
-    """ps_solve_host: the copies in and out inside the call, the same bits as the
-    device-buffer call, the oracle's solution."""
+HOST = [((12, 24, 32), "fp64", 1e-10, 6), ((12, 24, 32), "fp32_refine", 1e-10, 6),
+        ((6, 128, 128), "fp32_refine", 1e-10, 6),   # copies overlapped with the first/last passes
+        ((6, 128, 128), "fp32_refine", 1e-10, 0),   # loop ends at pass 0: p copied again
+        ((6, 128, 128), "fp32_refine", 1e-13, 8)]   # several corrections: p copied again
+
+
+@pytest.mark.parametrize("shape,precision,rtol,max_iter", HOST,
+                         ids=[f"{'x'.join(map(str, s))}-{p}-{r:g}-{m}" for s, p, r, m in HOST])
+def test_solve_from_host_buffers(lib, shape, precision, rtol, max_iter):
+    """ps_solve_host: the copies in and out inside the call (overlapped with the first and
+    last passes for refinement with the register-resident kernels), the same bits and
+    the same status as the device-buffer call, and the oracle's solution."""
     import torch
-    nz, ny, nx = 12, 24, 32
+    nz, ny, nx = shape
     bcs = ("P", "NN", "DD")
     zf = synth.tanh_faces(nz, 1.0, 1.5)
-    f = np.random.default_rng(21).uniform(-1, 1, (nz, ny, nx))
+    f = np.random.default_rng(21).uniform(-1, 1, shape)
     plan = lib.Plan(nx, ny, nz, 1.0 / nx, 1.0 / ny, zf=zf, bcs=bcs, precision=precision,
-                    rtol=1e-10, max_iter=6)
+                    rtol=rtol, max_iter=max_iter)
     fh = torch.from_numpy(f.copy()).pin_memory()
     ph = torch.zeros_like(fh).pin_memory()
-    fd = torch.empty(f.shape, dtype=torch.float64, device="cuda")
+    fd = torch.empty(shape, dtype=torch.float64, device="cuda")
     pd = torch.empty_like(fd)
-    info = plan.solve_host(fh, ph, fd, pd)
-    assert info.status == 0, info.status
-    p_dev = plan.solve(torch.as_tensor(f, device="cuda").contiguous())
+    info_h = plan.solve_host(fh, ph, fd, pd)
+    info = lib.info_tensor()
+    p_dev = plan.solve(torch.as_tensor(f, device="cuda").contiguous(), info=info)
     torch.cuda.synchronize()
+    info_d = lib.read_info(info)
     plan.close()
+    assert (info_h.status, info_h.iterations) == (info_d.status, info_d.iterations)
     assert np.array_equal(ph.numpy(), p_dev.cpu().numpy())
+    if max_iter == 0:
+        assert info_h.iterations == 0
+    if rtol < 1e-12:
+        assert info_h.iterations >= 2
     q = S.solve(f, 1.0 / nx, 1.0 / ny, zf, *bcs)
-    assert _relerr(ph.numpy(), q) <= tol
+    assert _relerr(ph.numpy(), q) <= (1e-12 if precision == "fp64" else (1e-5 if max_iter == 0 else 1e-8))
 
 
 REPORTED = [
