@@ -648,13 +648,13 @@ ps_status ps_batch_autotune(ps_batch* b, double* const* f_dev, double* const* p_
       fclose(fp);
     }
   }
-  const int cands[3] = {1, 2, 4};
+  const int cands[5] = {1, 2, 4, 8, 16};
   double best = 1e300;
   int best_scale = b->scale;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int ci = 0; ci < 3; ++ci) {
+  for (int ci = 0; ci < (int)(sizeof(cands) / sizeof(cands[0])); ++ci) {
     b->scale = cands[ci];
     ps_status s2 = build_tables(b);
     if (s2 != PS_OK) continue;
