@@ -48,6 +48,19 @@ constexpr int ZTAB_MAX = 4096;     // planes whose coefficient table fits in sha
 // the same launch as the FP32 columns, so they overlap them. Output rounded to FP32.
 constexpr int ZL = 4;  // rows in flight per FP64 column (keeps the kernel's registers at the FP32 path's)
 
+// 1/x in FP64 for those columns: the hardware approximation refined by two
+// Newton–Raphson steps r ← r + r·(1 − x·r) (each roughly doubles the correct bits),
+// well below the FP32 rounding of the result; an IEEE FP64 division costs several
+// times more on the FP64 pipe.
+__device__ __forceinline__ double rcp_newton(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 __device__ void zlow_column(const ZArgs<float>& a, int t) {
   const int nrect = a.lowx * a.lowy;
   if (t >= nrect) return;
@@ -85,7 +98,7 @@ __device__ void zlow_column(const ZArgs<float>& a, int t) {
       if (k >= kb && k < nz) {
         const double ak = (k > kb) ? __ldg(a.za64 + k) : 0.0;
         const double ck = (k < nz - 1) ? __ldg(a.zc64 + k) : 0.0;
-        const double mk = 1.0 / (__ldg(a.zb64 + k) + (sing ? 0.0 : lam) - ak * cp);
+        const double mk = rcp_newton(__ldg(a.zb64 + k) + (sing ? 0.0 : lam) - ak * cp);
         cp = ck * mk;
         dp = (((double)cur[u] - mean) - ak * dp) * mk;
         cs[(size_t)k * nrect] = cp;
