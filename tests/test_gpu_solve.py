@@ -286,3 +286,33 @@ def test_refine_reported_residual_is_the_solution_residual(lib, kind, shape, bcs
     rr = O.relative_residual(p, f, lx / nx, ly / ny, zf, *bcs)
     assert info.status == (0 if rr <= 1e-10 else 5), (info.status, info.rel_residual, rr)
     assert abs(info.rel_residual - rr) <= 1e-11, (info.rel_residual, rr)
+
+
+# Long z columns (n_z from 64 to 1040) for the FP32 z solve: ragged last chunks of
+# the checkpointed elimination (n_z not a multiple of 16), column counts that leave a
+# partial CTA, and the FP64 low-wavenumber rectangle solved beside the FP32 columns.
+# The domain is narrow in x and y (0.05 × 0.05 × 1) so that every column with
+# κ > 10^4 lies in the FP64 rectangle (with few columns on a wide domain nearly all
+# would, and the rectangle is capped at 1/8 of them).
+ZPART = [((64, 24, 32), ("P", "P", "NN")), ((65, 12, 6), ("DD", "NN", "DD")),
+         ((200, 16, 24), ("NN", "DD", "ND")), ((1040, 8, 6), ("P", "NN", "NN")),
+         ((1024, 12, 6), ("ND", "P", "DD")), ((1023, 8, 12), ("NN", "NN", "ND"))]
+
+
+@pytest.mark.parametrize("shape,bcs", ZPART, ids=["x".join(map(str, s)) + "-" + "-".join(b) for s, b in ZPART])
+def test_fp32_and_refine_long_z_columns(lib, shape, bcs):
+    nz, ny, nx = shape
+    lx, ly = 0.05, 0.05
+    zf = synth.tanh_faces(nz, 1.0, 1.5)
+    f = np.random.default_rng(nz + nx).uniform(-1, 1, shape)
+    q = S.solve(f, lx / nx, ly / ny, zf, *bcs)
+    p32, _ = _run(lib, f, lx / nx, ly / ny, zf, bcs, precision="fp32")
+    # FP32 columns have κ ≤ 10^4 (the rest are solved in FP64), so an elimination
+    # in FP32 errs by up to ~κ·ε_32 relative to its column; 1e-4 of ‖p‖∞ still
+    # fails any wrong coupling between blocks by orders of magnitude
+    assert _relerr(p32, q) <= 1e-4
+    p, info = _run(lib, f, lx / nx, ly / ny, zf, bcs, precision="fp32_refine", rtol=1e-10, max_iter=6)
+    assert info.status == 0 and info.rel_residual <= 1e-10, (info.status, info.rel_residual)
+    rr = O.relative_residual(p, f, lx / nx, ly / ny, zf, *bcs)
+    assert rr <= 1e-10 and abs(info.rel_residual - rr) <= 1e-11, (info.rel_residual, rr)
+    assert _relerr(p, q) <= 1e-8
