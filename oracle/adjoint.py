@@ -29,11 +29,11 @@ from .operator import metrics, uniform_faces
 from .solve import solve
 
 
-def solve_transpose(g, dx, dy, zf, bcx, bcy, bcz):
-    """Mᵀ g = W · M(W⁻¹ g), W = diag(Δz^f) along z."""
+def solve_transpose(g, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
+    """Mᵀ g = W · M(W⁻¹ g), W = diag(Δz^f) along z (A − α = W⁻¹(S − αW), S − αW symmetric)."""
     dzf, _ = metrics(zf)
     w = dzf[:, None, None]
-    return w * solve(g / w, dx, dy, zf, bcx, bcy, bcz)
+    return w * solve(g / w, dx, dy, zf, bcx, bcy, bcz, alpha)
 
 
 def _check(bcs):

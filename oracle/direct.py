@@ -20,13 +20,13 @@ import scipy.sparse.linalg as spla
 from .operator import operator_3d, is_singular, cell_volumes
 
 
-def solve_direct(f, dx, dy, zf, bcx, bcy, bcz, dense=False):
+def solve_direct(f, dx, dy, zf, bcx, bcy, bcz, dense=False, alpha=0.0):
     f = np.asarray(f, dtype=np.float64)
     nz, ny, nx = f.shape
-    A = operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz)
+    A = operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz, alpha)
     rhs = f.ravel()
     N = rhs.size
-    if is_singular(bcx, bcy, bcz):
+    if is_singular(bcx, bcy, bcz, alpha):
         v = np.ascontiguousarray(cell_volumes(nx, ny, dx, dy, zf)).ravel()
         A = sp.bmat([[A, sp.csr_matrix(np.ones((N, 1)))],
                      [sp.csr_matrix(v[None, :]), None]]).tocsr()

@@ -23,6 +23,11 @@ Readings (the paper gives the uniform stencil only):
 
 ``operator_1d`` and ``apply`` are two separate codings of these rules (a matrix
 assembled row by row, and a padded-array stencil); tests check they agree.
+
+Helmholtz variant (§2: an implicit diffusion step needs one Helmholtz equation
+per velocity component; §4: done with the same method): the operator of Eq. 4
+minus α times the identity, α ≥ 0 (``alpha``; α = 0 is the Poisson problem).
+For α > 0 the constants leave the null space, so no problem is singular.
 """
 
 import numpy as np
@@ -82,8 +87,8 @@ def operator_1d(bc, faces):
     return L
 
 
-def operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz):
-    """Sparse (CSR) N×N matrix of Eq. 4 on the [n_z][n_y][n_x] grid."""
+def operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
+    """Sparse (CSR) N×N matrix of Eq. 4 (minus α·I) on the [n_z][n_y][n_x] grid."""
     zf = np.asarray(zf, dtype=np.float64)
     nz = len(zf) - 1
     Lx = sp.csr_matrix(operator_1d(bcx, uniform_faces(nx, dx)))
@@ -91,6 +96,8 @@ def operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz):
     Lz = sp.csr_matrix(operator_1d(bcz, zf))
     Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
     A = sp.kron(Lz, sp.kron(Iy, Ix)) + sp.kron(Iz, sp.kron(Ly, Ix)) + sp.kron(Iz, sp.kron(Iy, Lx))
+    if alpha:
+        A = A - alpha * sp.identity(nx * ny * nz)
     return A.tocsr()
 
 
@@ -114,18 +121,19 @@ def _axis_term(p, axis, faces, bc):
     return np.moveaxis(term, 0, axis)
 
 
-def apply(p, dx, dy, zf, bcx, bcy, bcz):
-    """A·p for a [n_z][n_y][n_x] FP64 array (stencil form of Eq. 4)."""
+def apply(p, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
+    """A·p − α·p for a [n_z][n_y][n_x] FP64 array (stencil form of Eq. 4)."""
     p = np.asarray(p, dtype=np.float64)
     nz, ny, nx = p.shape
-    return (_axis_term(p, 2, uniform_faces(nx, dx), bcx)
-            + _axis_term(p, 1, uniform_faces(ny, dy), bcy)
-            + _axis_term(p, 0, np.asarray(zf, dtype=np.float64), bcz))
+    ap = (_axis_term(p, 2, uniform_faces(nx, dx), bcx)
+          + _axis_term(p, 1, uniform_faces(ny, dy), bcy)
+          + _axis_term(p, 0, np.asarray(zf, dtype=np.float64), bcz))
+    return ap - alpha * p if alpha else ap
 
 
-def is_singular(bcx, bcy, bcz):
-    """True when the constant is in the null space: every axis P or NN."""
-    return all(b in ("P", "NN") for b in (bcx, bcy, bcz))
+def is_singular(bcx, bcy, bcz, alpha=0.0):
+    """True when the constant is in the null space: every axis P or NN, and α = 0."""
+    return alpha == 0 and all(b in ("P", "NN") for b in (bcx, bcy, bcz))
 
 
 def cell_volumes(nx, ny, dx, dy, zf):
@@ -134,17 +142,17 @@ def cell_volumes(nx, ny, dx, dy, zf):
     return np.broadcast_to((dx * dy * dzf)[:, None, None], (len(dzf), ny, nx))
 
 
-def compatible_part(f, dx, dy, zf, bcx, bcy, bcz):
+def compatible_part(f, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
     """f with its volume-weighted mean removed when the operator is singular."""
-    if not is_singular(bcx, bcy, bcz):
+    if not is_singular(bcx, bcy, bcz, alpha):
         return np.array(f, dtype=np.float64, copy=True)
     nz, ny, nx = f.shape
     v = cell_volumes(nx, ny, dx, dy, zf)
     return f - (v * f).sum() / v.sum()
 
 
-def relative_residual(p, f, dx, dy, zf, bcx, bcy, bcz):
-    """‖f_c − A p‖∞ / ‖f_c‖∞ with f_c the compatible part of f."""
-    fc = compatible_part(f, dx, dy, zf, bcx, bcy, bcz)
-    r = fc - apply(p, dx, dy, zf, bcx, bcy, bcz)
+def relative_residual(p, f, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
+    """‖f_c − (A − α) p‖∞ / ‖f_c‖∞ with f_c the compatible part of f."""
+    fc = compatible_part(f, dx, dy, zf, bcx, bcy, bcz, alpha)
+    r = fc - apply(p, dx, dy, zf, bcx, bcy, bcz, alpha)
     return np.abs(r).max() / np.abs(fc).max()

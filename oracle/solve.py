@@ -18,6 +18,10 @@ the incompatible part), solve that column with Φ̂_0 = 0 pinned (row 0
 dropped; it is implied by the others for a compatible right-hand side), then
 subtract the Δz^f-weighted mean of the column. The result solves A p = f_c
 (f_c = f minus its volume-weighted mean) with zero volume-weighted mean of p.
+
+Helmholtz variant (``alpha`` = α ≥ 0, see ``oracle.operator``): the transforms
+diagonalise the identity as well, so α only moves every diagonal of Eq. 5 by −α;
+for α > 0 no column is singular.
 """
 
 import numpy as np
@@ -102,13 +106,14 @@ def solve_columns(fh, lam, zf, bcz, singular):
     return ph
 
 
-def solve(f, dx, dy, zf, bcx, bcy, bcz):
-    """Φ with A Φ = f (f_c for singular problems), A the operator of Eq. 4."""
+def solve(f, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
+    """Φ with (A − α) Φ = f (f_c for singular problems), A the operator of Eq. 4."""
     f = np.asarray(f, dtype=np.float64)
     nz, ny, nx = f.shape
     zf = np.asarray(zf, dtype=np.float64)
     if len(zf) != nz + 1:
         raise ValueError("zf must hold n_z + 1 face coordinates")
     fh = forward_xy(f, bcx, bcy)
-    ph = solve_columns(fh, shifts(nx, ny, dx, dy, bcx, bcy), zf, bcz, is_singular(bcx, bcy, bcz))
+    lam = shifts(nx, ny, dx, dy, bcx, bcy) - alpha
+    ph = solve_columns(fh, lam, zf, bcz, is_singular(bcx, bcy, bcz, alpha))
     return backward_xy(ph, bcx, bcy)

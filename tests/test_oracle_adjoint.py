@@ -88,3 +88,19 @@ def test_projection_vjp_dot_product_and_fd():
           - (AD.project(u - h * d, 0.25, 0.25, zf, *bcs) * g).sum()) / (2 * h)
     an = (AD.project_vjp(g, 0.25, 0.25, zf, *bcs) * d).sum()
     assert abs(fd - an) < 1e-6 * abs(an)
+
+
+@pytest.mark.parametrize("bcs", [("P", "P", "NN"), ("DD", "ND", "NN")])
+def test_helmholtz_transpose_solve_is_explicit_transpose(bcs):
+    """A − α = W⁻¹(S − αW) with S − αW symmetric: the same W·M·W⁻¹ rule holds."""
+    zf = synth.tanh_faces(4, 1.0, 1.5)
+    nz, ny, nx, alpha = 4, 2, 4, 6.0
+    N = nx * ny * nz
+    M = np.zeros((N, N))
+    for c in range(N):
+        e = np.zeros(N)
+        e[c] = 1.0
+        M[:, c] = S.solve(e.reshape(nz, ny, nx), 0.3, 0.6, zf, *bcs, alpha=alpha).ravel()
+    g = np.random.default_rng(1).standard_normal((nz, ny, nx))
+    got = AD.solve_transpose(g, 0.3, 0.6, zf, *bcs, alpha=alpha)
+    assert np.abs(got.ravel() - M.T @ g.ravel()).max() < 1e-12 * np.abs(M).max() * np.abs(g).max() * 10

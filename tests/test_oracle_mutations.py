@@ -38,6 +38,14 @@ def _pins_fail():
         q = D.solve_direct(f, 0.3, 0.7, zf, *bcs, dense=True)
         if not np.all(np.isfinite(p)) or np.abs(p - q).max() > 1e-10 * np.abs(q).max():
             return True
+    for bcs in (("P", "NN", "NN"), ("DD", "P", "ND")):  # Helmholtz: α > 0
+        f = rng.uniform(-1, 1, (6, 4, 8)) + 0.3
+        p = S.solve(f, 0.3, 0.7, zf, *bcs, alpha=2.5)
+        q = D.solve_direct(f, 0.3, 0.7, zf, *bcs, dense=True, alpha=2.5)
+        if not np.all(np.isfinite(p)) or np.abs(p - q).max() > 1e-10 * np.abs(q).max():
+            return True
+        if np.abs(O.apply(p, 0.3, 0.7, zf, *bcs, alpha=2.5) - f).max() > 1e-10 * np.abs(f).max():
+            return True
     from fractions import Fraction
     exp = {"NN": "-2/3 2/3 0 1/3 -8/15 1/5 0 2/15 -2/15", "DD": "-8/3 2/3 0 1/3 -8/15 1/5 0 2/15 -16/45"}
     for bc, row in exp.items():
@@ -104,6 +112,24 @@ def _swap_metric(orig):
     return f
 
 
+def _flip_alpha(orig):
+    def f(nx, ny, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
+        return orig(nx, ny, dx, dy, zf, bcx, bcy, bcz, -alpha)
+    return f
+
+
+def _drop_alpha(orig):
+    def f(p, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
+        return orig(p, dx, dy, zf, bcx, bcy, bcz, 0.0)
+    return f
+
+
+def _singular_ignores_alpha(orig):
+    def f(bcx, bcy, bcz, alpha=0.0):
+        return orig(bcx, bcy, bcz, 0.0)
+    return f
+
+
 MUTATIONS = [
     ("transposed forward matrix", T, "forward_matrix", _transposed_forward),
     ("wrong sign of periodic sine rows", T, "backward_matrix", _flip_sin_rows),
@@ -112,6 +138,9 @@ MUTATIONS = [
     ("perturbed back substitution", S, "thomas", _wrong_backsub),
     ("singular column mean not removed", S, "_singular_column", _no_mean_removal),
     ("reversed cell widths", O, "metrics", _swap_metric),
+    ("Helmholtz shift with the wrong sign in the assembled operator", O, "operator_3d", _flip_alpha),
+    ("Helmholtz shift dropped from the stencil", O, "apply", _drop_alpha),
+    ("singular-mode treatment kept for a Helmholtz shift", O, "is_singular", _singular_ignores_alpha),
 ]
 
 

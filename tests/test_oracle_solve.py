@@ -164,3 +164,55 @@ def test_golden_nonuniform_operator():
             M[0, 2] += a[0]
             M[2, 0] += c[2]
         assert np.abs(M - expect).max() < 1e-15, bc
+
+
+# ---- Helmholtz variant: (A − α) p = f, α > 0 (§2: implicit diffusion; §4) ----
+
+HELM = [("P", "P", "NN"), ("NN", "NN", "NN"), ("P", "P", "P"), ("DD", "ND", "P"), ("ND", "NN", "DD")]
+
+
+@pytest.mark.parametrize("alpha", [0.37, 25.0])
+@pytest.mark.parametrize("bcs", HELM, ids=["-".join(b) for b in HELM])
+def test_helmholtz_eigen_solve_equals_dense_lu(bcs, alpha):
+    """The shift enters the eigen-expansion as −α on every Eq. 5 diagonal and the
+    assembled matrix as −α·I: two codings that must agree. With α > 0 the all-P/NN
+    triples are regular: the LU is unbordered and f keeps its mean."""
+    zf = _stretched(6, seed=11)
+    f = np.random.default_rng(12).uniform(-1, 1, (6, 4, 8)) + 0.3
+    p = S.solve(f, 0.3, 0.7, zf, *bcs, alpha=alpha)
+    q = D.solve_direct(f, 0.3, 0.7, zf, *bcs, dense=True, alpha=alpha)
+    assert np.abs(p - q).max() <= 1e-12 * np.abs(q).max()
+    r = f - O.apply(p, 0.3, 0.7, zf, *bcs, alpha=alpha)
+    assert np.abs(r).max() < 1e-12 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("bcs", [("P", "NN", "DD"), ("ND", "P", "NN"), ("P", "P", "P")])
+def test_helmholtz_single_mode_closed_form(bcs):
+    """f = product of eigenvectors ⇒ p = f / (λx/Δx² + λy/Δy² + λz/Δz² − α)."""
+    nx, ny, nz, dx, dy, dz, alpha = 8, 6, 10, 0.25, 0.5, 0.1, 7.5
+    qx, qy, qz = 3, 1, 2
+    ex = T.backward_matrix(bcs[0], nx)[:, qx]
+    ey = T.backward_matrix(bcs[1], ny)[:, qy]
+    ez = T.backward_matrix(bcs[2], nz)[:, qz]
+    f = ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    lam = (T.eigenvalues(bcs[0], nx)[qx] / dx ** 2 + T.eigenvalues(bcs[1], ny)[qy] / dy ** 2
+           + T.eigenvalues(bcs[2], nz)[qz] / dz ** 2) - alpha
+    p = S.solve(f, dx, dy, O.uniform_faces(nz, dz), *bcs, alpha=alpha)
+    assert np.abs(p - f / lam).max() < 1e-13 * np.abs(f / lam).max()
+
+
+@pytest.mark.parametrize("bcs", [("P", "P", "NN"), ("NN", "P", "P"), ("NN", "NN", "NN")])
+def test_helmholtz_constant_closed_form(bcs):
+    """Constants are harmonic under P/NN ends (stretched z too), so f ≡ c gives p ≡ −c/α."""
+    zf = _stretched(7, seed=13)
+    f = np.full((7, 6, 4), 2.5)
+    p = S.solve(f, 0.4, 0.2, zf, *bcs, alpha=3.0)
+    assert np.abs(p + 2.5 / 3.0).max() < 1e-14
+
+
+def test_helmholtz_stencil_equals_sparse_matrix():
+    zf = _stretched(5, seed=14)
+    x = np.random.default_rng(15).standard_normal((5, 6, 4))
+    bcs = ("DD", "P", "ND")
+    A = O.operator_3d(4, 6, 0.2, 0.9, zf, *bcs, alpha=4.25)
+    assert np.abs(A @ x.ravel() - O.apply(x, 0.2, 0.9, zf, *bcs, alpha=4.25).ravel()).max() < 1e-12
