@@ -95,6 +95,21 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
                          const double* zf, double dz, ps_bc bcx, ps_bc bcy, ps_bc bcz,
                          ps_precision prec, double rtol, int max_iter);
 
+/* Helmholtz variant (§2: integrating the diffusion term implicitly needs one
+ * Helmholtz equation per velocity component; §4 reports it done with the same
+ * method). The plan solves (A − α·I)·p = f, A the operator of Eq. 4, with a
+ * shift α ≥ 0 (a Crank–Nicolson step of ∂u/∂t = ν∇²u has α = 2/(ν·Δt)). The
+ * transforms of Table 2 diagonalise the identity too, so only the diagonal of
+ * every z system of Eq. 5 moves by −α. Arguments and results as
+ * ps_plan_create, which is this call with α = 0; every solve entry point takes
+ * the plan (ps_solve_transpose applies (A − α·I)⁻ᵀ). With α > 0 no problem is
+ * singular: f is used as given and p carries no mean constraint. The boundary
+ * pairs are the staggered ones of Table 1 (cell-centred unknowns).
+ * PS_INVALID_ARG when α is negative or not finite. */
+ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double dx, double dy,
+                                   const double* zf, double dz, ps_bc bcx, ps_bc bcy, ps_bc bcz,
+                                   ps_precision prec, double rtol, int max_iter, double alpha);
+
 /* Bytes of device workspace a solve on this plan needs (caller allocates it,
  * 256-byte aligned, and may reuse it across solves on the same stream). */
 ps_status ps_workspace_bytes(const ps_plan* plan, size_t* bytes);

@@ -53,6 +53,7 @@ class PsKernelStat(ctypes.Structure):
 _vp, _i, _d, _st = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int
 _SIGS = {
     "ps_plan_create": [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _vp, _d, _i, _i, _i, _i, _d, _i],
+    "ps_plan_create_helmholtz": [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _vp, _d, _i, _i, _i, _i, _d, _i, _d],
     "ps_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "ps_solve": [_vp, _vp, _vp, _vp, _vp, _vp],
     "ps_solve_f32": [_vp, _vp, _vp, _vp, _vp, _vp],
@@ -126,19 +127,24 @@ def read_info(t):
 
 
 class Plan:
-    """A solver plan for one grid (see ps_plan_create)."""
+    """A solver plan for one grid (see ps_plan_create); alpha > 0 makes it a
+    Helmholtz plan, (A − α·I)·p = f (see ps_plan_create_helmholtz)."""
 
     def __init__(self, nx, ny, nz, dx, dy, zf=None, dz=None, bcs=("P", "P", "NN"),
-                 precision="fp64", rtol=1e-10, max_iter=5):
+                 precision="fp64", rtol=1e-10, max_iter=5, alpha=0.0):
         self.shape = (nz, ny, nx)
         self.precision = precision
         self.bcs = tuple(bcs)
+        self.alpha = float(alpha)
         self._zf = None if zf is None else np.ascontiguousarray(zf, dtype=np.float64)
         h = _vp()
         zp = None if self._zf is None else self._zf.ctypes.data_as(_vp)
-        _check(_lib.ps_plan_create(ctypes.byref(h), nx, ny, nz, float(dx), float(dy), zp,
-                                   float(dz or 0.0), BC[bcs[0]], BC[bcs[1]], BC[bcs[2]],
-                                   PRECISION[precision], float(rtol), int(max_iter)))
+        args = (ctypes.byref(h), nx, ny, nz, float(dx), float(dy), zp, float(dz or 0.0),
+                BC[bcs[0]], BC[bcs[1]], BC[bcs[2]], PRECISION[precision], float(rtol), int(max_iter))
+        if self.alpha != 0.0:
+            _check(_lib.ps_plan_create_helmholtz(*args, self.alpha))
+        else:
+            _check(_lib.ps_plan_create(*args))
         self.handle = h
         n = ctypes.c_size_t()
         _check(_lib.ps_workspace_bytes(h, ctypes.byref(n)), h)

@@ -87,6 +87,7 @@ struct ResidArgs {
   const float2* zres;       // passes m ≥ 1: per plane (a_k, c_k, w_c) in double-float, the
                             // Dirichlet ghost sign folded into a_0 / c_{n−1} (see residual.cu)
   double asum;              // max over planes of Σ_j |w_j| (the 7 coefficients of a row)
+  df nalpha;                // −α of a Helmholtz plan (A − α·I), double-float; zero otherwise
   const float* wz;          // Δz^f_k (weights of the mean, singular problems)
   const float* mu;          // double-float volume-weighted mean of f (singular)
   const unsigned long long* pmax_bits;  // bit pattern of max|operand| (sets the fixed-point scale)

@@ -155,6 +155,8 @@ struct ps_plan {
   double asum;   // max over rows of Σ_j |w_j| (those passes' accumulator binade)
   double wsum;  // Σ Δz^f (the per-plane weights of the singular mean, times nx·ny)
   double anorm; // an upper bound of ‖A‖∞ (the drift bound of the incremental residual)
+  double alpha = 0.0;  // Helmholtz shift: the plan solves (A − α·I)·p = f
+  df nalpha = {0.f, 0.f};  // −α in double-float (residual pass 0)
   int lowx, lowy;  // FP32 non-periodic z: rectangle of columns solved in FP64 (tridiag.cu)
   df idx2, idy2;
   void* dev;    // one allocation for all of the above
@@ -483,6 +485,7 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   ra.zhi = pl->zhi;
   ra.zres = pl->zres;
   ra.asum = pl->asum;
+  ra.nalpha = pl->nalpha;
   ra.wz = pl->dzf32;
   ra.mu = ctrl->mu;
   ra.singular = pl->singular;
@@ -597,8 +600,16 @@ extern "C" {
 ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, double dy,
                          const double* zf, double dz, ps_bc bcx, ps_bc bcy, ps_bc bcz,
                          ps_precision prec, double rtol, int max_iter) {
+  return ps_plan_create_helmholtz(out, nx, ny, nz, dx, dy, zf, dz, bcx, bcy, bcz, prec, rtol, max_iter, 0.0);
+}
+
+ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double dx, double dy,
+                                   const double* zf, double dz, ps_bc bcx, ps_bc bcy, ps_bc bcz,
+                                   ps_precision prec, double rtol, int max_iter, double alpha) {
   if (!out) return fail(nullptr, PS_INVALID_ARG, "null output pointer");
   *out = nullptr;
+  if (!(alpha >= 0.0) || !std::isfinite(alpha))
+    return fail(nullptr, PS_INVALID_ARG, "the Helmholtz shift alpha must be finite and >= 0");
   if ((unsigned)bcx > 3u || (unsigned)bcy > 3u || (unsigned)bcz > 3u)
     return fail(nullptr, PS_INVALID_ARG, "unknown boundary condition");
   if ((unsigned)prec > 2u) return fail(nullptr, PS_INVALID_ARG, "unknown precision");
@@ -622,7 +633,13 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
   p->N = (size_t)nx * ny * nz;
   p->periodic_z = (bcz == PS_BC_PERIODIC);
   auto pn = [](int b) { return b == PS_BC_PERIODIC || b == PS_BC_NEUMANN_NEUMANN; };
-  p->singular = pn(bcx) && pn(bcy) && pn(bcz);
+  p->singular = pn(bcx) && pn(bcy) && pn(bcz) && alpha == 0.0;  // α > 0: no null space
+  p->alpha = alpha;
+  {
+    float2 t;
+    split_df(-alpha, &t);
+    p->nalpha = df{t.x, t.y};
+  }
   p->resid_blocks3 = residual_blocks(nx, ny, nz, 1);
   p->resid_blocks2 = residual_blocks(nx, ny, nz, 0);
   p->resid_blocks = p->resid_blocks3 > p->resid_blocks2 ? p->resid_blocks3 : p->resid_blocks2;
@@ -673,7 +690,7 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
       const double zr = std::fabs(za[k]) + std::fabs(zb[k]) + std::fabs(zc[k]);
       zmax = zr > zmax ? zr : zmax;
     }
-    p->anorm = 8.0 / (dx * dx) + 8.0 / (dy * dy) + zmax;
+    p->anorm = 8.0 / (dx * dx) + 8.0 / (dy * dy) + zmax + alpha;
   }
   // Sum form of a row for the residual passes m ≥ 1: A·e = Σ_j w_j·e_j over x±1,
   // y±1, z±1 and the centre (w_c = −Σ of the others). The ghost plane at a
@@ -690,8 +707,8 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
       const double ch = (k == nz - 1 && dhi) ? -hi[k] : hi[k];
       split_df(cl, &zres[3 * (size_t)k]);
       split_df(ch, &zres[3 * (size_t)k + 1]);
-      split_df(-(2.0 * ix2 + 2.0 * iy2 + lo[k] + hi[k]), &zres[3 * (size_t)k + 2]);
-      const double rs = 4.0 * ix2 + 4.0 * iy2 + 2.0 * (lo[k] + hi[k]);
+      split_df(-(2.0 * ix2 + 2.0 * iy2 + lo[k] + hi[k]) - alpha, &zres[3 * (size_t)k + 2]);
+      const double rs = 4.0 * ix2 + 4.0 * iy2 + 2.0 * (lo[k] + hi[k]) + alpha;
       asum = rs > asum ? rs : asum;
     }
     p->asum = asum;
@@ -723,7 +740,8 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
   {
     // FP32 paths with a non-periodic z: columns whose z system has κ ≈ ‖T_z‖/|λ| > 10^4
     // are solved in FP64 (tridiag.cu). λ grows with q along each axis, so they lie in
-    // the rectangle q_x < lowx, q_y < lowy; at most 1/8 of the columns.
+    // the rectangle q_x < lowx, q_y < lowy; at most 1/8 of the columns. A Helmholtz
+    // shift adds α to every |λ| (all terms of the diagonal shift have one sign).
     p->lowx = p->lowy = 0;
     if (prec != PS_FP64 && bcz != PS_BC_PERIODIC) {
       double zmax = 0.0;
@@ -732,8 +750,8 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
       const double thr = zmax / 1e4;
       const std::vector<double> lx = eig_scaled(bcx, nx, dx), ly = eig_scaled(bcy, ny, dy);
       int qx = 0, qy = 0;
-      while (qx < nx && std::fabs(lx[qx]) < thr) ++qx;
-      while (qy < ny && std::fabs(ly[qy]) < thr) ++qy;
+      while (qx < nx && std::fabs(lx[qx]) + alpha < thr) ++qx;
+      while (qy < ny && std::fabs(ly[qy]) + alpha < thr) ++qy;
       while ((size_t)qx * qy * 8 > (size_t)nx * ny && qy > 1) --qy;
       while ((size_t)qx * qy * 8 > (size_t)nx * ny && qx > 1) --qx;
       if ((size_t)qx * qy * 8 <= (size_t)nx * ny && qx > 0 && qy > 0) {
@@ -779,7 +797,10 @@ ps_status ps_plan_create(ps_plan** out, int nx, int ny, int nz, double dx, doubl
   for (int k = 0; k < nz; ++k) idzf[k] = 1.0 / dzf[k];
   for (int k = 1; k < nz; ++k) idzc[k] = 1.0 / dzc[k - 1];
   if (bcz == PS_BC_PERIODIC) idzc[0] = 1.0 / (0.5 * (dzf[0] + dzf[nz - 1]));
-  const std::vector<double>* srcs[6] = {&za, &zb, &zc, &dzf, &idzf, &idzc};
+  // the z solves' diagonal b_k carries the Helmholtz shift (−α on every row of Eq. 5)
+  std::vector<double> zbs(zb);
+  for (int k = 0; k < nz; ++k) zbs[k] -= alpha;
+  const std::vector<double>* srcs[6] = {&za, &zbs, &zc, &dzf, &idzf, &idzc};
   for (int i = 0; i < 6; ++i) {
     *d64[i] = reinterpret_cast<double*>(take(nz * sizeof(double)));
     *d32[i] = reinterpret_cast<float*>(take(nz * sizeof(float)));

@@ -64,6 +64,7 @@ enum : int {
   RK_FIRST = 2,   // pass 0: max/min of f, and (singular) the weighted sum of f
   RK_SUBMU = 4,   // subtract μ_f (double-float) from the base
   RK_U32 = 8,     // operand U is FP32 (else FP64)
+  RK_SHIFT = 16,  // Helmholtz plan: the row also holds −α·U (exact product with each level)
   RK_SPLIT3 = 32  // three-level split of U (pass 0 and the exact pass; see below)
 };
 
@@ -215,7 +216,7 @@ __device__ __forceinline__ void resid_reduce(const ResidArgs& a, float rmax, flo
 template <int RPT, int KIND>
 __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(ResidArgs a) {
   constexpr bool SING = KIND & RK_SING, FIRST = KIND & RK_FIRST, SUBMU = KIND & RK_SUBMU;
-  constexpr bool U32 = KIND & RK_U32, SPLIT3 = KIND & RK_SPLIT3;
+  constexpr bool U32 = KIND & RK_U32, SPLIT3 = KIND & RK_SPLIT3, SHIFT = KIND & RK_SHIFT;
   using UT = typename std::conditional<U32, float, double>::type;
   using CT = typename std::conditional<SPLIT3, fxp3, fxp>::type;  // a split cell
   constexpr int TY = RWARPS * RPT, W = RTX + 2, CELLS = resid_cells(RPT);
@@ -394,6 +395,12 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
       const df s123 = two_sum(s12.h, t3.h);
       df s1234 = two_sum(s123.h, t4.h);
       float ap_lo = ((s12.l + s123.l) + (s1234.l + t1.l)) + ((t2.l + t3.l) + (t4.l + lo_terms));
+      if constexpr (SHIFT) {  // −α·U: the high level's product exact, the low level in FP32
+        const df t5 = prod(pc.h, a.nalpha);
+        const df s5 = two_sum(s1234.h, t5.h);
+        s1234 = {s5.h, 0.f};
+        ap_lo += (s5.l + t5.l) + a.nalpha.h * pc.l;
+      }
       if constexpr (SPLIT3) {
         // the middle level: exact sums on its grid, exact products, double-float sums
         const float mx = (xm.m + xp.m) - 2.f * pc.m, my = (ym.m + yp.m) - 2.f * pc.m;
@@ -401,7 +408,13 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
         const df u3 = prod(zmv.m - pc.m, df{cl.x, cl.y}), u4 = prod(zpv.m - pc.m, df{ch.x, ch.y});
         const df m12 = two_sum(u1.h, u2.h);
         const df m123 = two_sum(m12.h, u3.h);
-        const df m1234 = two_sum(m123.h, u4.h);
+        df m1234 = two_sum(m123.h, u4.h);
+        if constexpr (SHIFT) {
+          const df u5 = prod(pc.m, a.nalpha);
+          const df m5 = two_sum(m1234.h, u5.h);
+          ap_lo += m1234.l + u5.l;
+          m1234 = {m5.h, m5.l};
+        }
         const df hm = two_sum(s1234.h, m1234.h);
         s1234 = {hm.h, 0.f};
         ap_lo += ((m12.l + m123.l) + (m1234.l + u1.l)) + ((u2.l + u3.l) + (u4.l + hm.l));
@@ -802,6 +815,9 @@ cudaError_t launch_rpt(const ResidArgs& b, int kind, dim3 grid, cudaStream_t st)
   if constexpr (RPT == 2) {  // the three-level passes run with two rows per thread only
     switch (kind) {
       case RK_SPLIT3: return launch_kind<RPT, RK_SPLIT3>(b, grid, st);
+      case RK_SPLIT3 | RK_SHIFT: return launch_kind<RPT, RK_SPLIT3 | RK_SHIFT>(b, grid, st);
+      case RK_SPLIT3 | RK_U32 | RK_FIRST | RK_SHIFT:
+        return launch_kind<RPT, RK_SPLIT3 | RK_U32 | RK_FIRST | RK_SHIFT>(b, grid, st);
       case RK_SPLIT3 | RK_SING | RK_SUBMU: return launch_kind<RPT, RK_SPLIT3 | RK_SING | RK_SUBMU>(b, grid, st);
       case RK_SPLIT3 | RK_U32 | RK_FIRST: return launch_kind<RPT, RK_SPLIT3 | RK_U32 | RK_FIRST>(b, grid, st);
       case RK_SPLIT3 | RK_U32 | RK_FIRST | RK_SING:
@@ -811,6 +827,7 @@ cudaError_t launch_rpt(const ResidArgs& b, int kind, dim3 grid, cudaStream_t st)
   }
   switch (kind) {
     case RK_U32 | RK_FIRST: return launch_kind<RPT, RK_U32 | RK_FIRST>(b, grid, st);
+    case RK_U32 | RK_FIRST | RK_SHIFT: return launch_kind<RPT, RK_U32 | RK_FIRST | RK_SHIFT>(b, grid, st);
     case RK_U32 | RK_FIRST | RK_SING: return launch_kind<RPT, RK_U32 | RK_FIRST | RK_SING>(b, grid, st);
     default: return cudaErrorInvalidValue;
   }
@@ -867,7 +884,7 @@ cudaError_t launch_residual_inc(const ResidArgs& a, int pass, int split3, cudaSt
     if (!a.zres) return cudaErrorInvalidValue;
     return launch_resid_acc(a, pass, st);
   }
-  int kind = RK_U32 | RK_FIRST | (split3 ? RK_SPLIT3 : 0);
+  int kind = RK_U32 | RK_FIRST | (split3 ? RK_SPLIT3 : 0) | (a.nalpha.h != 0.f ? RK_SHIFT : 0);
   if (a.singular) kind |= RK_SING;
   if (a.singular && pass == 1) kind |= RK_SUBMU;
   return launch_resid(a, kind, pass == 0, st);
@@ -875,7 +892,8 @@ cudaError_t launch_residual_inc(const ResidArgs& a, int pass, int split3, cudaSt
 
 cudaError_t launch_residual_exact(const ResidArgs& a, cudaStream_t st) {
   if (!a.p || !a.r) return cudaErrorInvalidValue;
-  return launch_resid(a, RK_SPLIT3 | (a.singular ? (RK_SING | RK_SUBMU) : 0), 0, st);
+  return launch_resid(a, RK_SPLIT3 | (a.singular ? (RK_SING | RK_SUBMU) : 0) | (a.nalpha.h != 0.f ? RK_SHIFT : 0),
+                      0, st);
 }
 
 namespace {

@@ -73,3 +73,13 @@ def test_null_arguments(binding):
     assert binding.ps_plan_destroy(None) == binding.PS_OK
     n = ctypes.c_size_t()
     assert binding.ps_workspace_bytes(None, ctypes.byref(n)) == binding.PS_INVALID_ARG
+
+
+@pytest.mark.parametrize("alpha", [-1.0, float("inf"), float("nan")])
+def test_helmholtz_shift_validated(binding, alpha):
+    h = ctypes.c_void_p()
+    st = binding.ps_plan_create_helmholtz(ctypes.byref(h), 8, 8, 8, 1.0, 1.0, None, 1.0, 0, 0, 1, 0,
+                                          1e-10, 3, alpha)
+    assert st == binding.PS_INVALID_ARG
+    assert not h.value
+    assert b"alpha" in binding.ps_last_error(None)
