@@ -13,7 +13,7 @@ Readings (the paper gives the uniform stencil only):
   face. Neumann: ghost Φ_{−1} = Φ_0 (zero flux). Dirichlet: ghost
   Φ_{−1} = −Φ_0 mirrored across the face (zero value on the face). Periodic:
   the ghost is the cell on the other end. ``"ND"`` is Neumann at the low end,
-  Dirichlet at the high end.
+  Dirichlet at the high end; ``"DN"`` (not in Table 1) the reverse.
 * Stretched z: finite-volume form ``(flux_{k+1/2} − flux_{k−1/2}) / Δz^f_k``
   with ``flux_{k+1/2} = (Φ_{k+1} − Φ_k) / Δz^c_k``; Δz^f_k is the width of
   cell k and Δz^c_k the distance between the centres of cells k and k+1. A
@@ -53,7 +53,7 @@ def _ends(bc):
     """BC kind at (low, high) end: 'N', 'D' or 'P'."""
     if bc not in BCS:
         raise ValueError(f"unknown BC {bc!r}")
-    return {"P": ("P", "P"), "NN": ("N", "N"), "DD": ("D", "D"), "ND": ("N", "D")}[bc]
+    return {"P": ("P", "P"), "NN": ("N", "N"), "DD": ("D", "D"), "ND": ("N", "D"), "DN": ("D", "N")}[bc]
 
 
 def operator_1d(bc, faces):

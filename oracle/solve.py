@@ -56,7 +56,7 @@ def z_system(zf, bcz):
         b[0] -= a[0]
         b[-1] -= c[-1]
     else:
-        lo_d = bcz == "DD"
+        lo_d = bcz in ("DD", "DN")
         hi_d = bcz in ("DD", "ND")
         if lo_d:
             b[0] -= 2.0 / dzf[0] ** 2

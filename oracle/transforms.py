@@ -7,6 +7,11 @@ staggered Neumann at both ends, ``"DD"`` staggered Dirichlet at both ends,
 ``"ND"`` Neumann at the low end and Dirichlet at the high end. ``n`` is the
 (even) number of cells along the axis (Table 1 caption).
 
+``"DN"`` (Dirichlet at the low end, Neumann at the high end) is not in Table 1.
+Reading taken: it is the ND problem on the reversed axis (a_p ↦ a_{n−1−p}), so
+its forward transform is ND's applied to the reversed line, its inverse ND's
+inverse followed by the reversal, and its θ_q (hence λ_q) are ND's.
+
 Conventions
 -----------
 ``forward_matrix(bc, n)[q, p]`` maps a physical line ``a_p`` to its spectral
@@ -32,7 +37,7 @@ With this layout Table 1's periodic θ reads θ_q = ⌈q/2⌉ π / n (its
 
 import numpy as np
 
-BCS = ("P", "NN", "DD", "ND")
+BCS = ("P", "NN", "DD", "ND", "DN")
 
 
 def _check(bc, n):
@@ -63,7 +68,7 @@ def theta(bc, n):
         return q * np.pi / (2 * n)
     if bc == "DD":
         return (q + 1) * np.pi / (2 * n)
-    return (2 * q + 1) * np.pi / (4 * n)           # ND
+    return (2 * q + 1) * np.pi / (4 * n)           # ND, and DN (the reversed ND axis)
 
 
 def eigenvalues(bc, n):
@@ -88,6 +93,8 @@ def forward_matrix(bc, n):
         return 2.0 * _cos_pi((2 * p + 1) * q, 2 * n)
     if bc == "DD":      # DST-II: 2 Σ a_p sin(π (p+1/2)(q+1) / n)
         return 2.0 * _sin_pi((2 * p + 1) * (q + 1), 2 * n)
+    if bc == "DN":      # the ND transform of the reversed line
+        return forward_matrix("ND", n)[:, ::-1].copy()
     # ND, DCT-IV: 2 Σ a_p cos(π (p+1/2)(q+1/2) / n)
     return 2.0 * _cos_pi((2 * p + 1) * (2 * q + 1), 4 * n)
 
@@ -113,6 +120,8 @@ def backward_matrix(bc, n):
         B = 2.0 * _sin_pi((q + 1) * (2 * p + 1), 2 * n)
         B[:, n - 1] = (-1.0) ** p[:, 0]
         return B / (2 * n)
+    if bc == "DN":      # ND's inverse, then the reversal
+        return backward_matrix("ND", n)[::-1, :].copy()
     # ND: (1/2n) DCT-IV
     return 2.0 * _cos_pi((2 * p + 1) * (2 * q + 1), 4 * n) / (2 * n)
 

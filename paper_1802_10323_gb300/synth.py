@@ -11,7 +11,7 @@ Workloads (domain sizes follow Table 3; the channel box is 6 × 3 × 1):
   z_k = (L/2)(1 + tanh(α(2k/n − 1)) / tanh α), k = 0…n, α = 1.5.
 * ``uniform_noise``: i.i.d. U[−1, 1] right-hand side, arithmetic mean removed.
 * ``manufactured``: a product of per-axis eigenfunction-like profiles that
-  satisfy each BC (P: cos 2πx/L, NN: cos πx/L, DD: sin πx/L, ND: cos πx/2L)
+  satisfy each BC (P: cos 2πx/L, NN: cos πx/L, DD: sin πx/L, ND: cos πx/2L, DN: sin πx/2L)
   with its analytic Laplacian at the cell centres, plus seeded noise.
 * ``staggered_velocity`` / ``divergence_rhs``: a Gaussian random velocity on
   the faces of a staggered grid that is periodic in x and y with walls in z
@@ -51,6 +51,7 @@ _PROFILE = {
     "NN": lambda x, L: (np.cos(np.pi * x / L), (np.pi / L) ** 2),
     "DD": lambda x, L: (np.sin(np.pi * x / L), (np.pi / L) ** 2),
     "ND": lambda x, L: (np.cos(0.5 * np.pi * x / L), (0.5 * np.pi / L) ** 2),
+    "DN": lambda x, L: (np.sin(0.5 * np.pi * x / L), (0.5 * np.pi / L) ** 2),
 }
 
 

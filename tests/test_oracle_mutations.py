@@ -112,6 +112,12 @@ def _swap_metric(orig):
     return f
 
 
+def _dn_ends_swapped(orig):
+    def f(bc):
+        return ("N", "D") if bc == "DN" else orig(bc)
+    return f
+
+
 def _flip_alpha(orig):
     def f(nx, ny, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
         return orig(nx, ny, dx, dy, zf, bcx, bcy, bcz, -alpha)
@@ -138,6 +144,7 @@ MUTATIONS = [
     ("perturbed back substitution", S, "thomas", _wrong_backsub),
     ("singular column mean not removed", S, "_singular_column", _no_mean_removal),
     ("reversed cell widths", O, "metrics", _swap_metric),
+    ("DN ends swapped (read as ND) in the ghost rules", O, "_ends", _dn_ends_swapped),
     ("Helmholtz shift with the wrong sign in the assembled operator", O, "operator_3d", _flip_alpha),
     ("Helmholtz shift dropped from the stencil", O, "apply", _drop_alpha),
     ("singular-mode treatment kept for a Helmholtz shift", O, "is_singular", _singular_ignores_alpha),

@@ -97,7 +97,8 @@ def test_single_mode_closed_form(bcs):
     assert np.abs(p - f / lam).max() < 1e-13 * np.abs(f / lam).max()
 
 
-@pytest.mark.parametrize("bcs", [("P", "NN", "DD"), ("ND", "DD", "NN"), ("NN", "P", "ND"), ("P", "P", "NN")])
+@pytest.mark.parametrize("bcs", [("P", "NN", "DD"), ("ND", "DD", "NN"), ("NN", "P", "ND"), ("P", "P", "NN"),
+                                 ("DN", "P", "DN"), ("NN", "DN", "ND")])
 def test_second_order_convergence(bcs):
     errs, hs = [], []
     for n in (16, 32, 64):

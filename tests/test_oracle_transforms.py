@@ -52,6 +52,16 @@ def test_backward_is_scaled_scipy(bc, kind, typ, n):
 
 
 @pytest.mark.parametrize("n", SIZES)
+def test_dn_is_signed_scipy_dst4(n):
+    """DN (not in Table 1, read as ND on the reversed axis): reversing a DCT-IV's input
+    gives (−1)^q times the DST-IV, so F_DN = diag((−1)^q)·DST-IV and B_DN = DST-IV·diag((−1)^q)/2n."""
+    sgn = (-1.0) ** np.arange(n)
+    dst4 = sfft.dst(np.eye(n), type=4, axis=0)
+    assert np.abs(T.forward_matrix("DN", n) - sgn[:, None] * dst4).max() < 1e-13 * n
+    assert np.abs(T.backward_matrix("DN", n) - dst4 * sgn[None, :] / (2 * n)).max() < 1e-14 * n
+
+
+@pytest.mark.parametrize("n", SIZES)
 def test_periodic_rows_are_rfft(n):
     X = np.fft.rfft(np.eye(n), axis=0)
     ref = np.zeros((n, n))
