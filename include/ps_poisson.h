@@ -47,12 +47,16 @@ typedef enum {
  * cell face). NEUMANN_DIRICHLET is Neumann at the low end, Dirichlet at the
  * high end. Forward transforms per Table 2: DFT (half-complex layout),
  * DCT-II, DST-II, DCT-IV; backward: 1/n IDFT, 1/(2n) DCT-III, 1/(2n) DST-III,
- * 1/(2n) DCT-IV. */
+ * 1/(2n) DCT-IV. DIRICHLET_NEUMANN (not in Table 1) is the reverse pair,
+ * solved as NEUMANN_DIRICHLET on the reversed axis: its transforms are the
+ * DCT-IV ones applied to the reversed line (forward: (−1)^q times a DST-IV)
+ * and its eigenvalues are NEUMANN_DIRICHLET's. */
 typedef enum {
   PS_BC_PERIODIC = 0,
   PS_BC_NEUMANN_NEUMANN = 1,
   PS_BC_DIRICHLET_DIRICHLET = 2,
-  PS_BC_NEUMANN_DIRICHLET = 3
+  PS_BC_NEUMANN_DIRICHLET = 3,
+  PS_BC_DIRICHLET_NEUMANN = 4
 } ps_bc;
 
 /* Arithmetic of the solve.

@@ -9,7 +9,11 @@
 
 namespace ps {
 
-enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3 };
+enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3, BC_DN = 4 };
+// ND and DN share the DCT-IV line transform: DN is the ND problem on the reversed
+// line, so on the physical side of a transform the two reals x_{2p} and x_{n−1−2p}
+// trade places; the spectral side, the tables and the eigenvalues are ND's.
+__host__ __device__ inline bool bc_iv(int bc) { return bc == BC_ND || bc == BC_DN; }
 constexpr int kMaxN = 1024;
 constexpr int kMaxStages = 12;
 extern thread_local char g_launch_diag[256];  // configuration of the last failed launch

@@ -81,7 +81,7 @@ long theta_j(int bc, int n, int q) {
     case BC_P: return 4L * ((q + 1) / 2);  // ⌈q/2⌉·π/n; Nyquist q = n−1 gives π/2
     case BC_NN: return 2L * q;
     case BC_DD: return 2L * (q + 1);
-    default: return 2L * q + 1;            // ND
+    default: return 2L * q + 1;            // ND, and DN (the reversed ND axis)
   }
 }
 
@@ -610,7 +610,7 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   *out = nullptr;
   if (!(alpha >= 0.0) || !std::isfinite(alpha))
     return fail(nullptr, PS_INVALID_ARG, "the Helmholtz shift alpha must be finite and >= 0");
-  if ((unsigned)bcx > 3u || (unsigned)bcy > 3u || (unsigned)bcz > 3u)
+  if ((unsigned)bcx > 4u || (unsigned)bcy > 4u || (unsigned)bcz > 4u)
     return fail(nullptr, PS_INVALID_ARG, "unknown boundary condition");
   if ((unsigned)prec > 2u) return fail(nullptr, PS_INVALID_ARG, "unknown precision");
   if (!(dx > 0) || !(dy > 0)) return fail(nullptr, PS_INVALID_ARG, "dx and dy must be > 0");
@@ -660,7 +660,7 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
     zb[0] -= za[0];
     zb[nz - 1] -= zc[nz - 1];
   } else {
-    if (bcz == PS_BC_DIRICHLET_DIRICHLET) {
+    if (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_DIRICHLET_NEUMANN) {
       zb[0] -= 2.0 / (dzf[0] * dzf[0]);
       lo[0] = 1.0 / (dzf[0] * dzf[0]);
     }
@@ -699,7 +699,7 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   std::vector<float2> zres(3 * (size_t)nz);
   {
     const double ix2 = 1.0 / (dx * dx), iy2 = 1.0 / (dy * dy);
-    const bool dlo = (bcz == PS_BC_DIRICHLET_DIRICHLET);
+    const bool dlo = (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_DIRICHLET_NEUMANN);
     const bool dhi = (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_NEUMANN_DIRICHLET);
     double asum = 0.0;
     for (int k = 0; k < nz; ++k) {

@@ -73,7 +73,7 @@ __host__ __device__ constexpr size_t resid_smem(int rpt, int usize, int csize) {
   return (size_t)RDEPTH * resid_cells(rpt) * usize + (size_t)2 * resid_cells(rpt) * csize;
 }
 
-__device__ __forceinline__ int end_lo(int bc) { return bc == BC_P ? END_WRAP : (bc == BC_DD ? END_D : END_N); }
+__device__ __forceinline__ int end_lo(int bc) { return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_DN) ? END_D : END_N); }
 __device__ __forceinline__ int end_hi(int bc) { return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_ND) ? END_D : END_N); }
 
 // unevaluated double-float sum

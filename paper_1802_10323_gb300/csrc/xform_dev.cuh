@@ -154,18 +154,19 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
           if (j1 >= m) v1 = -v1;
         }
         z = {v0, v1};
-      } else {  // ND
-        z = cmul(cplx<T>{x[2 * p], x[n - 1 - 2 * p]}, tw[4 * p]);
+      } else {  // ND (DN: the reversed line, the two reals swap)
+        const T e0 = x[2 * p], e1 = x[n - 1 - 2 * p];
+        z = cmul(bc == BC_DN ? cplx<T>{e1, e0} : cplx<T>{e0, e1}, tw[4 * p]);
       }
       bufA[l * ld + p] = z;
     }
   } else {
-    const int np = (bc == BC_ND) ? m : (m / 2 + 1);
+    const int np = bc_iv(bc) ? m : (m / 2 + 1);
     for (int idx = threadIdx.x; idx < L * np; idx += blockDim.x) {
       const int l = idx / np, k = idx - l * np;
       const T* X = rB + l * ldr;
       cplx<T>* Z = bufA + l * ld;
-      if (bc == BC_ND) {
+      if (bc_iv(bc)) {
         Z[k] = cmul(cplx<T>{X[2 * k], X[n - 1 - 2 * k]}, tw[4 * k]);
         continue;
       }
@@ -216,7 +217,7 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
   cplx<T>* src = bufA;
   cplx<T>* dst = bufB;
   {
-    const bool inv = !FWD && bc != BC_ND;
+    const bool inv = !FWD && !bc_iv(bc);
     int Ns = 1;
     for (int s = 0; s < a.nstages; ++s) {
       const int R = a.radix[s];
@@ -241,12 +242,12 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
 
   // ---- 4. post-processing: m complex points -> n reals --------------------------
   if (FWD) {
-    const int np = (bc == BC_ND) ? m : (m / 2 + 1);
+    const int np = bc_iv(bc) ? m : (m / 2 + 1);
     for (int idx = threadIdx.x; idx < L * np; idx += blockDim.x) {
       const int l = idx / np, k = idx - l * np;
       const cplx<T>* Z = src + l * ld;
       T* o = rO + l * ldr;
-      if (bc == BC_ND) {
+      if (bc_iv(bc)) {
         cplx<T> c = cmul(tw[4 * k + 1], Z[k]);
         o[2 * k] = (T)2 * c.x;
         o[n - 1 - 2 * k] = (T)-2 * c.y;
@@ -296,11 +297,12 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
       const int l = idx / m, k = idx - l * m;
       const cplx<T>* Z = src + l * ld;
       T* o = rO + l * ldr;
-      if (bc == BC_ND) {
+      if (bc_iv(bc)) {
         const T s = (T)1 / (T)n;  // 2·(1/2n)
         cplx<T> c = cmul(tw[4 * k + 1], Z[k]);
-        o[2 * k] = s * c.x;
-        o[n - 1 - 2 * k] = -s * c.y;
+        const bool sw = (bc == BC_DN);
+        o[sw ? n - 1 - 2 * k : 2 * k] = s * c.x;
+        o[sw ? 2 * k : n - 1 - 2 * k] = -s * c.y;
       } else if (bc == BC_P) {
         o[2 * k] = Z[k].x * inv_m;
         o[2 * k + 1] = Z[k].y * inv_m;

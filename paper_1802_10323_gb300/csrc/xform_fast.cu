@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
   for (int i = threadIdx.x; i <= M; i += blockDim.x) ptw[i] = a.tw[8 * i];
   if (bc == BC_NN || bc == BC_DD) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) xtw[i] = a.tw[2 * i];
-  } else if (bc == BC_ND) {
+  } else if (bc_iv(bc)) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
       xtw[i] = a.tw[4 * i];          // e^{−iπr/n}
       xtw[M + i] = a.tw[4 * i + 1];  // e^{−iπ(4k+1)/4n}
@@ -155,8 +155,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
             cplx<T> z;
             if (bc == BC_P) {
               z = *reinterpret_cast<const cplx<T>*>(&lr[2 * p]);
-            } else if (bc == BC_ND) {
-              z = cmul(cplx<T>{lr[2 * p], lr[N - 1 - 2 * p]}, xtw[p]);
+            } else if (bc_iv(bc)) {  // DN: the reversed line, the two reals swap
+              const T e0 = lr[2 * p], e1 = lr[N - 1 - 2 * p];
+              z = cmul(bc == BC_DN ? cplx<T>{e1, e0} : cplx<T>{e0, e1}, xtw[p]);
             } else {
               const int j0 = 2 * p, j1 = 2 * p + 1;
               T v0 = lr[j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0];
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
 #pragma unroll
           for (int r = 0; r < RL; ++r) lc[cpad(t + q * TPL + r * (M / RL))] = v[q * RL + r];
         __syncwarp();
-        if (bc == BC_ND) {
+        if (bc_iv(bc)) {
           cplx<T> c[E];
 #pragma unroll
           for (int i = 0; i < E; ++i) {
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         }
       } else {
         // ---- backward pre-processing into the complex buffer ----
-        if (bc == BC_ND) {
+        if (bc_iv(bc)) {
           cplx<T> z[E];
 #pragma unroll
           for (int i = 0; i < E; ++i) {
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
         for (int q = 0; q < E / R0; ++q)
 #pragma unroll
           for (int r = 0; r < R0; ++r) v[q * R0 + r] = lc[cpad(t + q * TPL + r * (M / R0))];
-        if (bc == BC_ND) fast::fft_stages<T, M, false, 0, 1>(v, lc, stw, t);
+        if (bc_iv(bc)) fast::fft_stages<T, M, false, 0, 1>(v, lc, stw, t);
         else fast::fft_stages<T, M, true, 0, 1>(v, lc, stw, t);
         // ---- backward post-processing straight from the last stage's outputs ----
         constexpr int RL = Shape<M>::radix(Shape<M>::NST - 1);
@@ -318,10 +319,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
           for (int r = 0; r < RL; ++r) {
             const int k = t + q * TPL + r * (M / RL);
             const cplx<T> zk = v[q * RL + r];
-            if (bc == BC_ND) {
+            if (bc_iv(bc)) {
               const cplx<T> c = cmul(xtw[M + k], zk);
-              lr[2 * k] = c.x * ((T)1 / (T)N);
-              lr[N - 1 - 2 * k] = -c.y * ((T)1 / (T)N);
+              const bool sw = (bc == BC_DN);
+              lr[sw ? N - 1 - 2 * k : 2 * k] = c.x * ((T)1 / (T)N);
+              lr[sw ? 2 * k : N - 1 - 2 * k] = -c.y * ((T)1 / (T)N);
             } else if (bc == BC_P) {
               lr[2 * k] = zk.x * inv_m;
               lr[2 * k + 1] = zk.y * inv_m;

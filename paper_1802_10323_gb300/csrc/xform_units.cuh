@@ -22,7 +22,7 @@ __device__ __forceinline__ void load_line_tables(const cplx<T>* tw, int bc, cplx
   for (int i = threadIdx.x; i <= M; i += blockDim.x) ptw[i] = tw[8 * i];
   if (bc == BC_NN || bc == BC_DD) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) xtw[i] = tw[2 * i];
-  } else if (bc == BC_ND) {
+  } else if (bc_iv(bc)) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
       xtw[i] = tw[4 * i];
       xtw[M + i] = tw[4 * i + 1];
@@ -109,15 +109,23 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
         const vec<TI, 2> x = *reinterpret_cast<const vec<TI, 2>*>(src + 2 * p);
         v[si] = {in_cvt<T>(x.v[0]) * s, in_cvt<T>(x.v[1]) * s};
       }
-    } else if (bc == BC_ND) {
+    } else if (bc_iv(bc)) {
       // z_p = (x_{2p}, x_{n−1−2p})·e^{−iπp/n}; x_{n−1−2p} = x_{2p'+1} of p' = M−1−p
+      // (DN, the reversed line: z_p = (x_{n−1−2p}, x_{2p}), the two parts trade places)
+      const bool sw = (bc == BC_DN);
 #pragma unroll
       for (int si = 0; si < E; ++si) {
         const int p = t + (si / R0) * TPL + (si % R0) * (M / R0);
         const vec<TI, 2> x = *reinterpret_cast<const vec<TI, 2>*>(src + 2 * p);
-        v[si].x = in_cvt<T>(x.v[0]) * s;
-        const T odd = in_cvt<T>(x.v[1]) * s;
-        v[E - 1 - si].y = __shfl_sync(full, odd, mate);
+        const T even = in_cvt<T>(x.v[0]) * s;
+        const T odd = __shfl_sync(full, in_cvt<T>(x.v[1]) * s, mate);
+        if (sw) {
+          v[si].y = even;
+          v[E - 1 - si].x = odd;
+        } else {
+          v[si].x = even;
+          v[E - 1 - si].y = odd;
+        }
       }
 #pragma unroll
       for (int si = 0; si < E; ++si) {
@@ -162,7 +170,7 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
       auto Y = [&](int i, T val) {
         if (live) dst[i] = st_cvt<TO, T>::f(val);
       };
-      if (bc == BC_ND) {
+      if (bc_iv(bc)) {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
           const int k = t + 32 * j;
@@ -229,7 +237,7 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
       auto Y = [&](int i, T val) {
         if (live) dst[i] = st_cvt<TO, T>::f(val);
       };
-      if (bc == BC_ND) {
+      if (bc_iv(bc)) {
   #pragma unroll
         for (int i = 0; i < E; ++i) {
           const int k = t + i * TPL;
@@ -299,7 +307,7 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
       // ---- backward pre-processing in registers: own V_k, V_{M−k} from the partner lane,
       // Z_k straight into its first-stage slot ----
       using LS = LaneSlots<M>;
-      if (bc == BC_ND) {
+      if (bc_iv(bc)) {
         // (x_{2k}, x_{n−1−2k})·e^{−iπk/n}; x_{n−1−2k} = x_{2k'+1} of k' = M−1−k (mirrored lane)
         cplx<T> z[E];
 #pragma unroll
@@ -352,7 +360,7 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
       }
     } else {
       // ---- backward pre-processing: pairs (k, M−k) from the line into the buffer ----
-      if (bc == BC_ND) {
+      if (bc_iv(bc)) {
         // (x_{2k}, x_{n−1−2k})·e^{−iπk/n}; x_{n−1−2k} = x_{2k'+1} of k' = M−1−k
   #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -423,7 +431,7 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
   #pragma unroll
         for (int r = 0; r < R0; ++r) v[q * R0 + r] = lc[cpad(t + q * TPL + r * (M / R0))];
     }
-    if (bc == BC_ND) fast::fft_stages<T, M, false, 0, 1>(v, lc, stw, t);
+    if (bc_iv(bc)) fast::fft_stages<T, M, false, 0, 1>(v, lc, stw, t);
     else fast::fft_stages<T, M, true, 0, 1>(v, lc, stw, t);
     __syncwarp();  // the last stage's buffer reads are done before the next line
     // ---- backward outputs straight from the last stage, as vectors ----
@@ -466,9 +474,10 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
         const T val[2] = {v[si].x * inv_m, v[si].y * inv_m};
         put(2 * k, val, two{});
       }
-    } else if (bc == BC_ND) {
+    } else if (bc_iv(bc)) {
       // output 2k = Re(c_k)/n, output n−1−2k = −Im(c_k)/n with c_k = e^{...}·z_k;
       // the pair (2k, 2k+1) takes −Im(c_{k'})/n of k' = M−1−k from the mirrored slot
+      // (DN, the reversed line: the two outputs of each k trade places)
       const T inv_n = (T)1 / (T)N;
       T re[E], im[E];
 #pragma unroll
@@ -478,10 +487,12 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
         re[si] = c.x * inv_n;
         im[si] = -c.y * inv_n;
       }
+      const bool sw = (bc == BC_DN);
 #pragma unroll
       for (int si = 0; si < E; ++si) {
         const int k = t + (si / RL) * TPL + (si % RL) * (M / RL);
-        const T val[2] = {re[si], __shfl_sync(full, im[E - 1 - si], mate)};
+        const T mine = sw ? im[si] : re[si];
+        const T val[2] = {mine, __shfl_sync(full, sw ? re[E - 1 - si] : im[E - 1 - si], mate)};
         put(2 * k, val, two{});
       }
     } else {
@@ -644,8 +655,9 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
       cplx<T> z;
       if (bc == BC_P) {
         z = {X(2 * p), X(2 * p + 1)};
-      } else if (bc == BC_ND) {
-        z = cmul(cplx<T>{X(2 * p), X(N - 1 - 2 * p)}, xtw[p]);
+      } else if (bc_iv(bc)) {  // DN: the reversed line, the two reals swap
+        const T e0 = X(2 * p), e1 = X(N - 1 - 2 * p);
+        z = cmul(bc == BC_DN ? cplx<T>{e1, e0} : cplx<T>{e0, e1}, xtw[p]);
       } else {
         const int j0 = 2 * p, j1 = 2 * p + 1;
         T v0 = X(j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0);
@@ -666,7 +678,7 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
 #pragma unroll
       for (int r = 0; r < RL; ++r) buf[(b + q * TPL + r * (M / RL)) * CW + c] = v[q * RL + r];
     __syncthreads();
-    if (bc == BC_ND) {
+    if (bc_iv(bc)) {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int k = b + i * TPL;
@@ -718,7 +730,7 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
     }
   } else {
     // ---- backward pre-processing from the rows into the buffer ----
-    if (bc == BC_ND) {
+    if (bc_iv(bc)) {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int k = b + i * TPL;
@@ -779,7 +791,7 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = buf[(b + r * TPL) * CW + c];
-    if (bc == BC_ND) fft_col<T, M, CW, false, 0, 1>(v, buf, stw, b, c);
+    if (bc_iv(bc)) fft_col<T, M, CW, false, 0, 1>(v, buf, stw, b, c);
     else fft_col<T, M, CW, true, 0, 1>(v, buf, stw, b, c);
     // ---- backward post-processing straight from the last stage to the rows ----
     const T inv_m = (T)1 / (T)M;
@@ -789,10 +801,11 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
       for (int r = 0; r < RL; ++r) {
         const int k = b + q * TPL + r * (M / RL);
         const cplx<T> zk = v[q * RL + r];
-        if (bc == BC_ND) {
+        if (bc_iv(bc)) {
           const cplx<T> cc = cmul(xtw[M + k], zk);
-          Y(2 * k, cc.x * ((T)1 / (T)N) * s);
-          Y(N - 1 - 2 * k, -cc.y * ((T)1 / (T)N) * s);
+          const bool sw = (bc == BC_DN);
+          Y(sw ? N - 1 - 2 * k : 2 * k, cc.x * ((T)1 / (T)N) * s);
+          Y(sw ? 2 * k : N - 1 - 2 * k, -cc.y * ((T)1 / (T)N) * s);
         } else if (bc == BC_P) {
           Y(2 * k, zk.x * inv_m * s);
           Y(2 * k + 1, zk.y * inv_m * s);

@@ -27,6 +27,7 @@ SMALL = [
     dict(nx=24, ny=64, nz=30, bcs=("ND", "NN", "DD"), stretched=True),
     dict(nx=96, ny=16, nz=12, bcs=("NN", "NN", "NN"), stretched=True),
     dict(nx=16, ny=96, nz=8, bcs=("P", "NN", "P"), stretched=False),
+    dict(nx=48, ny=24, nz=18, bcs=("DN", "ND", "DN"), stretched=True),
 ]
 
 

@@ -19,7 +19,7 @@ from paper_1802_10323_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-BCS = ("P", "NN", "DD", "ND")
+BCS = ("P", "NN", "DD", "ND", "DN")  # DN: not in Table 1, the reversed ND axis
 
 
 def _run(lib, f, dx, dy, zf, bcs, precision="fp64", transpose=False, **kw):
