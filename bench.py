@@ -351,6 +351,30 @@ def bench_ours(args):
         planh.close()
         plan.solve(f, p, info=info)  # p again holds the Poisson solution (e2e below reuses it)
 
+    # ---- the D-N pair (not in Table 1) on x and z of the same grid and input ----
+    dn = None
+    if not args.no_dn:
+        bcs_dn = ("DN", BCS[1], "DN")
+        pland = lib.Plan(n[0], n[1], n[2], dx, dy, zf=zf, bcs=bcs_dn, precision="fp32_refine",
+                         rtol=RTOL, max_iter=MAX_ITER)
+        infd = lib.info_tensor(dev)
+        for _ in range(args.warmup):
+            pland.solve(f, p, info=infd)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            pland.solve(f, p, info=infd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msd = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        idn = lib.read_info(infd)
+        dn = {"value": job_rate(world, N, msd), "unit": "Mpts/s", "ms_per_step": msd, "bcs": list(bcs_dn),
+              "iterations": idn.iterations, "rel_residual": idn.rel_residual, "status": idn.status,
+              "workload": "the same grid and f with Dirichlet-Neumann pairs on x and z, FP32+refine to 1e-10"}
+        pland.close()
+        plan.solve(f, p, info=info)
+
     # ---- end to end through the public host-buffer call ----
     e2e = None
     if not args.no_e2e:
@@ -440,6 +464,7 @@ def bench_ours(args):
             "cpu_baseline": cpu,
             "batch_64": batch,
             "helmholtz": helm,
+            "dirichlet_neumann": dn,
         }
         print(json.dumps(line))
     plan.close()
@@ -461,6 +486,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-helmholtz", action="store_true")
+    ap.add_argument("--no-dn", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
