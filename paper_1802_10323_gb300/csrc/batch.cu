@@ -258,7 +258,7 @@ __device__ void finalize_grid(const BGrid& G, Ctrl* c, const float* partial, dou
   if (ok) c->converged = 1;
 }
 
-__global__ void __launch_bounds__(256) batch_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(256, 4) batch_kernel(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_task, s_run;
   for (;;) {

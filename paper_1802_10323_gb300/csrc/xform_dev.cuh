@@ -300,9 +300,9 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
       if (bc_iv(bc)) {
         const T s = (T)1 / (T)n;  // 2·(1/2n)
         cplx<T> c = cmul(tw[4 * k + 1], Z[k]);
-        const bool sw = (bc == BC_DN);
-        o[sw ? n - 1 - 2 * k : 2 * k] = s * c.x;
-        o[sw ? 2 * k : n - 1 - 2 * k] = -s * c.y;
+        const T A = s * c.x, B = -s * c.y;  // DN: the two outputs trade places
+        o[2 * k] = (bc == BC_DN) ? B : A;
+        o[n - 1 - 2 * k] = (bc == BC_DN) ? A : B;
       } else if (bc == BC_P) {
         o[2 * k] = Z[k].x * inv_m;
         o[2 * k + 1] = Z[k].y * inv_m;

@@ -321,9 +321,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) xform_fast_kernel
             const cplx<T> zk = v[q * RL + r];
             if (bc_iv(bc)) {
               const cplx<T> c = cmul(xtw[M + k], zk);
-              const bool sw = (bc == BC_DN);
-              lr[sw ? N - 1 - 2 * k : 2 * k] = c.x * ((T)1 / (T)N);
-              lr[sw ? 2 * k : N - 1 - 2 * k] = -c.y * ((T)1 / (T)N);
+              const T A = c.x * ((T)1 / (T)N), B = -c.y * ((T)1 / (T)N);  // DN: trade places
+              lr[2 * k] = (bc == BC_DN) ? B : A;
+              lr[N - 1 - 2 * k] = (bc == BC_DN) ? A : B;
             } else if (bc == BC_P) {
               lr[2 * k] = zk.x * inv_m;
               lr[2 * k + 1] = zk.y * inv_m;

@@ -112,20 +112,17 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
     } else if (bc_iv(bc)) {
       // z_p = (x_{2p}, x_{n−1−2p})·e^{−iπp/n}; x_{n−1−2p} = x_{2p'+1} of p' = M−1−p
       // (DN, the reversed line: z_p = (x_{n−1−2p}, x_{2p}), the two parts trade places)
-      const bool sw = (bc == BC_DN);
 #pragma unroll
       for (int si = 0; si < E; ++si) {
         const int p = t + (si / R0) * TPL + (si % R0) * (M / R0);
         const vec<TI, 2> x = *reinterpret_cast<const vec<TI, 2>*>(src + 2 * p);
-        const T even = in_cvt<T>(x.v[0]) * s;
-        const T odd = __shfl_sync(full, in_cvt<T>(x.v[1]) * s, mate);
-        if (sw) {
-          v[si].y = even;
-          v[E - 1 - si].x = odd;
-        } else {
-          v[si].x = even;
-          v[E - 1 - si].y = odd;
-        }
+        v[si].x = in_cvt<T>(x.v[0]) * s;
+        const T odd = in_cvt<T>(x.v[1]) * s;
+        v[E - 1 - si].y = __shfl_sync(full, odd, mate);
+      }
+      if (bc == BC_DN) {
+#pragma unroll
+        for (int si = 0; si < E; ++si) v[si] = {v[si].y, v[si].x};
       }
 #pragma unroll
       for (int si = 0; si < E; ++si) {
@@ -484,15 +481,14 @@ __device__ __forceinline__ void row_line(const FastArgs<T>& a, const cplx<T>* st
       for (int si = 0; si < E; ++si) {
         const int k = t + (si / RL) * TPL + (si % RL) * (M / RL);
         const cplx<T> c = cmul(xtw[M + k], v[si]);
-        re[si] = c.x * inv_n;
-        im[si] = -c.y * inv_n;
+        const T A = c.x * inv_n, B = -c.y * inv_n;
+        re[si] = (bc == BC_DN) ? B : A;
+        im[si] = (bc == BC_DN) ? A : B;
       }
-      const bool sw = (bc == BC_DN);
 #pragma unroll
       for (int si = 0; si < E; ++si) {
         const int k = t + (si / RL) * TPL + (si % RL) * (M / RL);
-        const T mine = sw ? im[si] : re[si];
-        const T val[2] = {mine, __shfl_sync(full, sw ? re[E - 1 - si] : im[E - 1 - si], mate)};
+        const T val[2] = {re[si], __shfl_sync(full, im[E - 1 - si], mate)};
         put(2 * k, val, two{});
       }
     } else {
@@ -639,10 +635,15 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
   const int nx = a.nx, ny = a.ny;
   const int tpz = nx / CW;
   const int zb = g / tpz, x0 = (g - zb * tpz) * CW;
-  const T* src = in + (size_t)zb * ny * nx + x0 + c;  // row q of this column: src[q·nx]
+  // DN is the ND problem on the reversed line: the forward transform reads its input
+  // rows from row n−1 downwards and runs the ND code unchanged; the backward one swaps
+  // the two outputs of each wavenumber
+  const bool rv = FWD && (bc == BC_DN);
+  const int sstr = rv ? -nx : nx;
+  const T* src = in + (size_t)zb * ny * nx + x0 + c + (rv ? (size_t)(N - 1) * nx : 0);
   T* dst = out + (size_t)zb * ny * nx + x0 + c;
   // row offsets fit in 32 bits (n_y·n_x ≤ 2^20)
-  auto X = [&](int q) { return src[q * nx]; };
+  auto X = [&](int q) { return src[q * sstr]; };
   auto Y = [&](int q, T val) { dst[q * nx] = val; };
   const T s = a.plane_scale ? a.plane_scale[zb] : (T)1;
   cplx<T> v[E];
@@ -655,9 +656,8 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
       cplx<T> z;
       if (bc == BC_P) {
         z = {X(2 * p), X(2 * p + 1)};
-      } else if (bc_iv(bc)) {  // DN: the reversed line, the two reals swap
-        const T e0 = X(2 * p), e1 = X(N - 1 - 2 * p);
-        z = cmul(bc == BC_DN ? cplx<T>{e1, e0} : cplx<T>{e0, e1}, xtw[p]);
+      } else if (bc_iv(bc)) {  // (DN: rows addressed in reverse, see above)
+        z = cmul(cplx<T>{X(2 * p), X(N - 1 - 2 * p)}, xtw[p]);
       } else {
         const int j0 = 2 * p, j1 = 2 * p + 1;
         T v0 = X(j0 < M ? 2 * j0 : 2 * N - 1 - 2 * j0);
@@ -803,9 +803,14 @@ __device__ __forceinline__ void col_tile(const FastArgs<T>& a, const cplx<T>* st
         const cplx<T> zk = v[q * RL + r];
         if (bc_iv(bc)) {
           const cplx<T> cc = cmul(xtw[M + k], zk);
-          const bool sw = (bc == BC_DN);
-          Y(sw ? N - 1 - 2 * k : 2 * k, cc.x * ((T)1 / (T)N) * s);
-          Y(sw ? 2 * k : N - 1 - 2 * k, -cc.y * ((T)1 / (T)N) * s);
+          const T A = cc.x * ((T)1 / (T)N) * s, B = -cc.y * ((T)1 / (T)N) * s;
+          if (bc == BC_DN) {
+            Y(2 * k, B);
+            Y(N - 1 - 2 * k, A);
+          } else {
+            Y(2 * k, A);
+            Y(N - 1 - 2 * k, B);
+          }
         } else if (bc == BC_P) {
           Y(2 * k, zk.x * inv_m * s);
           Y(2 * k + 1, zk.y * inv_m * s);
