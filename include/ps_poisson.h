@@ -36,7 +36,7 @@ extern "C" {
 typedef enum {
   PS_OK = 0,
   PS_INVALID_ARG = 1,        /* null pointer, bad spacing, inconsistent sizes   */
-  PS_UNSUPPORTED_SIZE = 2,   /* n odd, n < 2, n > 1024, or n/2 not 2^a·3^b     */
+  PS_UNSUPPORTED_SIZE = 2,   /* n odd, n < 2, n > 8192, or n/2 not 2^a·3^b     */
   PS_CUDA_ERROR = 3,         /* a CUDA runtime call failed (see ps_last_error)  */
   PS_OUT_OF_MEMORY = 4,      /* cudaMalloc of plan tables failed                */
   PS_NOT_CONVERGED = 5,      /* refinement did not reach rtol in max_iter       */
@@ -85,7 +85,10 @@ typedef struct ps_batch ps_batch;
 /* Create a plan (§2.1; Table 1 eigenvalues λ_q = −4 sin²θ_q / Δ² and the
  * Table 2 twiddles are computed here in FP64, cast once for FP32 paths; the
  * z coefficients follow the finite-volume form of Eq. 4 on the faces zf).
- *   nx, ny, nz   cells per axis; each even, 2 ≤ n ≤ 1024, n/2 = 2^a·3^b.
+ *   nx, ny       cells along x and y; each even, 2 ≤ n ≤ 8192, n/2 = 2^a·3^b
+ *                (lines of n ≤ 1024 run in register-resident transform kernels,
+ *                longer ones one line per CTA in shared memory).
+ *   nz           cells along z, 2 ≤ nz ≤ 8192.
  *   dx, dy       uniform spacings (> 0).
  *   zf           host array of nz+1 increasing face coordinates, or NULL for a
  *                uniform z of spacing dz (> 0). Copied; the caller keeps it.

@@ -14,7 +14,10 @@ enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3, BC_DN = 4 };
 // line, so on the physical side of a transform the two reals x_{2p} and x_{n−1−2p}
 // trade places; the spectral side, the tables and the eigenvalues are ND's.
 __host__ __device__ inline bool bc_iv(int bc) { return bc == BC_ND || bc == BC_DN; }
-constexpr int kMaxN = 1024;
+// Longest x or y line: lines of n ≤ 1024 run in the register-resident transform
+// kernels; longer ones in the shared-memory kernel, one line per CTA (two buffers
+// of n/2 + 1 complex values: 131 KB for an FP64 line of 8192)
+constexpr int kMaxN = 8192;
 constexpr int kMaxStages = 12;
 extern thread_local char g_launch_diag[256];  // configuration of the last failed launch
 

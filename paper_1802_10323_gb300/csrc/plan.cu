@@ -616,7 +616,7 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   if (!(dx > 0) || !(dy > 0)) return fail(nullptr, PS_INVALID_ARG, "dx and dy must be > 0");
   if (!zf && !(dz > 0)) return fail(nullptr, PS_INVALID_ARG, "dz must be > 0 when zf is NULL");
   if (!size_ok(nx) || !size_ok(ny))
-    return fail(nullptr, PS_UNSUPPORTED_SIZE, "nx, ny must be even, 2..1024, with n/2 = 2^a 3^b");
+    return fail(nullptr, PS_UNSUPPORTED_SIZE, "nx, ny must be even, 2..8192, with n/2 = 2^a 3^b");
   if (nz < 2 || nz > 8192) return fail(nullptr, PS_UNSUPPORTED_SIZE, "nz must be in 2..8192");
   if (prec == PS_FP32_REFINE && (max_iter < 0 || !(rtol > 0)))
     return fail(nullptr, PS_INVALID_ARG, "refinement needs rtol > 0 and max_iter >= 0");

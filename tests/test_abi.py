@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(binding):
     assert declared == set(binding.EXPORTS)
 
 
-@pytest.mark.parametrize("n,status", [(0, 2), (3, 2), (7, 2), (2048, 2), (10, 2), (14, 2)])
+@pytest.mark.parametrize("n,status", [(0, 2), (3, 2), (7, 2), (16384, 2), (10, 2), (14, 2), (5120, 2)])
 def test_unsupported_sizes_rejected(binding, n, status):
     h = ctypes.c_void_p()
     st = binding.ps_plan_create(ctypes.byref(h), n, 8, 8, 1.0, 1.0, None, 1.0, 0, 0, 1, 0, 1e-10, 3)
