@@ -187,6 +187,28 @@ const char* ps_last_error(const ps_plan* plan);
  * Field types follow the plan: float for PS_FP32 plans, double otherwise. All
  * pointers are device pointers; the calls enqueue one kernel on the stream. */
 
+/* One substep k ∈ {1, 2, 3} of the low-storage RK3 fractional-step integration of
+ * §2 around the solve (Eqs. 2a–2d), α_k = 8/15, 5/12, 3/4, β_k = 0, −17/60, −5/12,
+ * γ_k = α_k + β_k:
+ *   u* = u + Δt (α_k AD^k + β_k AD^{k−1} − γ_k G p),   AD = −(u·∇)u + ν∇²u,
+ *   solve A Φ' = D u* (Φ' = γ_k Δt Φ),  u ← u* − G Φ',  p ← p + Φ,
+ * on the staggered layout of the projection operators above. AD is second-order
+ * central: advection in divergence form with arithmetic averages, the viscous term
+ * the finite-volume second differences of Eq. 4, each on its component's control
+ * volume. The plan must be a Poisson plan (α = 0) with periodic x and y and a
+ * periodic or NEUMANN_NEUMANN z; the latter means no-slip walls: w = 0 on the wall
+ * faces, tangential ghosts mirrored with the opposite sign.
+ *   u      3·N stacked faces [u | v | w]: u^k in, u^{k+1} out (divergence-free).
+ *   ustar  3·N scratch (u*), distinct from u.
+ *   ad     3·N: AD^{k−1} in (not read when k = 1), AD^k out (in place).
+ *   p      N cells: p^{k−1/2} in, p^{k+1/2} out.
+ *   phi    N cells: Φ out.   rhs: N cells of scratch (D u*), distinct from phi.
+ *   ws     the solve's workspace (ps_workspace_bytes); info as for ps_solve.
+ * Field types follow the plan (float for PS_FP32, double otherwise); device
+ * pointers; enqueued on the stream (four kernels and the solve). */
+ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, void* ustar, void* ad, void* p,
+                        void* phi, void* rhs, void* ws, void* stream, ps_info* info);
+
 /* f = D·u* (cell-centred right-hand side of Eq. 2b). */
 ps_status ps_div(ps_plan* plan, const void* u, void* f, void* stream);
 /* u = u* − G·φ (Eq. 2c). u may equal ustar. */

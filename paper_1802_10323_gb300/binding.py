@@ -54,6 +54,7 @@ _vp, _i, _d, _st = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int
 _SIGS = {
     "ps_plan_create": [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _vp, _d, _i, _i, _i, _i, _d, _i],
     "ps_plan_create_helmholtz": [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _vp, _d, _i, _i, _i, _i, _d, _i, _d],
+    "ps_ns_substep": [_vp, _i, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "ps_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "ps_solve": [_vp, _vp, _vp, _vp, _vp, _vp],
     "ps_solve_f32": [_vp, _vp, _vp, _vp, _vp, _vp],
@@ -177,6 +178,20 @@ class Plan:
         assert g.is_cuda and g.is_contiguous() and tuple(g.shape) == self.shape
         fn = _lib.ps_solve_transpose_f32 if self.precision == "fp32" else _lib.ps_solve_transpose
         return self._call(fn, g, out, info, stream)
+
+    def ns_substep(self, k, dt, nu, u, ustar, ad, p, phi, rhs, info=None, stream=None):
+        """One RK3 substep k ∈ {1, 2, 3} around the solve (see ps_ns_substep): u, ustar, ad
+        are stacked (3, nz, ny, nx) face fields, p, phi, rhs cell fields, all contiguous CUDA
+        tensors of the plan's dtype; u, ad, p, phi are updated in place."""
+        for t, shp in ((u, (3,) + self.shape), (ustar, (3,) + self.shape), (ad, (3,) + self.shape),
+                       (p, self.shape), (phi, self.shape), (rhs, self.shape)):
+            assert t.is_cuda and t.is_contiguous() and tuple(t.shape) == shp
+        ws = self.workspace(u.device)
+        ip = _vp(info.data_ptr()) if info is not None else None
+        _check(_lib.ps_ns_substep(self.handle, int(k), float(dt), float(nu), _vp(u.data_ptr()),
+                                  _vp(ustar.data_ptr()), _vp(ad.data_ptr()), _vp(p.data_ptr()),
+                                  _vp(phi.data_ptr()), _vp(rhs.data_ptr()), _vp(ws.data_ptr()),
+                                  _stream_ptr(stream), ip), self.handle)
 
     def solve_host(self, f_host, p_host, f_dev, p_dev, stream=None):
         """End-to-end solve from host memory (copies inside the call); returns PsInfo."""

@@ -155,6 +155,24 @@ template <class T>
 cudaError_t launch_projection(int op, const ProjArgs<T>& a, const void* x0, const void* x1, void* y,
                               cudaStream_t st);
 
+// One RK3 substep around the solve (navier_stokes.cu): the predictor (2a) and the
+// pressure update (2d). idzf[k] = 1/Δz^f_k; idzc[k] = 1/(centre distance between
+// cells k−1 and k), idzc[0] the periodic wrap.
+template <class T>
+struct NsArgs {
+  int nx, ny, nz;
+  int per_z;                // z periodic (else no-slip walls)
+  T idx, idy, idx2, idy2;   // 1/Δx, 1/Δy, 1/Δx², 1/Δy²
+  const T* idzf;
+  const T* idzc;
+  T nu, dt, alpha, beta, gamma;
+};
+template <class T>
+cudaError_t launch_ns_predict(const NsArgs<T>& a, const void* u3, const void* p, const void* ad_prev,
+                              void* ustar, void* ad_out, cudaStream_t st);
+template <class T>
+cudaError_t launch_ns_pressure(size_t N, double scale, void* p, void* phi, cudaStream_t st);
+
 // Record a message for ps_last_error(plan).
 void set_plan_error(ps_plan* plan, const char* msg);
 

@@ -1048,6 +1048,63 @@ ps_status ps_div_adjoint_correct(ps_plan* plan, const void* g, const void* s, vo
   return projection_op(plan, 3, g, s, out, stream);
 }
 
+ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, void* ustar, void* ad, void* p,
+                        void* phi, void* rhs, void* ws, void* stream, ps_info* info) {
+  if (!plan) return fail(nullptr, PS_INVALID_ARG, "null plan");
+  if (!u || !ustar || !ad || !p || !phi || !rhs || !ws) return fail(plan, PS_INVALID_ARG, "null pointer");
+  if (u == ustar || phi == rhs || ustar == rhs || u == ad || ustar == ad)
+    return fail(plan, PS_INVALID_ARG, "u, ustar, ad and phi, rhs must be distinct arrays");
+  if (k < 1 || k > 3) return fail(plan, PS_INVALID_ARG, "the RK3 substep k must be 1, 2 or 3");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !(nu >= 0.0) || !std::isfinite(nu))
+    return fail(plan, PS_INVALID_ARG, "dt must be > 0 and nu >= 0 (finite)");
+  if (plan->bcx != PS_BC_PERIODIC || plan->bcy != PS_BC_PERIODIC ||
+      (plan->bcz != PS_BC_PERIODIC && plan->bcz != PS_BC_NEUMANN_NEUMANN))
+    return fail(plan, PS_INVALID_ARG, "the substep needs periodic x and y, and a periodic or Neumann (wall) z");
+  if (plan->alpha != 0.0) return fail(plan, PS_INVALID_ARG, "the substep needs a Poisson plan (alpha = 0)");
+  static const double kAlpha[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+  static const double kBeta[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+  const double al = kAlpha[k - 1], be = kBeta[k - 1], ga = al + be;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t N = plan->N;
+  auto body = [&](auto tag) -> ps_status {
+    using T = decltype(tag);
+    NsArgs<T> a{};
+    a.nx = plan->nx;
+    a.ny = plan->ny;
+    a.nz = plan->nz;
+    a.per_z = plan->bcz == PS_BC_PERIODIC;
+    a.idx = (T)(1.0 / plan->dx);
+    a.idy = (T)(1.0 / plan->dy);
+    a.idx2 = (T)(1.0 / (plan->dx * plan->dx));
+    a.idy2 = (T)(1.0 / (plan->dy * plan->dy));
+    if constexpr (sizeof(T) == 8) { a.idzf = plan->idzf64; a.idzc = plan->idzc64; }
+    else { a.idzf = plan->idzf32; a.idzc = plan->idzc32; }
+    a.nu = (T)nu;
+    a.dt = (T)dt;
+    a.alpha = (T)al;
+    a.beta = (T)be;
+    a.gamma = (T)ga;
+    cudaError_t e;
+    if ((e = launch_ns_predict<T>(a, u, p, ad, ustar, ad, st)) != cudaSuccess)
+      return cuda_fail(plan, e, "substep predictor");
+    const ProjArgs<T> pa = proj_args<T>(plan);
+    if ((e = launch_projection<T>(0, pa, ustar, nullptr, rhs, st)) != cudaSuccess)
+      return cuda_fail(plan, e, "substep divergence");
+    ps_status s;
+    if constexpr (sizeof(T) == 4)
+      s = ps_solve_f32(plan, static_cast<const float*>(rhs), static_cast<float*>(phi), ws, stream, info);
+    else
+      s = ps_solve(plan, static_cast<const double*>(rhs), static_cast<double*>(phi), ws, stream, info);
+    if (s != PS_OK) return s;
+    if ((e = launch_projection<T>(1, pa, ustar, phi, u, st)) != cudaSuccess)
+      return cuda_fail(plan, e, "substep projection");
+    if ((e = launch_ns_pressure<T>(N, 1.0 / (ga * dt), p, phi, st)) != cudaSuccess)
+      return cuda_fail(plan, e, "substep pressure update");
+    return PS_OK;
+  };
+  return plan->prec == PS_FP32 ? body(float{}) : body(double{});
+}
+
 ps_status ps_plan_destroy(ps_plan* plan) {
   if (!plan) return PS_OK;
   for (auto& ev : plan->prof.ev) cudaEventDestroy(ev);

@@ -83,3 +83,8 @@ def test_helmholtz_shift_validated(binding, alpha):
     assert st == binding.PS_INVALID_ARG
     assert not h.value
     assert b"alpha" in binding.ps_last_error(None)
+
+
+def test_ns_substep_null_plan(binding):
+    assert binding.ps_ns_substep(None, 1, 1e-3, 0.0, None, None, None, None, None, None, None, None,
+                                 None) == binding.PS_INVALID_ARG
