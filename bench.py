@@ -410,6 +410,50 @@ def bench_ours(args):
         del fl, pl_, planl
         torch.cuda.empty_cache()
 
+    # ---- one RK3 time step of the fractional-step integration around the solve (§2):
+    # the 512 x 256 x 256 channel (6x3x1, P/P/NN, tanh z), FP64 fields, refined solves ----
+    ns = None
+    if not args.no_ns and args.n == 1024 and not args.nz:
+        from paper_1802_10323_gb300 import synth
+        n5 = (512, 256, 256)
+        z5 = synth.tanh_faces(n5[2], 1.0, 1.5)
+        plan5 = lib.Plan(n5[0], n5[1], n5[2], 6.0 / n5[0], 3.0 / n5[1], zf=z5, bcs=BCS,
+                         precision="fp32_refine", rtol=RTOL, max_iter=MAX_ITER)
+        uu, vv, ww = synth.staggered_velocity_torch(n5[0], n5[1], n5[2], 5, device=dev)
+        u5 = torch.stack([uu, vv, ww]).contiguous()
+        del uu, vv, ww
+        us5, ad5 = torch.empty_like(u5), torch.zeros_like(u5)
+        p5 = torch.zeros((n5[2], n5[1], n5[0]), dtype=torch.float64, device=dev)
+        phi5, rhs5 = torch.empty_like(p5), torch.empty_like(p5)
+        inf5 = lib.info_tensor(dev)
+        dt5, nu5 = 1e-3, 1.0 / 5600.0
+
+        def rk3():
+            for kk in (1, 2, 3):
+                plan5.ns_substep(kk, dt5, nu5, u5, us5, ad5, p5, phi5, rhs5, info=inf5)
+
+        for _ in range(2):
+            rk3()
+        torch.cuda.synchronize()
+        barrier()
+        k5 = max(1, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(k5):
+            rk3()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms5 = max_over_ranks(e0.elapsed_time(e1) / k5)
+        i5 = lib.read_info(inf5)
+        ns = {"value": job_rate(world, n5[0] * n5[1] * n5[2], ms5), "unit": "Mpts/s (cells x RK3 steps)",
+              "ms_per_rk3_step": ms5, "grid": list(n5), "last_solve_status": i5.status,
+              "last_solve_rel_residual": i5.rel_residual,
+              "workload": "3 substeps of ps_ns_substep (predictor, divergence, refined solve to 1e-10, "
+                          "projection, pressure update) per step; FP64 fields; Gaussian staggered velocity "
+                          "(seed 5), nu = 1/5600, dt = 1e-3"}
+        plan5.close()
+        del u5, us5, ad5, p5, phi5, rhs5, plan5
+        torch.cuda.empty_cache()
+
     # ---- end to end through the public host-buffer call ----
     e2e = None
     if not args.no_e2e:
@@ -506,6 +550,7 @@ def bench_ours(args):
             "helmholtz": helm,
             "dirichlet_neumann": dn,
             "long_lines": longl,
+            "rk3_step": ns,
         }
         print(json.dumps(line))
     plan.close()
@@ -529,6 +574,7 @@ def main():
     ap.add_argument("--no-helmholtz", action="store_true")
     ap.add_argument("--no-dn", action="store_true")
     ap.add_argument("--no-long", action="store_true")
+    ap.add_argument("--no-ns", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
