@@ -163,6 +163,7 @@ struct NsArgs {
   int nx, ny, nz;
   int per_z;                // z periodic (else no-slip walls)
   T idx, idy, idx2, idy2;   // 1/Δx, 1/Δy, 1/Δx², 1/Δy²
+  T qx, qy;                 // ¼/Δx, ¼/Δy (flux differences of products of two sums)
   const T* idzf;
   const T* idzc;
   T nu, dt, alpha, beta, gamma;

@@ -37,7 +37,6 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
   const T* __restrict__ U = u3;
   const T* __restrict__ V = u3 + N;
   const T* __restrict__ W = u3 + 2 * N;
-  const T h = (T)0.5;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(g % nx);
     const size_t t = g / nx;
@@ -59,27 +58,27 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
     auto Wv = [&](long off, int kk) -> T { return (!per && kk == 0) ? (T)0 : W[g + off]; };
     const T uc = U[g], vc = V[g], wc = Wv(0, k);
 
+    // Every flux below is a product of two sums of neighbours (an average each): the two
+    // factors ½ go into one factor ¼ on the flux difference (q* = ¼/Δ), and the normal
+    // term d(ū²) = ((a + b)² − (c + a)²)/4 is formed as (b − c)(b + 2a + c)/4.
     // ---------------- x momentum at x face i ----------------
     T adu;
     {
       const T uxp = U[g + dxp], uxm = U[g + dxm];
       const T uyp = U[g + dyp], uym = U[g + dym];
       const T uzp = has_up ? U[g + dzp] : -uc, uzm = has_dn ? U[g + dzm] : -uc;
-      const T ucc = h * (uc + uxp), ucl = h * (uxm + uc);
-      const T duu = (ucc * ucc - ucl * ucl) * a.idx;
+      const T duu = (uxp - uxm) * (uxp + 2 * uc + uxm) * a.qx;
       // uv on the y faces j and j+1 of this x face
-      const T uv0 = h * (uc + uym) * h * (vc + V[g + dxm]);
-      const T uv1 = h * (uyp + uc) * h * (V[g + dyp] + V[g + dyp + dxm]);
-      const T duv = (uv1 - uv0) * a.idy;
-      // uw on the z faces k and k+1 of this x face
-      const T w0 = has_dn ? h * (wc + Wv(dxm, k)) : (T)0;     // (k = 0 on a wall: w = 0)
-      const T uw0 = h * (uc + uzm) * w0;
-      const T w1 = has_up ? h * (Wv(dzp, k + 1 < nz ? k + 1 : 0) + Wv(dzp + dxm, k + 1 < nz ? k + 1 : 0)) : (T)0;
-      const T uw1 = h * (uzp + uc) * w1;
-      const T duw = (uw1 - uw0) * idzf;
+      const T uv0 = (uc + uym) * (vc + V[g + dxm]);
+      const T uv1 = (uyp + uc) * (V[g + dyp] + V[g + dyp + dxm]);
+      const T duv = (uv1 - uv0) * a.qy;
+      // uw on the z faces k and k+1 of this x face (k = 0 on a wall: w = 0)
+      const T uw0 = has_dn ? (uc + uzm) * (wc + Wv(dxm, k)) : (T)0;
+      const T uw1 = has_up ? (uzp + uc) * (Wv(dzp, k + 1 < nz ? k + 1 : 0) + Wv(dzp + dxm, k + 1 < nz ? k + 1 : 0)) : (T)0;
+      const T duw = (uw1 - uw0) * ((T)0.25 * idzf);
       const T lap = (uxp - 2 * uc + uxm) * a.idx2 + (uyp - 2 * uc + uym) * a.idy2 +
                     ((uzp - uc) * ihup - (uc - uzm) * ihdn) * idzf;
-      adu = -(duu + duv + duw) + a.nu * lap;
+      adu = a.nu * lap - (duu + duv + duw);
     }
     // ---------------- y momentum at y face j ----------------
     T adv;
@@ -87,20 +86,17 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
       const T vxp = V[g + dxp], vxm = V[g + dxm];
       const T vyp = V[g + dyp], vym = V[g + dym];
       const T vzp = has_up ? V[g + dzp] : -vc, vzm = has_dn ? V[g + dzm] : -vc;
-      const T vcc = h * (vc + vyp), vcl = h * (vym + vc);
-      const T dvv = (vcc * vcc - vcl * vcl) * a.idy;
+      const T dvv = (vyp - vym) * (vyp + 2 * vc + vym) * a.qy;
       // uv on the x faces i and i+1 of this y face
-      const T uv0 = h * (uc + U[g + dym]) * h * (vc + vxm);
-      const T uv1 = h * (U[g + dxp] + U[g + dxp + dym]) * h * (vxp + vc);
-      const T duv = (uv1 - uv0) * a.idx;
-      const T w0 = has_dn ? h * (wc + Wv(dym, k)) : (T)0;
-      const T vw0 = h * (vc + vzm) * w0;
-      const T w1 = has_up ? h * (Wv(dzp, k + 1 < nz ? k + 1 : 0) + Wv(dzp + dym, k + 1 < nz ? k + 1 : 0)) : (T)0;
-      const T vw1 = h * (vzp + vc) * w1;
-      const T dvw = (vw1 - vw0) * idzf;
+      const T uv0 = (uc + U[g + dym]) * (vc + vxm);
+      const T uv1 = (U[g + dxp] + U[g + dxp + dym]) * (vxp + vc);
+      const T duv = (uv1 - uv0) * a.qx;
+      const T vw0 = has_dn ? (vc + vzm) * (wc + Wv(dym, k)) : (T)0;
+      const T vw1 = has_up ? (vzp + vc) * (Wv(dzp, k + 1 < nz ? k + 1 : 0) + Wv(dzp + dym, k + 1 < nz ? k + 1 : 0)) : (T)0;
+      const T dvw = (vw1 - vw0) * ((T)0.25 * idzf);
       const T lap = (vxp - 2 * vc + vxm) * a.idx2 + (vyp - 2 * vc + vym) * a.idy2 +
                     ((vzp - vc) * ihup - (vc - vzm) * ihdn) * idzf;
-      adv = -(duv + dvv + dvw) + a.nu * lap;
+      adv = a.nu * lap - (duv + dvv + dvw);
     }
     // ---------------- z momentum at z face k ----------------
     T adw = (T)0;
@@ -109,19 +105,19 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
       const T wzp = has_up ? Wv(dzp, kup) : (T)0;
       const int kdn = k > 0 ? k - 1 : nz - 1;
       const T wzm = Wv(dzm, kdn);
-      const T wcc = h * (wc + wzp), wcl = h * (wzm + wc);
-      const T dww = (wcc * wcc - wcl * wcl) * ihdn;
+      const T wxp = Wv(dxp, k), wxm = Wv(dxm, k), wyp = Wv(dyp, k), wym = Wv(dym, k);
+      const T dww = (wzp - wzm) * (wzp + 2 * wc + wzm) * ((T)0.25 * ihdn);
       // uw on the x faces i and i+1 of this z face (u averaged over cells k−1 and k)
-      const T uw0 = h * (uc + U[g + dzm]) * h * (wc + Wv(dxm, k));
-      const T uw1 = h * (U[g + dxp] + U[g + dxp + dzm]) * h * (Wv(dxp, k) + wc);
-      const T duw = (uw1 - uw0) * a.idx;
-      const T vw0 = h * (vc + V[g + dzm]) * h * (wc + Wv(dym, k));
-      const T vw1 = h * (V[g + dyp] + V[g + dyp + dzm]) * h * (Wv(dyp, k) + wc);
-      const T dvw = (vw1 - vw0) * a.idy;
+      const T uw0 = (uc + U[g + dzm]) * (wc + wxm);
+      const T uw1 = (U[g + dxp] + U[g + dxp + dzm]) * (wxp + wc);
+      const T duw = (uw1 - uw0) * a.qx;
+      const T vw0 = (vc + V[g + dzm]) * (wc + wym);
+      const T vw1 = (V[g + dyp] + V[g + dyp + dzm]) * (wyp + wc);
+      const T dvw = (vw1 - vw0) * a.qy;
       const T idzf_m = a.idzf[kdn];
-      const T lap = (Wv(dxp, k) - 2 * wc + Wv(dxm, k)) * a.idx2 + (Wv(dyp, k) - 2 * wc + Wv(dym, k)) * a.idy2 +
+      const T lap = (wxp - 2 * wc + wxm) * a.idx2 + (wyp - 2 * wc + wym) * a.idy2 +
                     ((wzp - wc) * idzf - (wc - wzm) * idzf_m) * ihdn;
-      adw = -(duw + dvw + dww) + a.nu * lap;
+      adw = a.nu * lap - (duw + dvw + dww);
     }
 
     // ---------------- predictor (2a) ----------------

@@ -1077,6 +1077,8 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
     a.idy = (T)(1.0 / plan->dy);
     a.idx2 = (T)(1.0 / (plan->dx * plan->dx));
     a.idy2 = (T)(1.0 / (plan->dy * plan->dy));
+    a.qx = (T)(0.25 / plan->dx);
+    a.qy = (T)(0.25 / plan->dy);
     if constexpr (sizeof(T) == 8) { a.idzf = plan->idzf64; a.idzc = plan->idzc64; }
     else { a.idzf = plan->idzf32; a.idzc = plan->idzc32; }
     a.nu = (T)nu;
