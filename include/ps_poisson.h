@@ -261,6 +261,12 @@ typedef struct {
  * every grid are built as in ps_plan_create. */
 ps_status ps_batch_create(ps_batch** out, int count, const ps_grid_desc* descs,
                           ps_precision prec, double rtol, int max_iter);
+/* The same with a Helmholtz shift per grid (see ps_plan_create_helmholtz): grid g
+ * solves (A − alphas[g]·I)·p = f. alphas: host array of count values ≥ 0 (copied),
+ * or NULL for all zero (ps_batch_create). PS_INVALID_ARG for a negative or
+ * non-finite shift (the message names the grid). */
+ps_status ps_batch_create_helmholtz(ps_batch** out, int count, const ps_grid_desc* descs,
+                                    ps_precision prec, double rtol, int max_iter, const double* alphas);
 
 /* Workspace bytes for one batched solve. */
 ps_status ps_batch_workspace_bytes(const ps_batch* batch, size_t* bytes);

@@ -70,6 +70,8 @@ _SIGS = {
     "ps_profile_enable": [_vp, _i],
     "ps_profile_read": [_vp, ctypes.POINTER(PsKernelStat), _i, ctypes.POINTER(_i)],
     "ps_batch_create": [ctypes.POINTER(_vp), _i, ctypes.POINTER(PsGridDesc), _i, _d, _i],
+    "ps_batch_create_helmholtz": [ctypes.POINTER(_vp), _i, ctypes.POINTER(PsGridDesc), _i, _d, _i,
+                                  ctypes.POINTER(ctypes.c_double)],
     "ps_batch_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "ps_batch_solve": [_vp, _vp, _vp, _vp, _vp, _vp],
     "ps_batch_destroy": [_vp],
@@ -228,7 +230,8 @@ class Plan:
 class Batch:
     """Many independent grids solved by one persistent launch (see ps_batch_create).
 
-    grids: list of dicts with nx, ny, nz, dx, dy, zf (array or None), dz, bcs.
+    grids: list of dicts with nx, ny, nz, dx, dy, zf (array or None), dz, bcs, and an
+    optional Helmholtz shift alpha (see ps_batch_create_helmholtz).
     """
 
     def __init__(self, grids, rtol=1e-10, max_iter=3):
@@ -246,8 +249,14 @@ class Batch:
             descs[g] = PsGridDesc(d["nx"], d["ny"], d["nz"], float(d["dx"]), float(d["dy"]), zp,
                                   float(d.get("dz") or 0.0), BC[bcs[0]], BC[bcs[1]], BC[bcs[2]])
         h = _vp()
-        st = _lib.ps_batch_create(ctypes.byref(h), self.count, descs, PRECISION["fp32_refine"],
-                                  float(rtol), int(max_iter))
+        alphas = [float(d.get("alpha", 0.0)) for d in grids]
+        if any(alphas):
+            arr = (ctypes.c_double * self.count)(*alphas)
+            st = _lib.ps_batch_create_helmholtz(ctypes.byref(h), self.count, descs, PRECISION["fp32_refine"],
+                                                float(rtol), int(max_iter), arr)
+        else:
+            st = _lib.ps_batch_create(ctypes.byref(h), self.count, descs, PRECISION["fp32_refine"],
+                                      float(rtol), int(max_iter))
         if st != PS_OK:
             raise PoissonError(st, _lib.ps_batch_last_error(None).decode())
         self.handle = h

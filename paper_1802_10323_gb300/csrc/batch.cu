@@ -50,6 +50,8 @@ struct BGrid {
   const float *lamx, *lamy, *za, *zb, *zc, *dzf;
   const float2 *zlo, *zhi;
   df idx2, idy2;
+  int shift;               // Helmholtz grid: the residual row also holds −α·Φ
+  df nalpha;               // −α in double-float
   double wsum_total;
   size_t ws_off;           // this grid's slice: partials | w | scr | scr_u
   size_t off_w, off_scr, off_scru;
@@ -151,8 +153,9 @@ __device__ void residual_tile(const BGrid& G, const double* f, const double* p, 
     const df dzm = bnb(zl, k > 0, (k > 0) ? pp - sxy : pp + (size_t)(nz - 1) * sxy, pc);
     const df dzp = bnb(zh, k < nz - 1, (k < nz - 1) ? pp + sxy : pp - (size_t)(nz - 1) * sxy, pc);
     const float2 cl = G.zlo[k], ch = G.zhi[k];
-    const df ap = df_add(df_add(df_mul(df_add(dxm, dxp), G.idx2), df_mul(df_add(dym, dyp), G.idy2)),
-                         df_add(df_mul(dzm, df{cl.x, cl.y}), df_mul(dzp, df{ch.x, ch.y})));
+    df ap = df_add(df_add(df_mul(df_add(dxm, dxp), G.idx2), df_mul(df_add(dym, dyp), G.idy2)),
+                   df_add(df_mul(dzm, df{cl.x, cl.y}), df_mul(dzp, df{ch.x, ch.y})));
+    if (G.shift) ap = df_add(ap, df_mul(pc, G.nalpha));
     const df fv = df_from_f64(f[g]);
     const df rv = df_sub(G.singular ? df_sub(fv, mu) : fv, ap);
     const float rf = df_to_f32(rv), ff = df_to_f32(fv);
@@ -425,7 +428,10 @@ ps_status build_tables(ps_batch* b) {
     B.nx = d.nx; B.ny = d.ny; B.nz = d.nz;
     B.bcx = d.bcx; B.bcy = d.bcy; B.bcz = d.bcz;
     auto pn = [](int v) { return v == PS_BC_PERIODIC || v == PS_BC_NEUMANN_NEUMANN; };
-    B.singular = pn(d.bcx) && pn(d.bcy) && pn(d.bcz);
+    const double alpha = ps_plan_internal_alpha(pl);  // its z tables carry the shift already
+    B.shift = alpha != 0.0;
+    B.nalpha = df{(float)(-alpha), (float)(-alpha - (double)(float)(-alpha))};
+    B.singular = pn(d.bcx) && pn(d.bcy) && pn(d.bcz) && !B.shift;
     B.periodic_z = d.bcz == PS_BC_PERIODIC;
     ps_plan_internal_tables(pl, &B.twx, &B.twy, &B.lamx, &B.lamy, &B.za, &B.zb, &B.zc, &B.dzf, &B.zlo,
                             &B.zhi, &B.idx2, &B.idy2, &B.wsum_total, B.radx, B.rady, &B.nstx, &B.nsty);
@@ -523,6 +529,11 @@ extern "C" {
 
 ps_status ps_batch_create(ps_batch** out, int count, const ps_grid_desc* descs, ps_precision prec,
                           double rtol, int max_iter) {
+  return ps_batch_create_helmholtz(out, count, descs, prec, rtol, max_iter, nullptr);
+}
+
+ps_status ps_batch_create_helmholtz(ps_batch** out, int count, const ps_grid_desc* descs, ps_precision prec,
+                                    double rtol, int max_iter, const double* alphas) {
   if (!out) return bfail(nullptr, PS_INVALID_ARG, "null output pointer");
   *out = nullptr;
   if (count < 1 || count > 4096 || !descs) return bfail(nullptr, PS_INVALID_ARG, "count must be 1..4096");
@@ -538,8 +549,8 @@ ps_status ps_batch_create(ps_batch** out, int count, const ps_grid_desc* descs, 
   for (int g = 0; g < count; ++g) {
     const ps_grid_desc& d = descs[g];
     ps_plan* pl = nullptr;
-    ps_status st = ps_plan_create(&pl, d.nx, d.ny, d.nz, d.dx, d.dy, d.zf, d.dz, d.bcx, d.bcy, d.bcz,
-                                  PS_FP32_REFINE, rtol, max_iter);
+    ps_status st = ps_plan_create_helmholtz(&pl, d.nx, d.ny, d.nz, d.dx, d.dy, d.zf, d.dz, d.bcx, d.bcy,
+                                            d.bcz, PS_FP32_REFINE, rtol, max_iter, alphas ? alphas[g] : 0.0);
     if (st != PS_OK) {
       char msg[256];
       snprintf(msg, sizeof(msg), "grid %d: %s", g, ps_last_error(nullptr));

@@ -178,6 +178,7 @@ cudaError_t launch_ns_pressure(size_t N, double scale, void* p, void* phi, cudaS
 void set_plan_error(ps_plan* plan, const char* msg);
 
 // The FP32 tables of a plan (used by the batched solve).
+double ps_plan_internal_alpha(const ps_plan* p);  // the plan's Helmholtz shift (0: Poisson)
 void ps_plan_internal_tables(const ps_plan* p, const cplx<float>** twx, const cplx<float>** twy,
                              const float** lamx, const float** lamy, const float** za, const float** zb,
                              const float** zc, const float** dzf, const float2** zlo, const float2** zhi,

@@ -568,6 +568,8 @@ ps_status check_solve_args(ps_plan* p, const void* f, const void* out, const voi
 namespace ps {
 void set_plan_error(ps_plan* plan, const char* msg) { fail(plan, PS_OK, msg); }
 
+double ps_plan_internal_alpha(const ps_plan* p) { return p->alpha; }
+
 void ps_plan_internal_tables(const ps_plan* p, const cplx<float>** twx, const cplx<float>** twy,
                              const float** lamx, const float** lamy, const float** za, const float** zb,
                              const float** zc, const float** dzf, const float2** zlo, const float2** zhi,

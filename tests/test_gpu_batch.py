@@ -137,3 +137,29 @@ def test_batch_autotune(lib, tmp_path, monkeypatch):
     torch.cuda.synchronize()
     assert all(i.status == 0 for i in lib.read_infos(infos, len(grids)))
     b.close()
+
+
+def test_batch_helmholtz_grids(lib):
+    """Per-grid Helmholtz shifts (ps_batch_create_helmholtz): each grid solves
+    (A − α_g·I)·p = f; a zero shift leaves its grid a Poisson grid (singular ones keep
+    the mean handling), a positive one makes the all-P/NN grids regular."""
+    import torch
+    spec = [dict(SMALL[0], alpha=3.0), dict(SMALL[1], alpha=0.0), dict(SMALL[4], alpha=250.0),
+            dict(SMALL[6], alpha=0.5)]
+    grids = _grids(spec)
+    for g, d in enumerate(grids):
+        d["alpha"] = spec[g]["alpha"]
+    b = lib.Batch(grids, rtol=1e-10, max_iter=6)
+    fs, ps = _fields(lib, grids, 70)
+    fptr, pptr = b.pointers(fs, ps)
+    infos = lib.infos_tensor(len(grids))
+    b.solve(fptr, pptr, infos)
+    torch.cuda.synchronize()
+    for g, (d, inf) in enumerate(zip(grids, lib.read_infos(infos, len(grids)))):
+        f, p = fs[g].cpu().numpy(), ps[g].cpu().numpy()
+        al = d["alpha"]
+        rr = O.relative_residual(p, f, d["dx"], d["dy"], d["zf"], *d["bcs"], alpha=al)
+        assert inf.status == 0 and inf.rel_residual <= 1e-10 and rr <= 1e-10, (g, inf.status, inf.rel_residual, rr)
+        q = S.solve(f, d["dx"], d["dy"], d["zf"], *d["bcs"], alpha=al)
+        assert np.abs(p - q).max() <= 1e-8 * np.abs(q).max(), g
+    b.close()
