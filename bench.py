@@ -73,6 +73,10 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+FP64_FLOPS_PER_POINT = 126      # plain FP64 solve at n = 1024 (see the fp64_solve roofline)
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64
+
+
 def recorded_traffic(kernel, n_points):
     """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -536,6 +540,16 @@ def bench_ours(args):
                        "status": inf.status},
             "fp64_solve": {"value": job_rate(world, N, ms64), "unit": "Mpts/s",
                            "ms_per_step": ms64, "max_rel_diff_vs_refined": diff,
+                           # FP64-ALU bound on this part: four transforms (≈ 2.5·log2 n + 4 flops
+                           # per point each) and the Thomas sweep (≈ 9), ≈ 126 flops per point at
+                           # n = 1024, against the nominal FP64 rate; and its 80 B/pt against HBM
+                           "roofline_fp64": {"bound": "fp64", "flops_per_point": FP64_FLOPS_PER_POINT,
+                                             "achieved": FP64_FLOPS_PER_POINT * N / (ms64 * 1e-3) / 1e12,
+                                             "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                             "peak_source": "nominal (no measured FP64 peak)",
+                                             "frac": FP64_FLOPS_PER_POINT * N / (ms64 * 1e-3) / 1e12
+                                             / FP64_NOMINAL_TFLOPS,
+                                             "hbm_frac": 80 * N / (ms64 * 1e-3) / 1e9 / peak},
                            "kernels": {k: v[3] / k64 for k, v in prof64.items() if v[0]}},
             "speedup_vs_fp64": ms64 / ms_max,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
