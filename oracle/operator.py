@@ -28,6 +28,14 @@ Helmholtz variant (§2: an implicit diffusion step needs one Helmholtz equation
 per velocity component; §4: done with the same method): the operator of Eq. 4
 minus α times the identity, α ≥ 0 (``alpha``; α = 0 is the Poisson problem).
 For α > 0 the constants leave the null space, so no problem is singular.
+
+Face-centred z (``"FD"``, z only; the velocity component normal to the walls in
+an implicit diffusion step, §2 and the end of §2.1: non-staggered unknowns). The
+unknown w_k sits on z face k; plane 0 is the bottom wall face and the top wall
+face n is implicit, both with w = 0 (Dirichlet on the node). Row k ≥ 1 is the
+finite-volume second difference on the control volume between the centres of
+cells k−1 and k: ((w_{k+1} − w_k)/Δz^f_k − (w_k − w_{k−1})/Δz^f_{k−1}) / Δz^c_{k−1},
+with w_n = 0; row 0 is −w_0 (so w_0 = 0 when the right-hand side is 0 there).
 """
 
 import numpy as np
@@ -56,8 +64,27 @@ def _ends(bc):
     return {"P": ("P", "P"), "NN": ("N", "N"), "DD": ("D", "D"), "ND": ("N", "D"), "DN": ("D", "N")}[bc]
 
 
+def operator_1d_faces(faces):
+    """Dense n×n matrix of the face-centred ("FD") z operator, assembled row by row."""
+    dzf, dzc = metrics(faces)
+    n = len(dzf)
+    L = np.zeros((n, n))
+    L[0, 0] = -1.0
+    for k in range(1, n):
+        h = dzc[k - 1]                     # control volume: centres of cells k−1 and k
+        up = 1.0 / (dzf[k] * h)            # flux to face k+1 (the top wall when k = n−1)
+        dn = 1.0 / (dzf[k - 1] * h)        # flux to face k−1 (the stored bottom wall when k = 1)
+        L[k, k] -= up + dn
+        L[k, k - 1] += dn
+        if k + 1 < n:
+            L[k, k + 1] += up
+    return L
+
+
 def operator_1d(bc, faces):
     """Dense n×n matrix of the 1D operator on one axis, assembled row by row."""
+    if bc == "FD":
+        return operator_1d_faces(faces)
     dzf, dzc = metrics(faces)
     n = len(dzf)
     lo, hi = _ends(bc)
@@ -101,8 +128,24 @@ def operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
     return A.tocsr()
 
 
+def _faces_term(p, axis, faces):
+    """The face-centred ("FD") z term from shifted copies (wall values 0)."""
+    dzf, dzc = metrics(faces)
+    w = np.moveaxis(p, axis, 0)
+    n = w.shape[0]
+    shape = (-1,) + (1,) * (w.ndim - 1)
+    wp = np.concatenate([w[1:], np.zeros_like(w[:1])], axis=0)        # w_{k+1}, w_n = 0
+    flux_up = (wp - w) / dzf.reshape(shape)                            # between faces k and k+1
+    term = np.empty_like(w)
+    term[1:] = (flux_up[1:] - flux_up[:-1]) / dzc.reshape(shape)       # rows k ≥ 1
+    term[0] = -w[0]
+    return np.moveaxis(term, 0, axis)
+
+
 def _axis_term(p, axis, faces, bc):
     """Second-difference term of one axis, from a padded copy (ghost rules above)."""
+    if bc == "FD":
+        return _faces_term(p, axis, faces)
     dzf, dzc = metrics(faces)
     lo, hi = _ends(bc)
     x = np.moveaxis(p, axis, 0)

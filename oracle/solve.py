@@ -45,6 +45,12 @@ def z_system(zf, bcz):
     a = np.zeros(n)
     c = np.zeros(n)
     b = np.zeros(n)
+    if bcz == "FD":  # face-centred unknowns between two walls (see oracle.operator)
+        b[0] = -1.0
+        a[1:] = 1.0 / (dzf[:-1] * dzc)     # to face k−1 (row 1: the stored wall face)
+        c[1:-1] = 1.0 / (dzf[1:-1] * dzc[:-1])
+        b[1:] = -(a[1:] + 1.0 / (dzf[1:] * dzc))
+        return a, b, c
     a[1:] = 1.0 / (dzf[1:] * dzc)
     c[:-1] = 1.0 / (dzf[:-1] * dzc)
     b[1:] -= a[1:]

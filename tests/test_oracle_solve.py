@@ -217,3 +217,54 @@ def test_helmholtz_stencil_equals_sparse_matrix():
     bcs = ("DD", "P", "ND")
     A = O.operator_3d(4, 6, 0.2, 0.9, zf, *bcs, alpha=4.25)
     assert np.abs(A @ x.ravel() - O.apply(x, 0.2, 0.9, zf, *bcs, alpha=4.25).ravel()).max() < 1e-12
+
+
+# ---- face-centred z ("FD"): the wall-normal velocity of an implicit diffusion step ----
+
+@pytest.mark.parametrize("bcxy", [("P", "P"), ("DD", "NN"), ("ND", "DN")])
+@pytest.mark.parametrize("alpha", [0.0, 12.0])
+def test_fd_eigen_solve_equals_dense_lu_and_codings(bcxy, alpha):
+    zf = _stretched(7, seed=21)
+    f = np.random.default_rng(22).uniform(-1, 1, (7, 4, 6))
+    f[0] = 0.0                                   # the bottom wall face carries no equation
+    bcs = (bcxy[0], bcxy[1], "FD")
+    p = S.solve(f, 0.3, 0.7, zf, *bcs, alpha=alpha)
+    q = D.solve_direct(f, 0.3, 0.7, zf, *bcs, dense=True, alpha=alpha)
+    assert np.abs(p - q).max() <= 1e-12 * np.abs(q).max()
+    assert np.abs(p[0]).max() <= 1e-12 * np.abs(q).max()
+    r = f - O.apply(p, 0.3, 0.7, zf, *bcs, alpha=alpha)
+    assert np.abs(r).max() < 1e-11 * np.abs(f).max()
+    a, b, c = S.z_system(zf, "FD")
+    M = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    assert np.abs(O.operator_1d("FD", zf) - M).max() < 1e-12 * np.abs(M).max()
+
+
+def test_fd_single_mode_closed_form():
+    """Uniform z: the face system with zero wall nodes has the sine modes sin(πqk/n)
+    (a DST-I basis) with λ_z = −4 sin²(πq/2n)/Δz², so p = f/(λ_x + λ_y + λ_z − α)."""
+    nx, ny, nz, dx, dy, dz, alpha = 8, 6, 10, 0.25, 0.5, 0.1, 2.0
+    qx, qy, qz = 3, 2, 4
+    ex = T.backward_matrix("P", nx)[:, qx]
+    ey = T.backward_matrix("NN", ny)[:, qy]
+    ez = np.sin(np.pi * qz * np.arange(nz) / nz)
+    f = ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    lam = (T.eigenvalues("P", nx)[qx] / dx ** 2 + T.eigenvalues("NN", ny)[qy] / dy ** 2
+           - 4 * np.sin(np.pi * qz / (2 * nz)) ** 2 / dz ** 2) - alpha
+    p = S.solve(f, dx, dy, O.uniform_faces(nz, dz), "P", "NN", "FD", alpha=alpha)
+    assert np.abs(p - f / lam).max() < 1e-13 * np.abs(f / lam).max()
+
+
+def test_fd_planted_control_volume_mistake_is_caught(monkeypatch):
+    """Dividing the face rows by the cell width instead of the centre distance: the
+    dense LU of the assembled operator no longer matches the eigen-expansion solve."""
+    orig = O.operator_1d_faces
+
+    def wrong(faces):
+        L = orig(faces)
+        dzf, dzc = O.metrics(faces)
+        L[1:] *= (dzc / dzf[1:])[:, None]
+        return L
+
+    monkeypatch.setattr(O, "operator_1d_faces", wrong)
+    with pytest.raises(AssertionError):
+        test_fd_eigen_solve_equals_dense_lu_and_codings(("P", "P"), 12.0)
