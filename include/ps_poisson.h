@@ -56,8 +56,16 @@ typedef enum {
   PS_BC_NEUMANN_NEUMANN = 1,
   PS_BC_DIRICHLET_DIRICHLET = 2,
   PS_BC_NEUMANN_DIRICHLET = 3,
-  PS_BC_DIRICHLET_NEUMANN = 4
+  PS_BC_DIRICHLET_NEUMANN = 4,
+  PS_BC_FACE_DIRICHLET = 5   /* z only: see below */
 } ps_bc;
+/* PS_BC_FACE_DIRICHLET (z only; the wall-normal velocity of an implicit
+ * diffusion step, §2): the unknowns sit on the z faces, plane k of the field
+ * being face k (its low face); plane 0 is the bottom wall face and the top wall
+ * face nz is implicit, both with value 0 (Dirichlet on the node). Row k ≥ 1 is
+ * the finite-volume second difference over the volume between the centres of
+ * cells k−1 and k; row 0 is −p_0 plus the x/y terms, so p_0 = 0 when f_0 = 0
+ * (the caller keeps f's plane 0 zero). Not singular; no transpose solve. */
 
 /* Arithmetic of the solve.
  *   PS_FP64         all of the path in FP64 arithmetic (fields double).

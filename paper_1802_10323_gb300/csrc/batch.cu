@@ -119,8 +119,12 @@ __device__ ZArgs<float> bz_args(const BGrid& G, char* ws) {
 }
 
 enum { BEND_WRAP = 0, BEND_N = 1, BEND_D = 2 };
-__device__ __forceinline__ int bend_lo(int bc) { return bc == BC_P ? BEND_WRAP : ((bc == BC_DD || bc == BC_DN) ? BEND_D : BEND_N); }
-__device__ __forceinline__ int bend_hi(int bc) { return bc == BC_P ? BEND_WRAP : ((bc == BC_DD || bc == BC_ND) ? BEND_D : BEND_N); }
+__device__ __forceinline__ int bend_lo(int bc) {
+  return bc == BC_P ? BEND_WRAP : ((bc == BC_DD || bc == BC_DN || bc == BC_FD) ? BEND_D : BEND_N);
+}
+__device__ __forceinline__ int bend_hi(int bc) {
+  return bc == BC_P ? BEND_WRAP : ((bc == BC_DD || bc == BC_ND || bc == BC_FD) ? BEND_D : BEND_N);
+}
 // (neighbour − Φ_c) under the end's ghost rule; q is the neighbour if inner or wrapped
 __device__ __forceinline__ df bnb(int kind, bool inner, const double* q, df pc) {
   if (inner || kind == BEND_WRAP) return df_sub(df_from_f64(*q), pc);

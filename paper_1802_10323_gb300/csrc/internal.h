@@ -9,7 +9,7 @@
 
 namespace ps {
 
-enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3, BC_DN = 4 };
+enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3, BC_DN = 4, BC_FD = 5 /* z only: face unknowns */ };
 // ND and DN share the DCT-IV line transform: DN is the ND problem on the reversed
 // line, so on the physical side of a transform the two reals x_{2p} and x_{n−1−2p}
 // trade places; the spectral side, the tables and the eigenvalues are ND's.

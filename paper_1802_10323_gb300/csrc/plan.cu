@@ -612,8 +612,8 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   *out = nullptr;
   if (!(alpha >= 0.0) || !std::isfinite(alpha))
     return fail(nullptr, PS_INVALID_ARG, "the Helmholtz shift alpha must be finite and >= 0");
-  if ((unsigned)bcx > 4u || (unsigned)bcy > 4u || (unsigned)bcz > 4u)
-    return fail(nullptr, PS_INVALID_ARG, "unknown boundary condition");
+  if ((unsigned)bcx > 4u || (unsigned)bcy > 4u || (unsigned)bcz > 5u)
+    return fail(nullptr, PS_INVALID_ARG, "unknown boundary condition (face unknowns are for z only)");
   if ((unsigned)prec > 2u) return fail(nullptr, PS_INVALID_ARG, "unknown precision");
   if (!(dx > 0) || !(dy > 0)) return fail(nullptr, PS_INVALID_ARG, "dx and dy must be > 0");
   if (!zf && !(dz > 0)) return fail(nullptr, PS_INVALID_ARG, "dz must be > 0 when zf is NULL");
@@ -671,6 +671,27 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
       hi[nz - 1] = 1.0 / (dzf[nz - 1] * dzf[nz - 1]);
     }
   }
+  if (bcz == PS_BC_FACE_DIRICHLET) {
+    // unknowns on the z faces: plane k is face k, face 0 the stored bottom wall and face
+    // nz the implicit top wall (both 0). Row k ≥ 1 on the volume between the centres of
+    // cells k−1 and k; row 0 is −p_0. For the residual stencils both ends take the
+    // Dirichlet ghost rule (ghost = −p): lo_0 = 1/2 makes row 0 read −p_0, and hi_{nz−1}
+    // = up/2 makes the top row see the zero wall node.
+    std::fill(za.begin(), za.end(), 0.0);
+    std::fill(zc.begin(), zc.end(), 0.0);
+    std::fill(lo.begin(), lo.end(), 0.0);
+    std::fill(hi.begin(), hi.end(), 0.0);
+    zb[0] = -1.0;
+    lo[0] = 0.5;
+    for (int k = 1; k < nz; ++k) {
+      const double h = dzc[k - 1];
+      const double dn = 1.0 / (dzf[k - 1] * h), up = 1.0 / (dzf[k] * h);
+      za[k] = lo[k] = dn;
+      zb[k] = -(dn + up);
+      if (k + 1 < nz) zc[k] = hi[k] = up;
+      else hi[k] = 0.5 * up;
+    }
+  }
   double wsum = 0.0;
   for (int k = 0; k < nz; ++k) {
     split_df(lo[k], &zlo[k]);
@@ -701,8 +722,10 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   std::vector<float2> zres(3 * (size_t)nz);
   {
     const double ix2 = 1.0 / (dx * dx), iy2 = 1.0 / (dy * dy);
-    const bool dlo = (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_DIRICHLET_NEUMANN);
-    const bool dhi = (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_NEUMANN_DIRICHLET);
+    const bool dlo = (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_DIRICHLET_NEUMANN ||
+                      bcz == PS_BC_FACE_DIRICHLET);
+    const bool dhi = (bcz == PS_BC_DIRICHLET_DIRICHLET || bcz == PS_BC_NEUMANN_DIRICHLET ||
+                      bcz == PS_BC_FACE_DIRICHLET);
     double asum = 0.0;
     for (int k = 0; k < nz; ++k) {
       const double cl = (k == 0 && dlo) ? -lo[k] : lo[k];
@@ -856,6 +879,8 @@ ps_status ps_solve_transpose(ps_plan* plan, const double* g, double* p, void* ws
                              ps_info* info) {
   ps_status s = check_solve_args(plan, g, p, ws);
   if (s != PS_OK) return s;
+  if (plan->bcz == PS_BC_FACE_DIRICHLET)
+    return fail(plan, PS_INVALID_ARG, "no transpose solve for face unknowns in z");
   if (plan->prec == PS_FP64)
     return solve_plain<double>(plan, g, p, ws, static_cast<cudaStream_t>(stream), info, true);
   return fail(plan, PS_INVALID_ARG, "ps_solve_transpose needs a PS_FP64 plan");
@@ -865,6 +890,8 @@ ps_status ps_solve_transpose_f32(ps_plan* plan, const float* g, float* p, void* 
                                  ps_info* info) {
   ps_status s = check_solve_args(plan, g, p, ws);
   if (s != PS_OK) return s;
+  if (plan->bcz == PS_BC_FACE_DIRICHLET)
+    return fail(plan, PS_INVALID_ARG, "no transpose solve for face unknowns in z");
   if (plan->prec != PS_FP32) return fail(plan, PS_INVALID_ARG, "needs a PS_FP32 plan");
   return solve_plain<float>(plan, g, p, ws, static_cast<cudaStream_t>(stream), info, true);
 }

@@ -73,8 +73,14 @@ __host__ __device__ constexpr size_t resid_smem(int rpt, int usize, int csize) {
   return (size_t)RDEPTH * resid_cells(rpt) * usize + (size_t)2 * resid_cells(rpt) * csize;
 }
 
-__device__ __forceinline__ int end_lo(int bc) { return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_DN) ? END_D : END_N); }
-__device__ __forceinline__ int end_hi(int bc) { return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_ND) ? END_D : END_N); }
+// (face unknowns in z, BC_FD: both ends take the Dirichlet ghost rule; the plan scales the
+// end coefficients so that row 0 reads −p_0 and the top row sees a zero wall node)
+__device__ __forceinline__ int end_lo(int bc) {
+  return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_DN || bc == BC_FD) ? END_D : END_N);
+}
+__device__ __forceinline__ int end_hi(int bc) {
+  return bc == BC_P ? END_WRAP : ((bc == BC_DD || bc == BC_ND || bc == BC_FD) ? END_D : END_N);
+}
 
 // unevaluated double-float sum
 __device__ __forceinline__ df add_u(df a, df b) {
