@@ -74,6 +74,8 @@ def source_hash():
 
 
 FP64_FLOPS_PER_POINT = 126      # plain FP64 solve at n = 1024 (see the fp64_solve roofline)
+NS_FP64_OPS_PER_CELL = 126      # the RK3 predictor kernel, FP64 fields (see the rk3_step roofline)
+NUM_SMS_GB300 = 152
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64
 
 
@@ -464,15 +466,31 @@ def bench_ours(args):
         torch.cuda.synchronize()
         barrier()
         k5 = max(1, min(args.steps, 5))
+        plan5.profile(True)
         e0.record(stream)
         for _ in range(k5):
             rk3()
         e1.record(stream)
         torch.cuda.synchronize()
         ms5 = max_over_ranks(e0.elapsed_time(e1) / k5)
+        prof5 = plan5.profile_read()
+        plan5.profile(False)
         i5 = lib.read_info(inf5)
+        cells5 = n5[0] * n5[1] * n5[2]
+        pl5, pa5, _, pm5 = prof5["ns_predict"]
+        pred_ms = pm5 / max(pa5, 1)
+        fp64_rate = 2 * NUM_SMS_GB300 * 2.07e9 / 1e12   # FP64 operations per second (T), max clock
         ns = {"value": job_rate(world, n5[0] * n5[1] * n5[2], ms5), "unit": "Mpts/s (cells x RK3 steps)",
               "ms_per_rk3_step": ms5, "grid": list(n5), "last_solve_status": i5.status,
+              # the fused predictor is bound by the FP64 pipe: ≈ 126 FP64 operations per cell
+              # (counted from the kernel source) against 2 per clock per SM
+              "roofline": {"bound": "fp64", "kernel": "ns_predict", "ops_per_cell": NS_FP64_OPS_PER_CELL,
+                           "avg_launch_ms": pred_ms,
+                           "achieved": NS_FP64_OPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12,
+                           "peak": fp64_rate, "unit": "T FP64 ops/s",
+                           "peak_source": "2 FP64 operations per clock per SM (probe) x 152 SMs x 2.07 GHz",
+                           "frac": NS_FP64_OPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12 / fp64_rate},
+              "kernels_ms_per_step": {k: v[3] / k5 for k, v in prof5.items() if v[0]},
               "last_solve_rel_residual": i5.rel_residual,
               "workload": "3 substeps of ps_ns_substep (predictor, divergence, refined solve to 1e-10, "
                           "projection, pressure update) per step; FP64 fields; Gaussian staggered velocity "

@@ -238,7 +238,8 @@ ps_status ps_div_adjoint_correct(ps_plan* plan, const void* g, const void* s, vo
 typedef struct {
   char name[24];          /* kernel kind: x_fwd, x_fwd_f64in, y_fwd, z_solve, z_singular,
                              y_bwd, x_bwd, x_bwd_f64store, x_bwd_f64acc, residual,
-                             residual_check, control */
+                             residual_check, control, …, and for ps_ns_substep
+                             ns_predict, ns_projection, ns_pressure */
   int launches;           /* all launches in the window                         */
   int active_launches;    /* launches that did work (see above)                 */
   double total_ms;        /* summed duration of all launches                    */

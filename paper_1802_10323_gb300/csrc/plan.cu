@@ -108,12 +108,14 @@ void split_df(double d, float2* out) {
 // per grid point (the FP32 refinement path has separate kinds for its FP64-input
 // x pass, its storing and accumulating x passes and its check-only residual).
 enum Kind { K_XF = 0, K_XF64IN, K_YF, K_Z, K_ZS, K_YB, K_XB, K_XB64ST, K_XB64ACC, K_RES, K_CHK,
-            K_CTL, K_VER, K_RES0, K_RES3, K_XB64BASE, K_MAT, K_RESOUT, K_NKINDS };
+            K_CTL, K_VER, K_RES0, K_RES3, K_XB64BASE, K_MAT, K_RESOUT, K_NSPRED, K_NSPROJ, K_NSPRES,
+            K_NKINDS };
 static const char* kKindName[K_NKINDS] = {"x_fwd", "x_fwd_f64in", "y_fwd", "z_solve",
                                           "z_singular", "y_bwd", "x_bwd", "x_bwd_f64store",
                                           "x_bwd_f64acc", "residual", "residual_check", "control",
                                           "residual_exact", "residual_first", "residual_first3",
-                                          "x_bwd_f64base", "materialize", "residual_out"};
+                                          "x_bwd_f64base", "materialize", "residual_out",
+                                          "ns_predict", "ns_projection", "ns_pressure"};
 constexpr int kProfMax = 4096;
 
 struct Prof {
@@ -1116,10 +1118,12 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
     a.beta = (T)be;
     a.gamma = (T)ga;
     cudaError_t e;
-    if ((e = launch_ns_predict<T>(a, u, p, ad, ustar, ad, st)) != cudaSuccess)
+    if ((e = run(plan, K_NSPRED, st, [&] { return launch_ns_predict<T>(a, u, p, ad, ustar, ad, st); })) !=
+        cudaSuccess)
       return cuda_fail(plan, e, "substep predictor");
     const ProjArgs<T> pa = proj_args<T>(plan);
-    if ((e = launch_projection<T>(0, pa, ustar, nullptr, rhs, st)) != cudaSuccess)
+    if ((e = run(plan, K_NSPROJ, st, [&] { return launch_projection<T>(0, pa, ustar, nullptr, rhs, st); })) !=
+        cudaSuccess)
       return cuda_fail(plan, e, "substep divergence");
     ps_status s;
     if constexpr (sizeof(T) == 4)
@@ -1127,9 +1131,11 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
     else
       s = ps_solve(plan, static_cast<const double*>(rhs), static_cast<double*>(phi), ws, stream, info);
     if (s != PS_OK) return s;
-    if ((e = launch_projection<T>(1, pa, ustar, phi, u, st)) != cudaSuccess)
+    if ((e = run(plan, K_NSPROJ, st, [&] { return launch_projection<T>(1, pa, ustar, phi, u, st); })) !=
+        cudaSuccess)
       return cuda_fail(plan, e, "substep projection");
-    if ((e = launch_ns_pressure<T>(N, 1.0 / (ga * dt), p, phi, st)) != cudaSuccess)
+    if ((e = run(plan, K_NSPRES, st, [&] { return launch_ns_pressure<T>(N, 1.0 / (ga * dt), p, phi, st); })) !=
+        cudaSuccess)
       return cuda_fail(plan, e, "substep pressure update");
     return PS_OK;
   };
