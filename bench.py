@@ -423,15 +423,25 @@ def bench_ours(args):
         torch.cuda.synchronize()
         barrier()
         kl = max(1, min(args.steps, 3))
+        planl.profile(True)
         e0.record(stream)
         for _ in range(kl):
             planl.solve(fl, pl_, info=infl)
         e1.record(stream)
         torch.cuda.synchronize()
         msl = max_over_ranks(e0.elapsed_time(e1) / kl)
+        profl = planl.profile_read()
+        planl.profile(False)
         il = lib.read_info(infl)
+        ptsl = nl[0] * nl[1] * nl[2]
+        doml = max((k for k in profl if k in bpp and profl[k][1]), key=lambda k: profl[k][3])
+        avgl = profl[doml][3] / profl[doml][1]
+        achl = bpp[doml] * ptsl / (avgl * 1e-3) / 1e9
         longl = {"value": job_rate(world, nl[0] * nl[1] * nl[2], msl), "unit": "Mpts/s",
                  "ms_per_step": msl, "grid": list(nl), "iterations": il.iterations,
+                 "roofline": {"bound": "hbm", "kernel": doml, "achieved": achl, "peak": peak,
+                              "unit": "GB/s", "frac": achl / peak, "avg_launch_ms": avgl,
+                              "algorithmic_bytes_per_launch": bpp[doml] * ptsl},
                  "rel_residual": il.rel_residual, "status": il.status,
                  "workload": "8192x8192x16 (x and y lines of 8192, the shared-memory transform kernel), "
                              "6x3x1 box, P/P/NN tanh z, f ~ N(0,1) mean removed (Philox seed 3), FP32+refine to 1e-10"}
