@@ -166,10 +166,15 @@ ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, dou
  * memory pool, or an interface through which no workspace can be passed).
  * The workspace lives in one fixed 8 MiB device array compiled into the
  * library, which every GPU that loads the library keeps until the process
- * exits; plans whose ps_workspace_bytes exceeds 8 MiB (roughly more than 10^6
- * cells) are rejected with PS_UNSUPPORTED_SIZE and a message in
- * ps_last_error(plan). The first call on a device looks up the array's device
- * address (a set-up step; make that first call before any stream capture).
+ * exits; plans whose ps_workspace_bytes exceeds 8 MiB are rejected with
+ * PS_UNSUPPORTED_SIZE and a message in ps_last_error(plan). The workspace is
+ * about 20 B per cell for PS_FP32_REFINE (24 B with a periodic z), 8 B per cell
+ * for PS_FP64 (16 B with a periodic z), so the limit is near 4.2·10^5 cells
+ * (3.5·10^5), resp. 1.0·10^6 cells (5.2·10^5); ps_workspace_bytes ≤ 8 MiB is the
+ * exact test. The first call on a device looks up the array's device address
+ * (a set-up step; make that first call before any stream capture); the address
+ * is kept with the id of the CUDA context, and the first call in a new context
+ * on that device (after cudaDeviceReset) looks it up again.
  * This entry point performs no device allocation. All calls share the one
  * array: calls whose GPU work overlaps (on different streams, or from
  * different threads) race on it and must be serialised by the caller. */
@@ -212,6 +217,8 @@ const char* ps_last_error(const ps_plan* plan);
  *   p      N cells: p^{k−1/2} in, p^{k+1/2} out.
  *   phi    N cells: Φ out.   rhs: N cells of scratch (D u*), distinct from phi.
  *   ws     the solve's workspace (ps_workspace_bytes); info as for ps_solve.
+ * The byte ranges of u, ustar, ad, p, phi, rhs and ws must be pairwise disjoint
+ * (PS_INVALID_ARG naming the overlapping pair otherwise).
  * Field types follow the plan (float for PS_FP32, double otherwise); device
  * pointers; enqueued on the stream (four kernels and the solve). */
 ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, void* ustar, void* ad, void* p,
@@ -292,14 +299,16 @@ ps_status ps_batch_solve(ps_batch* batch, double* const* f_dev, double* const* p
 /* Pick the tile sizes of the batched solve (lines per transform task, points
  * per residual task) by timing candidate scales on the caller's fields; the
  * choice is kept in the batch and, when the environment variable
- * PS_AUTOTUNE_CACHE names a file, appended to it as one JSON line keyed by the
- * grid descriptions and the GPU name (later calls read it back instead of
- * timing). Runs several solves and synchronises the stream; not capturable.
+ * PS_AUTOTUNE_CACHE names a file, appended to it as one JSON line keyed by a
+ * hash of every grid's sizes, BCs, spacings, z faces and Helmholtz shift, the
+ * batch's rtol and max_iter and the GPU name (later calls read it back instead
+ * of timing, and return the stored time in best_ms). Runs several solves and synchronises the stream; not capturable.
  * best_ms (may be NULL) receives the time of one batched solve. */
 ps_status ps_batch_autotune(ps_batch* batch, double* const* f_dev, double* const* p_dev, void* ws,
                             void* stream, double* best_ms);
 
-/* Current tile scale of the batch (1, 2 or 4). */
+/* Current tile scale of the batch: 2 after ps_batch_create, then whichever of
+ * the autotuner's candidates 1, 2, 4, 8, 16 it picked. */
 int ps_batch_tile_scale(const ps_batch* batch);
 
 /* Wait limit of the persistent kernel's dependency waits, in seconds

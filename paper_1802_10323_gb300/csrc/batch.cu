@@ -373,7 +373,8 @@ struct ps_batch {
   int max_iter = 3;
   std::vector<ps_plan*> plans;
   std::vector<ps_grid_desc> descs;
-  std::vector<std::vector<double>> faces;
+  std::vector<std::vector<double>> faces;  // each grid's z faces (empty: uniform dz)
+  std::vector<double> alphas;              // each grid's Helmholtz shift
   int nstage = 0, ntasks = 0;
   void* dev = nullptr;         // grids, tasks, need, dep, stage tables
   BGrid* d_grids = nullptr;
@@ -398,6 +399,15 @@ ps_status bfail(ps_batch* b, ps_status st, const char* msg) {
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Tile scales the autotuner times (and the only ones a cache entry may name).
+constexpr int kScales[] = {1, 2, 4, 8, 16};
+constexpr int kNumScales = (int)(sizeof(kScales) / sizeof(kScales[0]));
+bool is_candidate_scale(int sc) {
+  for (int i = 0; i < kNumScales; ++i)
+    if (kScales[i] == sc) return true;
+  return false;
+}
 
 // Build the device tables for the current tile scale.
 ps_status build_tables(ps_batch* b) {
@@ -550,8 +560,12 @@ ps_status ps_batch_create_helmholtz(ps_batch** out, int count, const ps_grid_des
   b->rtol = rtol;
   b->max_iter = max_iter;
   b->descs.assign(descs, descs + count);
+  b->faces.resize(count);
+  b->alphas.assign(count, 0.0);
   for (int g = 0; g < count; ++g) {
     const ps_grid_desc& d = descs[g];
+    if (d.zf) b->faces[g].assign(d.zf, d.zf + (d.nz > 0 ? d.nz + 1 : 0));  // host copy: autotune cache key
+    if (alphas) b->alphas[g] = alphas[g];
     ps_plan* pl = nullptr;
     ps_status st = ps_plan_create_helmholtz(&pl, d.nx, d.ny, d.nz, d.dx, d.dy, d.zf, d.dz, d.bcx, d.bcy,
                                             d.bcz, PS_FP32_REFINE, rtol, max_iter, alphas ? alphas[g] : 0.0);
@@ -635,11 +649,16 @@ ps_status ps_batch_autotune(ps_batch* b, double* const* f_dev, double* const* p_
     for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
   };
   for (int g = 0; g < b->count; ++g) {
+    // everything that decides a grid's work: sizes, BCs, spacings, z faces, shift
     const ps_grid_desc& d = b->descs[g];
     int ints[6] = {d.nx, d.ny, d.nz, (int)d.bcx, (int)d.bcy, (int)d.bcz};
     mix(ints, sizeof(ints));
+    const double dbl[4] = {d.dx, d.dy, b->faces[g].empty() ? d.dz : 0.0, b->alphas[g]};
+    mix(dbl, sizeof(dbl));
+    if (!b->faces[g].empty()) mix(b->faces[g].data(), b->faces[g].size() * sizeof(double));
   }
   mix(&b->max_iter, sizeof(int));
+  mix(&b->rtol, sizeof(double));
   mix(dev_name, strlen(dev_name));
   char key[64];
   snprintf(key, sizeof(key), "%016llx", h);
@@ -653,7 +672,7 @@ ps_status ps_batch_autotune(ps_batch* b, double* const* f_dev, double* const* p_
         int sc;
         double ms;
         if (sscanf(line, "{\"key\": \"%63[^\"]\", \"scale\": %d, \"ms\": %lf", k, &sc, &ms) == 3 &&
-            strcmp(k, key) == 0 && (sc == 1 || sc == 2 || sc == 4)) {
+            strcmp(k, key) == 0 && is_candidate_scale(sc)) {
           fclose(fp);
           b->scale = sc;
           if (best_ms) *best_ms = ms;
@@ -663,14 +682,13 @@ ps_status ps_batch_autotune(ps_batch* b, double* const* f_dev, double* const* p_
       fclose(fp);
     }
   }
-  const int cands[5] = {1, 2, 4, 8, 16};
   double best = 1e300;
   int best_scale = b->scale;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int ci = 0; ci < (int)(sizeof(cands) / sizeof(cands[0])); ++ci) {
-    b->scale = cands[ci];
+  for (int ci = 0; ci < kNumScales; ++ci) {
+    b->scale = kScales[ci];
     ps_status s2 = build_tables(b);
     if (s2 != PS_OK) continue;
     ps_batch_solve(b, f_dev, p_dev, ws, stream, nullptr);  // warm
@@ -682,7 +700,7 @@ ps_status ps_batch_autotune(ps_batch* b, double* const* f_dev, double* const* p_
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms / 3 < best) {
       best = ms / 3;
-      best_scale = cands[ci];
+      best_scale = kScales[ci];
     }
   }
   cudaEventDestroy(e0);

@@ -1083,8 +1083,28 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
                         void* phi, void* rhs, void* ws, void* stream, ps_info* info) {
   if (!plan) return fail(nullptr, PS_INVALID_ARG, "null plan");
   if (!u || !ustar || !ad || !p || !phi || !rhs || !ws) return fail(plan, PS_INVALID_ARG, "null pointer");
-  if (u == ustar || phi == rhs || ustar == rhs || u == ad || ustar == ad)
-    return fail(plan, PS_INVALID_ARG, "u, ustar, ad and phi, rhs must be distinct arrays");
+  {
+    // Every array is read and written at different stages (p += Φ reads phi, the
+    // solve overwrites ws and phi, the divergence writes rhs from ustar), so any
+    // overlap of their byte ranges changes the result: refuse it.
+    const size_t es = plan->prec == PS_FP32 ? sizeof(float) : sizeof(double);
+    size_t wsb = 0;
+    ps_workspace_bytes(plan, &wsb);
+    const struct { const char* name; uintptr_t lo; size_t bytes; } arr[7] = {
+        {"u", (uintptr_t)u, 3 * plan->N * es},       {"ustar", (uintptr_t)ustar, 3 * plan->N * es},
+        {"ad", (uintptr_t)ad, 3 * plan->N * es},     {"p", (uintptr_t)p, plan->N * es},
+        {"phi", (uintptr_t)phi, plan->N * es},       {"rhs", (uintptr_t)rhs, plan->N * es},
+        {"ws", (uintptr_t)ws, wsb}};
+    for (int i = 0; i < 7; ++i)
+      for (int j = i + 1; j < 7; ++j)
+        if (arr[i].bytes && arr[j].bytes && arr[i].lo < arr[j].lo + arr[j].bytes &&
+            arr[j].lo < arr[i].lo + arr[i].bytes) {
+          char msg[128];
+          snprintf(msg, sizeof(msg), "%s and %s overlap: u, ustar, ad, p, phi, rhs and ws must be disjoint",
+                   arr[i].name, arr[j].name);
+          return fail(plan, PS_INVALID_ARG, msg);
+        }
+  }
   if (k < 1 || k > 3) return fail(plan, PS_INVALID_ARG, "the RK3 substep k must be 1, 2 or 3");
   if (!(dt > 0.0) || !std::isfinite(dt) || !(nu >= 0.0) || !std::isfinite(nu))
     return fail(plan, PS_INVALID_ARG, "dt must be > 0 and nu >= 0 (finite)");

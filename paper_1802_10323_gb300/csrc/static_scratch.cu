@@ -5,9 +5,12 @@
 // The array is a file-scope __device__ object of kStaticScratchBytes; every GPU
 // on which the library's module is loaded holds it until the process exits. In
 // host code its name is only a host-side stand-in, so the device address is
-// obtained once per device with cudaGetSymbolAddress (with that device current)
-// and cached. Nothing here calls cudaMalloc, cudaFree or an allocating library
-// routine.
+// obtained with cudaGetSymbolAddress (with that device current) and cached per
+// device together with the id of the CUDA context it belongs to: a context
+// created anew on that device (after cudaDeviceReset, which unloads the module)
+// may hold the array elsewhere, so the address is looked up again then. Nothing
+// here calls cudaMalloc, cudaFree or an allocating library routine.
+#include <cuda.h>
 #include <mutex>
 #include <stdio.h>
 
@@ -19,8 +22,37 @@ constexpr size_t kStaticScratchBytes = (size_t)8 << 20;  // 8 MiB
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+struct Slot {
+  unsigned long long ctx_id;  // context the address was resolved in
+  void* addr;
+};
+Slot g_slot[kMaxDevices] = {};
 std::mutex g_scratch_mu;
+
+// Driver entry points for the current context's unique id (CUDA 12.0+), taken
+// through the runtime so that the library needs no link-time libcuda.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return false;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -50,8 +82,21 @@ ps_status ps_solve_static(ps_plan* plan, const double* f, double* p, void* strea
   void* ws = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-      // first call on this device: resolve the array's device address
+    // the context the solve's kernels will run in; if none is current yet the
+    // runtime has not initialised dev, and cudaSetDevice makes its primary
+    // context current (a device that is current already stays so)
+    unsigned long long ctx_id = 0;
+    bool have = current_context_id(&ctx_id);
+    if (!have && cudaSetDevice(dev) == cudaSuccess) have = current_context_id(&ctx_id);
+    if (!have) {
+      snprintf(msg, sizeof(msg), "ps_solve_static: cannot identify the current CUDA context");
+      ps::set_plan_error(plan, msg);
+      return PS_CUDA_ERROR;
+    }
+    Slot& s = g_slot[dev];
+    if (!s.addr || s.ctx_id != ctx_id) {
+      // first call on this device (or in a new context on it): resolve the
+      // array's device address
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_static_scratch);
       if (e != cudaSuccess || !ptr) {
@@ -60,9 +105,10 @@ ps_status ps_solve_static(ps_plan* plan, const double* f, double* p, void* strea
         ps::set_plan_error(plan, msg);
         return PS_CUDA_ERROR;
       }
-      g_scratch_addr[dev] = ptr;
+      s.addr = ptr;
+      s.ctx_id = ctx_id;
     }
-    ws = g_scratch_addr[dev];
+    ws = s.addr;
   }
   return ps_solve(plan, f, p, ws, stream, info);
 }

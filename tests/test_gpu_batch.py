@@ -8,8 +8,11 @@
 * the bounded wait: an unsatisfiable dependency (host-side test hook) ends
   with PS_TIMEOUT in the infos instead of a hang, and the context stays usable;
 * the autotuner picks one of its candidate tile scales and the solve still
-  agrees.
+  agrees; a second batch of the same grids reads the choice back from the
+  cache file, and a batch with another z stretching is a new cache key.
 """
+
+import json
 
 import numpy as np
 import pytest
@@ -128,8 +131,11 @@ def test_batch_autotune(lib, tmp_path, monkeypatch):
     fs, ps = _fields(lib, grids, 70)
     fptr, pptr = b.pointers(fs, ps)
     scale, ms = b.autotune(fptr, pptr)
-    assert scale in (1, 2, 4) and ms > 0
-    assert (tmp_path / "tune.jsonl").read_text().count("scale") == 1
+    assert scale in (1, 2, 4, 8, 16) and ms > 0
+    cache = tmp_path / "tune.jsonl"
+    assert cache.read_text().count("scale") == 1
+    stored = json.loads(cache.read_text().splitlines()[0])
+    assert stored["scale"] == scale
     infos = lib.infos_tensor(len(grids))
     for p in ps:
         p.zero_()
@@ -137,6 +143,23 @@ def test_batch_autotune(lib, tmp_path, monkeypatch):
     torch.cuda.synchronize()
     assert all(i.status == 0 for i in lib.read_infos(infos, len(grids)))
     b.close()
+    # a new batch of the same grids reads the cached choice back without timing:
+    # the returned time is the stored one and nothing is appended
+    b2 = lib.Batch(grids, rtol=1e-10, max_iter=6)
+    fptr2, pptr2 = b2.pointers(fs, ps)
+    scale2, ms2 = b2.autotune(fptr2, pptr2)
+    assert scale2 == scale and ms2 == stored["ms"]
+    assert cache.read_text().count("scale") == 1
+    b2.close()
+    # a different z stretching (or shift) is another key: it is timed and appended
+    grids3 = _grids(SMALL)
+    grids3[0]["zf"] = synth.tanh_faces(SMALL[0]["nz"], 1.0, 1.2)
+    b3 = lib.Batch(grids3, rtol=1e-10, max_iter=6)
+    fs3, ps3 = _fields(lib, grids3, 70)
+    fptr3, pptr3 = b3.pointers(fs3, ps3)
+    b3.autotune(fptr3, pptr3)
+    assert cache.read_text().count("scale") == 2
+    b3.close()
 
 
 def test_batch_helmholtz_grids(lib):

@@ -97,3 +97,27 @@ def test_rk3_taylor_green_decays_on_gpu(lib):
     err = np.abs(ut.cpu().numpy() - tg(T)).max()
     assert err < 1.5e-3, err
     plan.close()
+
+
+def test_substep_refuses_overlapping_arrays(lib):
+    """Every pair of the substep's arrays (and the workspace) must be disjoint: p
+    equal to phi, or ustar starting inside u, is refused before any launch."""
+    import torch
+    shape, bcs = (8, 12, 16), ("P", "P", "P")
+    nz, ny, nx = shape
+    plan = lib.Plan(nx, ny, nz, 0.1, 0.1, zf=O.uniform_faces(nz, 0.1), bcs=bcs, precision="fp64")
+    ut = torch.zeros((3,) + shape, dtype=torch.float64, device="cuda")
+    big = torch.zeros((4,) + shape, dtype=torch.float64, device="cuda")
+    pt = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    ad_t, us = torch.zeros_like(ut), torch.zeros_like(ut)
+    phi, rhs = torch.zeros_like(pt), torch.zeros_like(pt)
+    with pytest.raises(lib.PoissonError, match="p and phi overlap"):
+        plan.ns_substep(1, 1e-3, 0.01, ut, us, ad_t, pt, pt, rhs)
+    # ustar = the last three components of a 4-component buffer whose first three are u
+    with pytest.raises(lib.PoissonError, match="u and ustar overlap"):
+        plan.ns_substep(1, 1e-3, 0.01, big[:3], big[1:], ad_t, pt, phi, rhs)
+    with pytest.raises(lib.PoissonError, match="phi and rhs overlap"):
+        plan.ns_substep(1, 1e-3, 0.01, ut, us, ad_t, pt, phi, phi)
+    plan.ns_substep(1, 1e-3, 0.01, ut, us, ad_t, pt, phi, rhs)   # disjoint: accepted
+    torch.cuda.synchronize()
+    plan.close()
