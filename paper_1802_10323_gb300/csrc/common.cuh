@@ -66,17 +66,20 @@ __device__ __forceinline__ float narrow_f64(double d) {
 // Split d into hi + lo: hi = d truncated to 24 significant bits, lo = the
 // remainder (same sign) rounded toward zero to 24 bits. |d − hi − lo| ≤ 2^-47 |d|
 // for |d| ≥ 2^-74; smaller magnitudes are flushed (absolute error < 2^-74).
+// hi: the exponent rebiased (1023 → 127) and the top 23 fraction bits taken with
+// one 64-bit funnel shift; zero below the float normal range. lo: the remaining 29
+// fraction bits, whose unit is 2^(E−52) for the exponent E of d (and of hi), i.e.
+// hi's exponent field minus 52 (zero when that is below the float normal range).
 __device__ __forceinline__ void split_f64(double d, float& h, float& l) {
-  uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
-  uint32_t s = hi & 0x80000000u;
-  int eb = (int)((hi >> 20) & 0x7FFu);
-  int ef = eb - 896;
-  uint32_t hb = s | ((uint32_t)ef << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  hb = (ef <= 0) ? s : hb;
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t s = hi & 0x80000000u;
+  const uint32_t mag = __funnelshift_l(lo, hi - (896u << 20), 3) & 0x7FFFFFFFu;
+  const bool normal = (hi & 0x7FF00000u) > (896u << 20);
+  const uint32_t hb = normal ? (s | mag) : s;
   h = __uint_as_float(hb);
-  int es = eb - 948;  // biased float exponent of 2^(eb − 1075), the weight of the low bit
-  float scale = __uint_as_float((uint32_t)(es > 0 ? es : 0) << 23);
-  float lf = __uint2float_rz(lo & 0x1FFFFFFFu) * scale;
+  const int eb = (int)(hb & 0x7F800000u) - (52 << 23);
+  const float scale = __int_as_float(eb > 0 ? eb : 0);
+  const float lf = __uint2float_rz(lo & 0x1FFFFFFFu) * scale;
   l = __uint_as_float(__float_as_uint(lf) | s);
 }
 

@@ -108,7 +108,9 @@ struct ResidArgs {
 
 // CTAs of one residual pass: the three-level passes (incremental pass 0 and the
 // exact pass) and the others have different shapes
-int residual_blocks(int nx, int ny, int nz, int split3);
+// CTAs (= partial sums) of a residual pass: which = 0 pass 0 (two-level split),
+// 1 three-level split (pass 0 repeated, exact pass), 2 passes m ≥ 1
+int residual_blocks(int nx, int ny, int nz, int which);
 cudaError_t launch_residual_inc(const ResidArgs& a, int pass, int split3, cudaStream_t st);
 cudaError_t launch_residual_exact(const ResidArgs& a, cudaStream_t st);
 

@@ -164,7 +164,8 @@ struct ps_plan {
   void* dev;    // one allocation for all of the above
   int resid_blocks;     // CTAs of a residual pass (max over the two shapes: partials size)
   int resid_blocks3;    // … of a three-level pass (incremental pass 0, exact pass)
-  int resid_blocks2;    // … of the other passes
+  int resid_blocks2;    // … of pass 0 (two-level)
+  int resid_blocksA;    // … of the passes m ≥ 1
   char err[256];
 };
 
@@ -511,8 +512,8 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
                  [&] { return launch_residual_inc(ra, it, 0, st); })) != cudaSuccess)
       return cuda_fail(pl, e, "residual");
     if ((e = run(pl, K_CTL, st, [&] {
-           return launch_finalize(ctrl, partial, pl->resid_blocks2, wsum_total, pl->singular, pl->rtol,
-                                  it, 0, last ? 1 : 0, pl->anorm, nullptr, info, st);
+           return launch_finalize(ctrl, partial, it == 0 ? pl->resid_blocks2 : pl->resid_blocksA, wsum_total,
+                                  pl->singular, pl->rtol, it, 0, last ? 1 : 0, pl->anorm, nullptr, info, st);
          })) != cudaSuccess)
       return cuda_fail(pl, e, "finalize");
     if (it == 0) {
@@ -646,7 +647,8 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   }
   p->resid_blocks3 = residual_blocks(nx, ny, nz, 1);
   p->resid_blocks2 = residual_blocks(nx, ny, nz, 0);
-  p->resid_blocks = p->resid_blocks3 > p->resid_blocks2 ? p->resid_blocks3 : p->resid_blocks2;
+  p->resid_blocksA = residual_blocks(nx, ny, nz, 2);
+  p->resid_blocks = std::max(p->resid_blocks3, std::max(p->resid_blocks2, p->resid_blocksA));
 
   // ---- z metric (finite-volume form of Eq. 4 on the faces) ----
   std::vector<double> dzf(nz), dzc(nz > 1 ? nz - 1 : 0), za(nz, 0.0), zb(nz, 0.0), zc(nz, 0.0);

@@ -113,8 +113,12 @@ __device__ __forceinline__ fxp to_fxp(double d, float S, float iS) {
   const float ph = __fmul_rn(rintf(__fmul_rn(h, S)), iS);
   return {ph, __fadd_rn(__fsub_rn(h, ph), l)};
 }
-__device__ __forceinline__ fxp to_fxp(float u, float S, float iS) {
-  const float ph = __fmul_rn(rintf(__fmul_rn(u, S)), iS);
+// (float operand: rounding to the grid 2^−s by adding and removing C = 1.5·2^(23−s),
+// whose unit in the last place is 2^−s; |u| < 2^(20−s) keeps u + C in C's binade, so
+// this is round-to-nearest-even onto the grid, as rint(u·2^s)·2^−s, in two additions)
+__device__ __forceinline__ float to_grid(float u, float C) { return __fsub_rn(__fadd_rn(u, C), C); }
+__device__ __forceinline__ fxp to_fxp(float u, float C) {
+  const float ph = to_grid(u, C);
   return {ph, __fsub_rn(u, ph)};
 }
 // Three levels of an FP64 value from its 53-bit significand M (x = ±M·2^(eb−1075)):
@@ -143,11 +147,11 @@ __device__ __forceinline__ fxp3 to_fxp3(double x, int sc, float iS, float iS2) {
   }
   return {ph, pm, pr, 0.f};
 }
-// three levels of an FP32 value (exact); S2 = S·2^20, iS2 = iS·2^−20
-__device__ __forceinline__ fxp3 to_fxp3(float u, float S, float iS, float S2, float iS2) {
-  const float ph = __fmul_rn(rintf(__fmul_rn(u, S)), iS);
+// three levels of an FP32 value (exact); C2 = C·2^−20 (the grid 2^−s−20)
+__device__ __forceinline__ fxp3 to_fxp3(float u, float C, float C2) {
+  const float ph = to_grid(u, C);
   const float d = __fsub_rn(u, ph);  // exact
-  const float pm = __fmul_rn(rintf(__fmul_rn(d, S2)), iS2);
+  const float pm = to_grid(d, C2);
   return {ph, pm, __fsub_rn(d, pm), 0.f};
 }
 // exact product of an FP32 value and a double-float coefficient, unevaluated
@@ -237,15 +241,16 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   const bool perz = (a.bcz == BC_P);
   const uint32_t zsg_lo = end_lo(a.bcz) == END_D ? 0x80000000u : 0u;
   const uint32_t zsg_hi = end_hi(a.bcz) == END_D ? 0x80000000u : 0u;
-  float S, iS, S2, iS2;
+  float S, iS, iS2, C, C2;
   int sc;
   {
     const int e = (int)((*a.pmax_bits >> 52) & 0x7FF) - 1023;  // max|U| ∈ [2^e, 2^(e+1))
     sc = max(-100, min(100, 19 - e));
     S = __uint_as_float((uint32_t)(sc + 127) << 23);
     iS = __uint_as_float((uint32_t)(127 - sc) << 23);
-    S2 = __uint_as_float((uint32_t)(sc + 20 + 127) << 23);
     iS2 = __uint_as_float((uint32_t)(127 - sc - 20) << 23);
+    C = __uint_as_float(((uint32_t)(23 - sc + 127) << 23) | 0x400000u);       // 1.5·2^(23−s)
+    C2 = __uint_as_float(((uint32_t)(23 - sc - 20 + 127) << 23) | 0x400000u); // 1.5·2^(3−s)
   }
   extern __shared__ __align__(16) double rsm[];
   UT* raw = reinterpret_cast<UT*>(rsm);  // [RDEPTH][CELLS]
@@ -299,14 +304,23 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     const uint32_t zs = q < 0 ? zsg_lo : (q >= nz ? zsg_hi : 0u);
     const UT* src = raw + slot * CELLS;
     CT* dst = fx + fslot * CELLS;
+    auto one = [&](UT x, int e) {
+      if constexpr (SPLIT3 && U32) dst[e] = to_fxp3(x, C, C2);
+      else if constexpr (SPLIT3) dst[e] = to_fxp3(x, sc, iS, iS2);
+      else if constexpr (U32) dst[e] = to_fxp(x, C);
+      else dst[e] = to_fxp(x, S, iS);
+    };
+    if ((negm | zs) == 0u) {  // no Dirichlet ghost among this thread's cells
 #pragma unroll
-    for (int h = 0; h < CPT; ++h) {
-      const int e = tid + h * RTHREADS;
-      if (h < CPT - 1 || e < CELLS) {
-        const UT x = flip_sign(src[e], (((negm >> h) & 1u) << 31) ^ zs);
-        if constexpr (SPLIT3 && U32) dst[e] = to_fxp3(x, S, iS, S2, iS2);
-        else if constexpr (SPLIT3) dst[e] = to_fxp3(x, sc, iS, iS2);
-        else dst[e] = to_fxp(x, S, iS);
+      for (int h = 0; h < CPT; ++h) {
+        const int e = tid + h * RTHREADS;
+        if (h < CPT - 1 || e < CELLS) one(src[e], e);
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < CPT; ++h) {
+        const int e = tid + h * RTHREADS;
+        if (h < CPT - 1 || e < CELLS) one(flip_sign(src[e], (((negm >> h) & 1u) << 31) ^ zs), e);
       }
     }
   };
@@ -357,8 +371,12 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
 
   float rmax = -INFINITY, rmin = INFINITY, fmax_ = -INFINITY, fmin_ = INFINITY;
   float wr = 0.f;
-  df wf = {0.f, 0.f};
+  // Σ Δz^f·f (pass 0 of a singular problem) in FP64: one FMA per point on the FP64
+  // pipe, which nothing else in this kernel uses, instead of ~12 FP32 operations
+  // of a double-float product and sum on the issue-bound FP32 path
+  double wfd = 0.0;
   const df mu = SUBMU ? df{a.mu[0], a.mu[1]} : df{0.f, 0.f};
+  const bool store_r = a.rh_out != nullptr;
   int islot = 0;                 // raw slot of plane k + RDEPTH − 1 (≡ k − k0 mod RDEPTH)
   int cslot = 2 % RDEPTH;        // raw slot of plane k + 1
   auto march = [&](auto full_tag) {
@@ -381,6 +399,7 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     for (int m = 0; m < RPT; ++m) zp[m] = Fn[cidx[m]];
     const float2 cl = __ldg(a.zlo + k), ch = __ldg(a.zhi + k);
     const float w = SING ? __ldg(a.wz + k) : 0.f;
+    const double wd = (SING && FIRST) ? (double)w : 0.0;
     const size_t gk = (size_t)k * sxy + col;
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
@@ -438,7 +457,7 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
       if (FULL || in[m]) {
         const size_t g = gk + (size_t)m * nx;
         if constexpr (U32) {
-          if (a.rh_out) {
+          if (store_r) {
             a.rh_out[g] = rf;
             a.rl_out[g] = r.l - (rf - r.h);
           }
@@ -454,10 +473,7 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
         }
         if constexpr (SING) {
           wr = fmaf(w, rf, wr);
-          if constexpr (FIRST) {  // Σ Δz^f·f in double-float (only pass 0 needs μ_f)
-            wf = add_u(wf, prod(bv.h, df{w, 0.f}));
-            wf.l = fmaf(w, bv.l, wf.l);
-          }
+          if constexpr (FIRST) wfd = fma(wd, bcur[m], wfd);  // only pass 0 needs μ_f
         }
       }
     }
@@ -473,6 +489,11 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
   else march(std::false_type{});
   cp_wait<0>();
 
+  df wf = {0.f, 0.f};
+  if constexpr (SING && FIRST) {
+    wf.h = (float)wfd;
+    wf.l = (float)(wfd - (double)wf.h);
+  }
   resid_reduce<FIRST>(a, rmax, rmin, fmax_, fmin_, wr, wf);
 }
 
@@ -512,7 +533,7 @@ constexpr int ADEPTH = 5;  // raw-plane ring: k, k+1 read; k+2 … k+4 in flight
 __host__ __device__ constexpr int acc_cells(int rpt) { return AW * (RWARPS * rpt + 2); }
 
 template <int RPT, int KIND>
-__global__ void __launch_bounds__(RTHREADS, 3) residual_acc_kernel(ResidArgs a) {
+__global__ void __launch_bounds__(RTHREADS, RPT >= 8 ? 2 : 3) residual_acc_kernel(ResidArgs a) {
   constexpr bool SING = KIND & AK_SING, SUBMU = KIND & AK_SUBMU, OUT = KIND & AK_OUT, VEC = KIND & AK_VEC;
   constexpr int TY = RWARPS * RPT, ROWS = TY + 2, CELLS = acc_cells(RPT);
   constexpr int NC16 = VEC ? (8 * ROWS + RTHREADS - 1) / RTHREADS : 1;           // 16-byte copies
@@ -790,12 +811,19 @@ struct ResidShape {
   int rpt, zchunk;
   dim3 grid;
 };
-ResidShape resid_shape(int nx, int ny, int nz, bool split3) {
+// which: RS_PASS0 (two-level split), RS_SPLIT3 (three-level), RS_ACC (passes m ≥ 1)
+enum { RS_PASS0 = 0, RS_SPLIT3 = 1, RS_ACC = 2 };
+ResidShape resid_shape(int nx, int ny, int nz, int which) {
   ResidShape s;
-  s.rpt = (ny >= 4 * RWARPS && !split3) ? 4 : 2;  // three-level cells need the registers of two rows
+  // rows per thread: more rows share the per-plane work (ring, barriers, addressing);
+  // the single-word passes take eight (two CTAs per SM, no spills; measured at 1024³:
+  // 3.29 against 3.47 ms with four), the two-level split four (with eight it spills
+  // and ran 7.5 against 6.1 ms), three-level cells need the registers of two rows
+  s.rpt = which == RS_SPLIT3 ? 2
+        : (which == RS_ACC && ny >= 8 * RWARPS) ? 8 : (ny >= 4 * RWARPS ? 4 : 2);
   const int tiles = ((nx + RTX - 1) / RTX) * ((ny + RWARPS * s.rpt - 1) / (RWARPS * s.rpt));
   // about four waves of three CTAs per SM, 8 … 64 planes per CTA
-  const long long want = 152LL * 3 * 4;
+  const long long want = 152LL * (s.rpt >= 8 ? 2 : 3) * 4;
   long long zc = ((long long)nz * tiles) / want;
   zc = zc < 8 ? 8 : (zc > 64 ? 64 : zc);
   s.zchunk = (int)(zc < nz ? zc : nz);
@@ -841,6 +869,13 @@ cudaError_t launch_rpt(const ResidArgs& b, int kind, dim3 grid, cudaStream_t st)
 template <int RPT, int KIND>
 cudaError_t launch_acc_kind(const ResidArgs& b, dim3 grid, cudaStream_t st) {
   constexpr size_t smem = (size_t)ADEPTH * acc_cells(RPT) * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(residual_acc_kernel<RPT, KIND>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   residual_acc_kernel<RPT, KIND><<<grid, dim3(RTX, RWARPS), smem, st>>>(b);
   return cudaGetLastError();
 }
@@ -861,25 +896,26 @@ cudaError_t launch_acc_rpt(const ResidArgs& b, int kind, bool out, bool vec, dim
 // Passes m ≥ 1: same grid as the two-level passes (the finalize sums that many partials).
 cudaError_t launch_resid_acc(const ResidArgs& b0, int pass, cudaStream_t st) {
   reset_red_kernel<<<1, 1, 0, st>>>(b0.red, b0.skip, 0);
-  const ResidShape s = resid_shape(b0.nx, b0.ny, b0.nz, false);
+  const ResidShape s = resid_shape(b0.nx, b0.ny, b0.nz, RS_ACC);
   ResidArgs b = b0;
   b.zchunk = s.zchunk;
   const int kind = b.singular ? (AK_SING | (pass == 1 ? AK_SUBMU : 0)) : 0;
   const bool out = b.rh_out != nullptr, vec = (b.nx % 4) == 0;
-  return s.rpt == 4 ? launch_acc_rpt<4>(b, kind, out, vec, s.grid, st)
+  return s.rpt == 8 ? launch_acc_rpt<8>(b, kind, out, vec, s.grid, st)
+       : s.rpt == 4 ? launch_acc_rpt<4>(b, kind, out, vec, s.grid, st)
                     : launch_acc_rpt<2>(b, kind, out, vec, s.grid, st);
 }
 cudaError_t launch_resid(const ResidArgs& b0, int kind, int reset_f, cudaStream_t st) {
   reset_red_kernel<<<1, 1, 0, st>>>(b0.red, b0.skip, reset_f);
-  const ResidShape s = resid_shape(b0.nx, b0.ny, b0.nz, (kind & RK_SPLIT3) != 0);
+  const ResidShape s = resid_shape(b0.nx, b0.ny, b0.nz, (kind & RK_SPLIT3) ? RS_SPLIT3 : RS_PASS0);
   ResidArgs b = b0;
   b.zchunk = s.zchunk;
   return s.rpt == 4 ? launch_rpt<4>(b, kind, s.grid, st) : launch_rpt<2>(b, kind, s.grid, st);
 }
 }  // namespace
 
-int residual_blocks(int nx, int ny, int nz, int split3) {
-  const ResidShape s = resid_shape(nx, ny, nz, split3 != 0);
+int residual_blocks(int nx, int ny, int nz, int which) {
+  const ResidShape s = resid_shape(nx, ny, nz, which);
   return (int)(s.grid.x * s.grid.y * s.grid.z);
 }
 
