@@ -106,8 +106,6 @@ struct ResidArgs {
   const int* skip;
 };
 
-// CTAs of one residual pass: the three-level passes (incremental pass 0 and the
-// exact pass) and the others have different shapes
 // CTAs (= partial sums) of a residual pass: which = 0 pass 0 (two-level split),
 // 1 three-level split (pass 0 repeated, exact pass), 2 passes m ≥ 1
 int residual_blocks(int nx, int ny, int nz, int which);
