@@ -280,14 +280,59 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
   return a;
 }
 
+template <class T, class TI, class TO, bool FWD>
+cudaError_t launch_long(int m, FastArgs<T> a, cudaStream_t st) {
+  switch (m) {
+    case 1024: return launch_xform_long<T, TI, TO, 1024, FWD>(a, st);
+    case 2048: return launch_xform_long<T, TI, TO, 2048, FWD>(a, st);
+    default: return launch_xform_long<T, TI, TO, 4096, FWD>(a, st);
+  }
+}
+
 // One pass of line transforms along x (axis 0) or y (axis 1): the register-resident
-// kernel for n ∈ {128, 256, 512, 1024} when the tile fits, else the generic one.
+// kernels for n ∈ {128, 256, 512, 1024} when the tile fits; for n ∈ {2048, 4096,
+// 8192} the one-line-per-CTA kernel (y lines: transposed into yscr, an idle
+// workspace array of n_x·n_y·n_z values of T, and back); else the generic one.
 template <class T, class TI, class TO, bool FWD>
 cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, const T* scale,
                        int accumulate, const int* skip, cudaStream_t st,
                        unsigned long long* amax = nullptr, float* out2 = nullptr,
-                       const float* base32 = nullptr, int zn = 0) {
+                       const float* base32 = nullptr, int zn = 0, void* yscr = nullptr) {
   const AxisTab& t = axis == 0 ? p->ax : p->ay;
+  const bool long_m = (t.m == 1024 || t.m == 2048 || t.m == 4096) && zn == 0;
+  if (long_m && (axis == 0 || (yscr && std::is_same<TI, T>::value && std::is_same<TO, T>::value &&
+                               !accumulate && !amax && !out2 && !base32))) {
+    FastArgs<T> a{};
+    a.axis = 0;
+    a.bc = t.bc;
+    if constexpr (sizeof(T) == 8) a.tw = reinterpret_cast<const cplx<T>*>(t.tw64);
+    else a.tw = reinterpret_cast<const cplx<T>*>(t.tw32);
+    a.plane_scale = scale;
+    a.accumulate = accumulate;
+    a.skip = skip;
+    a.amax = amax;
+    a.out2 = out2;
+    a.base32 = base32;
+    a.nx = t.n;
+    a.nz = p->nz;
+    if (axis == 0) {
+      a.in = in;
+      a.out = out;
+      a.ny = p->ny;  // lines per plane
+      a.nlines = p->ny * p->nz;
+      return launch_long<T, TI, TO, FWD>(t.m, a, st);
+    }
+    // y: every plane [n_y][n_x] → [n_x][n_y] in yscr, the lines there, and back
+    T* sc = static_cast<T*>(yscr);
+    cudaError_t e = launch_plane_transpose<T>(static_cast<const T*>(in), sc, p->ny, p->nx, p->nz, skip, st);
+    if (e != cudaSuccess) return e;
+    a.in = sc;
+    a.out = sc;
+    a.ny = p->nx;  // lines per plane
+    a.nlines = p->nx * p->nz;
+    if ((e = launch_long<T, T, T, FWD>(t.m, a, st)) != cudaSuccess) return e;
+    return launch_plane_transpose<T>(sc, static_cast<T*>(out), p->nx, p->ny, p->nz, skip, st);
+  }
   const int lpc_y = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
   const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) &&
                        (axis == 0 || p->nx % lpc_y == 0);
@@ -373,7 +418,10 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
   cudaError_t e;
   if ((e = run(pl, K_XF, st, [&] { return line_xform<T, T, T, true>(pl, 0, f, p, sin_, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "x forward");
-  if ((e = run(pl, K_YF, st, [&] { return line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st); })) != cudaSuccess)
+  void* yscr = static_cast<char*>(ws) + L.scr_c;  // idle outside the z solve
+  if ((e = run(pl, K_YF, st, [&] {
+         return line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st, nullptr, nullptr, nullptr, 0, yscr);
+       })) != cudaSuccess)
     return cuda_fail(pl, e, "y forward");
   const ZArgs<T> za = zargs<T>(pl, p, ws, L, nullptr);
   if ((e = run(pl, K_Z, st, [&] {
@@ -385,7 +433,9 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
   if (pl->singular && !(sizeof(T) == 4 && !pl->periodic_z && pl->lowx > 0) &&
       (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z singular column");
-  if ((e = run(pl, K_YB, st, [&] { return line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st); })) != cudaSuccess)
+  if ((e = run(pl, K_YB, st, [&] {
+         return line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st, nullptr, nullptr, nullptr, 0, yscr);
+       })) != cudaSuccess)
     return cuda_fail(pl, e, "y backward");
   if ((e = run(pl, K_XB, st, [&] { return line_xform<T, T, T, false>(pl, 0, p, p, sout, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "x backward");
@@ -408,6 +458,7 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   float* rh = reinterpret_cast<float*>(wb + L.rh);
   float* rl = reinterpret_cast<float*>(wb + L.rl);
   float* u0 = reinterpret_cast<float*>(wb + L.u0);
+  void* yscr = wb + L.scr_c;  // the transposed y lines of n ≥ 2048 (idle outside the z solve)
   const ZArgs<float> zw = zargs<float>(pl, w, ws, L, skip);
   // One FP32 solve (c = 0: of f; c ≥ 1: of r = rh, the c-th correction) through w.
   // The x backward writes Φ_0 to u0 only (c = 0; the FP64 p is written by the first
@@ -439,7 +490,11 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       else
         r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, rh, w, nullptr, 0, skip, st); });
       if (r != cudaSuccess) return r;
-      if ((r = run(pl, K_YF, st, [&] { return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
+      if ((r = run(pl, K_YF, st, [&] {
+             return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st, nullptr, nullptr,
+                                                          nullptr, 0, yscr);
+           })) != cudaSuccess)
+        return r;
     }
     if ((r = run(pl, K_Z, st, [&] {
            return pl->periodic_z ? launch_zsolve<float>(zw, st) : launch_zsolve_ckpt(zw, st);
@@ -447,7 +502,11 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       return r;
     if (pl->singular && (pl->periodic_z || pl->lowx == 0) &&
         (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
-    if ((r = run(pl, K_YB, st, [&] { return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st); })) != cudaSuccess) return r;
+    if ((r = run(pl, K_YB, st, [&] {
+           return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st, nullptr, nullptr,
+                                                         nullptr, 0, yscr);
+         })) != cudaSuccess)
+      return r;
     if (first)
       return run(pl, K_XB64ST, st, [&] {
         return line_xform<float, float, double, false>(pl, 0, w, nullptr, nullptr, 0, skip, st, &ctrl->pmax, u0);

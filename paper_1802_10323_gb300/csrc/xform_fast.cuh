@@ -168,4 +168,14 @@ cudaError_t launch_xform_row(FastArgs<T> a, cudaStream_t st);
 template <class T, int M, bool FWD>
 cudaError_t launch_xform_col(FastArgs<T> a, cudaStream_t st);
 
+// Lines of n = 2M contiguous reals with M ∈ {1024, 2048, 4096}, one CTA per line
+// (xform_long.cu): a.nlines lines, line ln in plane ln / a.ny; x-row output modes.
+template <class T, class TI, class TO, int M, bool FWD>
+cudaError_t launch_xform_long(FastArgs<T> a, cudaStream_t st);
+
+// dst[z][c][r] = src[z][r][c] for every plane z < nz (rows × cols per plane).
+template <class T>
+cudaError_t launch_plane_transpose(const T* src, T* dst, int rows, int cols, int nz, const int* skip,
+                                   cudaStream_t st);
+
 }  // namespace ps
