@@ -21,6 +21,15 @@ Readings (the paper gives the uniform stencil only):
   image); a periodic ghost sits (Δz^f_0 + Δz^f_{n−1})/2 away. On a uniform grid
   this is exactly the z row of Eq. 4.
 
+Face-centred x or y (``"FD"`` on a transformed axis; non-staggered unknowns for the
+velocity normal to walls on that axis). Entry i of a line is x face i; entry 0 is
+the low wall face and the high wall face n is implicit, both with value 0. Reading
+taken (the transforms of §2.1 must diagonalise it): the interior faces 1 … n−1
+carry the Dirichlet second difference (u_{i+1} − 2u_i + u_{i−1})/Δ² with the wall
+values u_0 = u_n = 0 (the node of the wall is boundary data, not the stored entry),
+and the wall entry's own row is −u_0/Δ². With f = 0 on the wall face (the caller's
+contract, as for z) u_0 = 0 and this is the same solution as the z rule.
+
 ``operator_1d`` and ``apply`` are two separate codings of these rules (a matrix
 assembled row by row, and a padded-array stencil); tests check they agree.
 
@@ -81,9 +90,26 @@ def operator_1d_faces(faces):
     return L
 
 
-def operator_1d(bc, faces):
-    """Dense n×n matrix of the 1D operator on one axis, assembled row by row."""
+def operator_1d_nodes(n, h):
+    """Dense n×n matrix of the face-centred ("FD") x/y operator, assembled row by row."""
+    L = np.zeros((n, n))
+    L[0, 0] = -1.0 / h ** 2                 # the wall face's own row
+    for i in range(1, n):
+        L[i, i] = -2.0 / h ** 2
+        if i > 1:                           # (i = 1: the low wall node carries 0)
+            L[i, i - 1] = 1.0 / h ** 2
+        if i < n - 1:                       # (i = n−1: the high wall node carries 0)
+            L[i, i + 1] = 1.0 / h ** 2
+    return L
+
+
+def operator_1d(bc, faces, axis="z"):
+    """Dense n×n matrix of the 1D operator on one axis, assembled row by row
+    (``axis`` "xy" selects the transformed-axis rule for "FD")."""
     if bc == "FD":
+        if axis == "xy":
+            faces = np.asarray(faces, dtype=np.float64)
+            return operator_1d_nodes(len(faces) - 1, faces[1] - faces[0])
         return operator_1d_faces(faces)
     dzf, dzc = metrics(faces)
     n = len(dzf)
@@ -118,8 +144,8 @@ def operator_3d(nx, ny, dx, dy, zf, bcx, bcy, bcz, alpha=0.0):
     """Sparse (CSR) N×N matrix of Eq. 4 (minus α·I) on the [n_z][n_y][n_x] grid."""
     zf = np.asarray(zf, dtype=np.float64)
     nz = len(zf) - 1
-    Lx = sp.csr_matrix(operator_1d(bcx, uniform_faces(nx, dx)))
-    Ly = sp.csr_matrix(operator_1d(bcy, uniform_faces(ny, dy)))
+    Lx = sp.csr_matrix(operator_1d(bcx, uniform_faces(nx, dx), axis="xy"))
+    Ly = sp.csr_matrix(operator_1d(bcy, uniform_faces(ny, dy), axis="xy"))
     Lz = sp.csr_matrix(operator_1d(bcz, zf))
     Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
     A = sp.kron(Lz, sp.kron(Iy, Ix)) + sp.kron(Iz, sp.kron(Ly, Ix)) + sp.kron(Iz, sp.kron(Iy, Lx))
@@ -142,9 +168,22 @@ def _faces_term(p, axis, faces):
     return np.moveaxis(term, 0, axis)
 
 
+def _nodes_term(p, axis, h):
+    """The face-centred ("FD") x/y term from shifted copies (wall nodes 0)."""
+    u = np.moveaxis(p, axis, 0)
+    z = np.zeros_like(u[:1])
+    um = np.concatenate([z, z, u[1:-1]], axis=0)      # u_{i−1}; row 1 sees the wall node 0
+    up = np.concatenate([u[1:], z], axis=0)           # u_{i+1}; the high wall node 0
+    term = (um + up - 2.0 * u) / h ** 2
+    term[0] = -u[0] / h ** 2                          # the wall face's own row
+    return np.moveaxis(term, 0, axis)
+
+
 def _axis_term(p, axis, faces, bc):
     """Second-difference term of one axis, from a padded copy (ghost rules above)."""
     if bc == "FD":
+        if axis != 0:
+            return _nodes_term(p, axis, faces[1] - faces[0])
         return _faces_term(p, axis, faces)
     dzf, dzc = metrics(faces)
     lo, hi = _ends(bc)

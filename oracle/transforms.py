@@ -33,15 +33,27 @@ half-complex layout of a real DFT of n reals (footnote of §3):
 
 With this layout Table 1's periodic θ reads θ_q = ⌈q/2⌉ π / n (its
 ``θ_{p−1}`` for even q is read as "the same θ as q − 1").
+
+Non-staggered unknowns on x or y (``"FD"``; the velocity component normal to
+walls on that axis in an implicit diffusion step: §2 and the end of §2.1 name
+non-staggered transforms for it without stating them). Entry 0 of a line is the
+low wall face (stored, value 0), entries 1 … n−1 the interior faces, the high
+wall face n implicit. The interior faces are the nodes of the Dirichlet second
+difference, diagonalised by the sine transform of type I: forward
+â_0 = a_0, â_k = 2 Σ_{i=1}^{n−1} a_i sin(π k i / n), k = 1 … n−1; its inverse
+a_0 = â_0, a_i = (1/n) Σ_k â_k sin(π k i / n) (the same transform divided by 2n);
+eigenvalues λ_0 = −1 (the wall face's own row, see ``oracle.operator``) and
+λ_k = −4 sin²(π k / 2n).
 """
 
 import numpy as np
 
 BCS = ("P", "NN", "DD", "ND", "DN")
+XY_BCS = BCS + ("FD",)   # accepted on x and y (FD: non-staggered, see above)
 
 
 def _check(bc, n):
-    if bc not in BCS:
+    if bc not in XY_BCS:
         raise ValueError(f"unknown BC {bc!r}")
     if n < 2 or n % 2:
         raise ValueError("n must be even and >= 2 (Table 1 caption)")
@@ -68,12 +80,18 @@ def theta(bc, n):
         return q * np.pi / (2 * n)
     if bc == "DD":
         return (q + 1) * np.pi / (2 * n)
+    if bc == "FD":                                 # interior faces: kπ/2n; q = 0 (wall) set below
+        return q * np.pi / (2 * n)
     return (2 * q + 1) * np.pi / (4 * n)           # ND, and DN (the reversed ND axis)
 
 
 def eigenvalues(bc, n):
-    """λ_q = −4 sin²(θ_q), Table 1 (dimensionless; divide by Δ² for Eq. 5)."""
-    return -4.0 * np.sin(theta(bc, n)) ** 2
+    """λ_q = −4 sin²(θ_q), Table 1 (dimensionless; divide by Δ² for Eq. 5); for FD the
+    wall face's row has λ_0 = −1."""
+    lam = -4.0 * np.sin(theta(bc, n)) ** 2
+    if bc == "FD":
+        lam[0] = -1.0
+    return lam
 
 
 def forward_matrix(bc, n):
@@ -95,6 +113,12 @@ def forward_matrix(bc, n):
         return 2.0 * _sin_pi((2 * p + 1) * (q + 1), 2 * n)
     if bc == "DN":      # the ND transform of the reversed line
         return forward_matrix("ND", n)[:, ::-1].copy()
+    if bc == "FD":      # wall entry copied; DST-I of the interior faces: 2 Σ a_i sin(π k i / n)
+        F = 2.0 * _sin_pi(q * p, n)
+        F[0, :] = 0.0
+        F[:, 0] = 0.0
+        F[0, 0] = 1.0
+        return F
     # ND, DCT-IV: 2 Σ a_p cos(π (p+1/2)(q+1/2) / n)
     return 2.0 * _cos_pi((2 * p + 1) * (2 * q + 1), 4 * n)
 
@@ -122,6 +146,12 @@ def backward_matrix(bc, n):
         return B / (2 * n)
     if bc == "DN":      # ND's inverse, then the reversal
         return backward_matrix("ND", n)[::-1, :].copy()
+    if bc == "FD":      # wall entry copied; (1/n) Σ_k â_k sin(π k i / n)
+        B = _sin_pi(p * q, n) / n
+        B[0, :] = 0.0
+        B[:, 0] = 0.0
+        B[0, 0] = 1.0
+        return B
     # ND: (1/2n) DCT-IV
     return 2.0 * _cos_pi((2 * p + 1) * (2 * q + 1), 4 * n) / (2 * n)
 

@@ -12,6 +12,8 @@ import itertools
 
 import numpy as np
 import pytest
+import scipy.fft as sfft
+import scipy.sparse as sp
 
 from oracle import transforms as T
 from oracle import operator as O
@@ -268,3 +270,103 @@ def test_fd_planted_control_volume_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(O, "operator_1d_faces", wrong)
     with pytest.raises(AssertionError):
         test_fd_eigen_solve_equals_dense_lu_and_codings(("P", "P"), 12.0)
+
+
+# ---- face-centred x and y ("FD" on a transformed axis): DST-I-type transforms ----
+
+@pytest.mark.parametrize("n", [2, 4, 8, 12, 18])
+def test_fd_xy_transform_is_dst1(n):
+    """The interior block of the forward FD transform is scipy's DST type I (a library
+    special case); the wall entry is copied; backward · forward = I."""
+    F, B = T.forward_matrix("FD", n), T.backward_matrix("FD", n)
+    assert np.abs(F[1:, 1:] - sfft.dst(np.eye(n - 1), type=1, axis=0)).max() < 1e-13 * n
+    assert F[0, 0] == 1.0 and not F[0, 1:].any() and not F[1:, 0].any()
+    assert np.abs(B @ F - np.eye(n)).max() < 1e-13
+
+
+@pytest.mark.parametrize("n,h", [(4, 0.5), (10, 0.13), (16, 1.0)])
+def test_fd_xy_eigen_identity(n, h):
+    """F·L·F⁻¹ = diag(λ/h²) for the node operator with λ_0 = −1, λ_k = −4 sin²(πk/2n)."""
+    L = O.operator_1d("FD", O.uniform_faces(n, h), axis="xy")
+    M = T.forward_matrix("FD", n) @ L @ T.backward_matrix("FD", n)
+    lam = T.eigenvalues("FD", n) / h ** 2
+    assert np.abs(M - np.diag(lam)).max() < 1e-12 * np.abs(lam).max()
+    k = np.arange(1, n)
+    assert np.allclose(lam[1:], -4 * np.sin(np.pi * k / (2 * n)) ** 2 / h ** 2, rtol=1e-14, atol=0)
+
+
+FDXY = [("FD", "P", "NN"), ("NN", "FD", "DD"), ("FD", "FD", "P"), ("FD", "DN", "FD"),
+        ("DD", "FD", "ND"), ("FD", "FD", "FD")]
+
+
+@pytest.mark.parametrize("bcs", FDXY)
+@pytest.mark.parametrize("alpha", [0.0, 7.5])
+def test_fd_xy_eigen_solve_equals_dense_lu_and_codings(bcs, alpha):
+    zf = _stretched(6, seed=31)
+    f = np.random.default_rng(32).uniform(-1, 1, (6, 8, 10))
+    p = S.solve(f, 0.3, 0.7, zf, *bcs, alpha=alpha)
+    q = D.solve_direct(f, 0.3, 0.7, zf, *bcs, dense=True, alpha=alpha)
+    assert np.abs(p - q).max() <= 1e-12 * np.abs(q).max()
+    r = f - O.apply(p, 0.3, 0.7, zf, *bcs, alpha=alpha)
+    assert np.abs(r).max() < 1e-11 * np.abs(f).max()
+    A = O.operator_3d(10, 8, 0.3, 0.7, zf, *bcs, alpha=alpha)
+    if bcs[2] != "FD":  # the x/y parts are symmetric (the z part is under the Δz^f weight)
+        W = sp.diags(np.repeat(np.diff(zf), 80))
+        assert abs(W @ A - (W @ A).T).max() < 1e-9 * abs(W @ A).max()
+
+
+def test_fd_xy_wall_contract():
+    """f = 0 on the wall faces gives u = 0 there, and then the first interior row
+    seeing the stored wall entry (the z rule) or the wall node 0 is the same."""
+    zf = O.uniform_faces(6, 0.2)
+    f = np.random.default_rng(33).uniform(-1, 1, (6, 8, 10))
+    f[:, :, 0] = 0.0
+    f[:, 0, :] = 0.0
+    p = S.solve(f, 0.3, 0.7, zf, "FD", "FD", "NN")
+    assert np.abs(p[:, :, 0]).max() == 0.0 and np.abs(p[:, 0, :]).max() == 0.0
+
+
+def test_fd_xy_second_order_convergence():
+    """u = sin(πx) sin(2πy)·cos(πz) with x and y on faces (walls at 0 and 1 on both)
+    and z cell-centred Neumann: the discrete solution converges at second order."""
+    err = []
+    for n in (8, 16, 32):
+        h = 1.0 / n
+        xf = np.arange(n) * h                        # faces 0 … n−1 (face 0 the wall)
+        zc = (np.arange(n) + 0.5) * h
+        Z, Y, X = np.meshgrid(zc, xf, xf, indexing="ij")
+        u = np.sin(np.pi * X) * np.sin(2 * np.pi * Y) * np.cos(np.pi * Z)
+        f = -(np.pi ** 2 + 4 * np.pi ** 2 + np.pi ** 2) * u
+        p = S.solve(f, h, h, O.uniform_faces(n, h), "FD", "FD", "NN")
+        err.append(np.abs(p - u).max())
+    assert err[1] < 0.3 * err[0] and err[2] < 0.3 * err[1], err
+
+
+def test_fd_xy_planted_mistakes_are_caught(monkeypatch):
+    """A sine index off by one in the FD eigenvalues fails the eigen identity; the wall
+    row coupled into the first interior row (the z rule) in the matrix but not in the
+    stencil fails the agreement of the two codings."""
+    orig = T.eigenvalues
+
+    def shifted(bc, n):
+        lam = orig(bc, n)
+        if bc == "FD":
+            k = np.arange(1, n) + 1
+            lam = lam.copy()
+            lam[1:] = -4 * np.sin(np.pi * k / (2 * n)) ** 2
+        return lam
+
+    monkeypatch.setattr(T, "eigenvalues", shifted)
+    with pytest.raises(AssertionError):
+        test_fd_xy_eigen_identity(10, 0.13)
+    monkeypatch.setattr(T, "eigenvalues", orig)
+    orig_nodes = O.operator_1d_nodes
+
+    def coupled(n, h):
+        L = orig_nodes(n, h)
+        L[1, 0] = 1.0 / h ** 2
+        return L
+
+    monkeypatch.setattr(O, "operator_1d_nodes", coupled)
+    with pytest.raises(AssertionError):
+        test_fd_xy_eigen_solve_equals_dense_lu_and_codings(("FD", "P", "NN"), 0.0)
