@@ -57,15 +57,24 @@ typedef enum {
   PS_BC_DIRICHLET_DIRICHLET = 2,
   PS_BC_NEUMANN_DIRICHLET = 3,
   PS_BC_DIRICHLET_NEUMANN = 4,
-  PS_BC_FACE_DIRICHLET = 5   /* z only: see below */
+  PS_BC_FACE_DIRICHLET = 5   /* face unknowns between two walls: see below */
 } ps_bc;
-/* PS_BC_FACE_DIRICHLET (z only; the wall-normal velocity of an implicit
- * diffusion step, §2): the unknowns sit on the z faces, plane k of the field
- * being face k (its low face); plane 0 is the bottom wall face and the top wall
- * face nz is implicit, both with value 0 (Dirichlet on the node). Row k ≥ 1 is
- * the finite-volume second difference over the volume between the centres of
- * cells k−1 and k; row 0 is −p_0 plus the x/y terms, so p_0 = 0 when f_0 = 0
- * (the caller keeps f's plane 0 zero). Not singular; no transpose solve. */
+/* PS_BC_FACE_DIRICHLET (the wall-normal velocity of an implicit diffusion step,
+ * §2; non-staggered unknowns, end of §2.1): the unknowns sit on the faces normal
+ * to the axis, entry i of a line being face i (the low face of cell i); entry 0
+ * is the low wall face and the high wall face n is implicit, both with value 0
+ * (Dirichlet on the node). The caller keeps f zero on the wall faces, and the
+ * solution is then zero there.
+ *   z: row k ≥ 1 is the finite-volume second difference over the volume between
+ *      the centres of cells k−1 and k; row 0 is −p_0 plus the x/y terms. No
+ *      transpose solve (the operator is not symmetric under the Δz^f weight).
+ *   x, y (uniform; n ≤ 4096): rows i ≥ 1 are the second difference between the
+ *      wall nodes of value 0, row 0 has the axis part −p_0/Δ²; transformed by a
+ *      DST-I of the interior faces with the wall entry copied (eigenvalues −1 and
+ *      −4 sin²(πk/2n), divided by Δ²), done as an FFT of n complex points of the
+ *      odd extension in the shared-memory transform kernel. Not with the batched
+ *      solve, the projection operators or ps_ns_substep.
+ * Not singular. */
 
 /* Arithmetic of the solve.
  *   PS_FP64         all of the path in FP64 arithmetic (fields double).

@@ -27,7 +27,7 @@ PS_OK, PS_INVALID_ARG, PS_UNSUPPORTED_SIZE, PS_CUDA_ERROR = 0, 1, 2, 3
 PS_OUT_OF_MEMORY, PS_NOT_CONVERGED, PS_TIMEOUT = 4, 5, 6
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "CUDA_ERROR",
                 4: "OUT_OF_MEMORY", 5: "NOT_CONVERGED", 6: "TIMEOUT"}
-BC = {"P": 0, "NN": 1, "DD": 2, "ND": 3, "DN": 4, "FD": 5}  # FD: face unknowns, z only
+BC = {"P": 0, "NN": 1, "DD": 2, "ND": 3, "DN": 4, "FD": 5}  # FD: face unknowns (x, y: n <= 4096)
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
 
 

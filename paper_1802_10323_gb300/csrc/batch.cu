@@ -564,6 +564,12 @@ ps_status ps_batch_create_helmholtz(ps_batch** out, int count, const ps_grid_des
   b->alphas.assign(count, 0.0);
   for (int g = 0; g < count; ++g) {
     const ps_grid_desc& d = descs[g];
+    if (d.bcx == PS_BC_FACE_DIRICHLET || d.bcy == PS_BC_FACE_DIRICHLET) {
+      char msg[128];
+      snprintf(msg, sizeof(msg), "grid %d: face-centred x or y unknowns are not supported by the batched solve", g);
+      ps_batch_destroy(b);
+      return bfail(nullptr, PS_INVALID_ARG, msg);
+    }
     if (d.zf) b->faces[g].assign(d.zf, d.zf + (d.nz > 0 ? d.nz + 1 : 0));  // host copy: autotune cache key
     if (alphas) b->alphas[g] = alphas[g];
     ps_plan* pl = nullptr;

@@ -81,6 +81,7 @@ long theta_j(int bc, int n, int q) {
     case BC_P: return 4L * ((q + 1) / 2);  // ⌈q/2⌉·π/n; Nyquist q = n−1 gives π/2
     case BC_NN: return 2L * q;
     case BC_DD: return 2L * (q + 1);
+    case BC_FD: return 2L * q;             // x/y face unknowns: kπ/2n (q = 0: the wall row)
     default: return 2L * q + 1;            // ND, and DN (the reversed ND axis)
   }
 }
@@ -92,6 +93,7 @@ std::vector<double> eig_scaled(int bc, int n, double h) {
     cis(theta_j(bc, n, q), 8L * n, &c, &s);  // sin(π j / 4n) = sin(2π j / 8n)
     lam[q] = -4.0 * s * s / (h * h);
   }
+  if (bc == BC_FD) lam[0] = -1.0 / (h * h);  // the wall face's own row −u_0/Δ²
   return lam;
 }
 
@@ -299,7 +301,7 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
                        unsigned long long* amax = nullptr, float* out2 = nullptr,
                        const float* base32 = nullptr, int zn = 0, void* yscr = nullptr) {
   const AxisTab& t = axis == 0 ? p->ax : p->ay;
-  const bool long_m = (t.m == 1024 || t.m == 2048 || t.m == 4096) && zn == 0;
+  const bool long_m = (t.m == 1024 || t.m == 2048 || t.m == 4096) && zn == 0 && t.bc != BC_FD;
   if (long_m && (axis == 0 || (yscr && std::is_same<TI, T>::value && std::is_same<TO, T>::value &&
                                !accumulate && !amax && !out2 && !base32))) {
     FastArgs<T> a{};
@@ -334,7 +336,7 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
     return launch_plane_transpose<T>(sc, static_cast<T*>(out), p->nx, p->ny, p->nz, skip, st);
   }
   const int lpc_y = (sizeof(T) == 4 && sizeof(TI) == 4 && sizeof(TO) == 4) ? 16 : 8;
-  const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) &&
+  const bool fast_ok = (t.m == 64 || t.m == 128 || t.m == 256 || t.m == 512) && t.bc != BC_FD &&
                        (axis == 0 || p->nx % lpc_y == 0);
   if (fast_ok) {
     FastArgs<T> a{};
@@ -674,13 +676,15 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   *out = nullptr;
   if (!(alpha >= 0.0) || !std::isfinite(alpha))
     return fail(nullptr, PS_INVALID_ARG, "the Helmholtz shift alpha must be finite and >= 0");
-  if ((unsigned)bcx > 4u || (unsigned)bcy > 4u || (unsigned)bcz > 5u)
-    return fail(nullptr, PS_INVALID_ARG, "unknown boundary condition (face unknowns are for z only)");
+  if ((unsigned)bcx > 5u || (unsigned)bcy > 5u || (unsigned)bcz > 5u)
+    return fail(nullptr, PS_INVALID_ARG, "unknown boundary condition");
   if ((unsigned)prec > 2u) return fail(nullptr, PS_INVALID_ARG, "unknown precision");
   if (!(dx > 0) || !(dy > 0)) return fail(nullptr, PS_INVALID_ARG, "dx and dy must be > 0");
   if (!zf && !(dz > 0)) return fail(nullptr, PS_INVALID_ARG, "dz must be > 0 when zf is NULL");
   if (!size_ok(nx) || !size_ok(ny))
     return fail(nullptr, PS_UNSUPPORTED_SIZE, "nx, ny must be even, 2..8192, with n/2 = 2^a 3^b");
+  if ((bcx == PS_BC_FACE_DIRICHLET && nx > 4096) || (bcy == PS_BC_FACE_DIRICHLET && ny > 4096))
+    return fail(nullptr, PS_UNSUPPORTED_SIZE, "face-centred x or y lines must have n <= 4096");
   if (nz < 2 || nz > 8192) return fail(nullptr, PS_UNSUPPORTED_SIZE, "nz must be in 2..8192");
   if (prec == PS_FP32_REFINE && (max_iter < 0 || !(rtol > 0)))
     return fail(nullptr, PS_INVALID_ARG, "refinement needs rtol > 0 and max_iter >= 0");
@@ -857,8 +861,8 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
     AxisTab& t = *axes[a];
     const int n = ns[a];
     t.n = n;
-    t.m = n / 2;
     t.bc = bcs[a];
+    t.m = t.bc == BC_FD ? n : n / 2;  // FD: the n-point FFT of the odd extension (xform_dev.cuh)
     t.nstages = make_radix(t.m, t.radix);
     t.tw64 = reinterpret_cast<cplx<double>*>(take(8 * n * sizeof(cplx<double>)));
     t.tw32 = reinterpret_cast<cplx<float>*>(take(8 * n * sizeof(cplx<float>)));
@@ -974,6 +978,7 @@ ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, dou
   // (overlapping the rest of that pass and of the loop), and p again after the loop
   // if a later correction changed it.
   const bool pipe = plan->prec == PS_FP32_REFINE && f_dev != p_dev && plan->nz >= 2 &&
+                    plan->ax.bc != BC_FD && plan->ay.bc != BC_FD &&
                     plan->nx % 16 == 0 && (plan->ax.m >= 64 && plan->ax.m <= 512) &&
                     (plan->ay.m >= 64 && plan->ay.m <= 512) && !(plan->ax.m & (plan->ax.m - 1)) &&
                     !(plan->ay.m & (plan->ay.m - 1));

@@ -65,7 +65,8 @@ enum : int {
   RK_SUBMU = 4,   // subtract μ_f (double-float) from the base
   RK_U32 = 8,     // operand U is FP32 (else FP64)
   RK_SHIFT = 16,  // Helmholtz plan: the row also holds −α·U (exact product with each level)
-  RK_SPLIT3 = 32  // three-level split of U (pass 0 and the exact pass; see below)
+  RK_SPLIT3 = 32,  // three-level split of U (pass 0 and the exact pass; see below)
+  RK_FACE = 64     // x or y face unknowns (BC_FD): the wall rows of face_rows
 };
 
 __host__ __device__ constexpr int resid_cells(int rpt) { return (RTX + 2) * (RWARPS * rpt + 2); }
@@ -223,10 +224,28 @@ __device__ __forceinline__ void resid_reduce(const ResidArgs& a, float rmax, flo
   }
 }
 
+// x/y face unknowns (BC_FD): the wall entry's row has the x (or y) part −u_0/Δ²,
+// i.e. the neighbours (u_0, 0) in the second difference, and the first interior
+// row sees the wall node 0 instead of the stored entry. Only tiles that touch the
+// low end of such an axis run this (they are never "interior").
+template <class CT>
+__device__ __forceinline__ void face_rows(const ResidArgs& a, int i, int j, const CT& pc, CT& xm, CT& xp, CT& ym,
+                                          CT& yp) {
+  const CT zero{};
+  if (a.bcx == BC_FD) {
+    if (i == 0) { xm = pc; xp = zero; }
+    else if (i == 1) xm = zero;
+  }
+  if (a.bcy == BC_FD) {
+    if (j == 0) { ym = pc; yp = zero; }
+    else if (j == 1) ym = zero;
+  }
+}
+
 template <int RPT, int KIND>
 __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(ResidArgs a) {
   constexpr bool SING = KIND & RK_SING, FIRST = KIND & RK_FIRST, SUBMU = KIND & RK_SUBMU;
-  constexpr bool U32 = KIND & RK_U32, SPLIT3 = KIND & RK_SPLIT3, SHIFT = KIND & RK_SHIFT;
+  constexpr bool U32 = KIND & RK_U32, SPLIT3 = KIND & RK_SPLIT3, SHIFT = KIND & RK_SHIFT, FACE = KIND & RK_FACE;
   using UT = typename std::conditional<U32, float, double>::type;
   using CT = typename std::conditional<SPLIT3, fxp3, fxp>::type;  // a split cell
   constexpr int TY = RWARPS * RPT, W = RTX + 2, CELLS = resid_cells(RPT);
@@ -270,6 +289,7 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
       int gi = x0 - 1 + cc, gj = y0 - 1 + rr;
       bool ok = e < CELLS && !((gi < 0 || gi >= nx) && (gj < 0 || gj >= ny));  // corners unused
       bool neg = false;
+      const bool gout = (gi < 0 || gi == nx), hout = (gj < 0 || gj == ny);
       if (gi < 0) {
         if (a.bcx == BC_P) gi = nx - 1; else { gi = 0; neg ^= (xl == END_D); }
       } else if (gi == nx) {
@@ -283,6 +303,9 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
         if (a.bcy == BC_P) gj = 0; else { gj = ny - 1; neg ^= (yh == END_D); }
       } else if (gj > ny) {
         ok = false;
+      }
+      if constexpr (FACE) {  // x/y face unknowns (BC_FD): the wall nodes beyond either end are 0
+        if ((gout && a.bcx == BC_FD) || (hout && a.bcy == BC_FD)) ok = false;
       }
       off[h] = ok ? gj * nx + gi : 0;
       okm |= (ok ? 1u : 0u) << h;
@@ -332,9 +355,10 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
     cidx[m] = (ty * RPT + m + 1) * W + tx + 1;
     in[m] = (i < nx) && (jb + m < ny);
   }
-  // Interior tiles (every row and column in the domain) take a copy of the
-  // march without the per-point domain tests.
-  const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny);
+  // Interior tiles (every row and column in the domain, no face-unknown wall row)
+  // take a copy of the march without the per-point domain tests.
+  const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny) &&
+                        !(FACE && ((a.bcx == BC_FD && x0 == 0) || (a.bcy == BC_FD && y0 == 0)));
   const size_t col = (size_t)jb * nx + i;  // this thread's column, row jb, plane 0
   // the base of each point: f (FP64, split into hi + lo)
   using base_t = double;
@@ -404,9 +428,10 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 4 ? 3 : 4) residual_kernel(Re
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
       const CT pc = zc[m];
-      const CT xm = Fc[cidx[m] - 1], xp = Fc[cidx[m] + 1];
-      const CT ym = (m == 0) ? Fc[cidx[0] - W] : zc[m > 0 ? m - 1 : 0];
-      const CT yp = (m == RPT - 1) ? Fc[cidx[RPT - 1] + W] : zc[m + 1 < RPT ? m + 1 : 0];
+      CT xm = Fc[cidx[m] - 1], xp = Fc[cidx[m] + 1];
+      CT ym = (m == 0) ? Fc[cidx[0] - W] : zc[m > 0 ? m - 1 : 0];
+      CT yp = (m == RPT - 1) ? Fc[cidx[RPT - 1] + W] : zc[m + 1 < RPT ? m + 1 : 0];
+      if constexpr (FACE && !FULL) face_rows(a, i, jb + m, pc, xm, xp, ym, yp);
       const CT zmv = zm[m], zpv = zp[m];
       const df bv = df_from_f64(bcur[m]);
       // exact high-part stencil sums (fixed-point grid), FP32 low parts
@@ -567,9 +592,9 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 8 ? 2 : 3) residual_acc_kerne
       ok = true;
       neg = false;
       if (gj < 0) {
-        if (a.bcy == BC_P) gj = ny - 1; else { gj = 0; neg = (yl == END_D); }
+        if (a.bcy == BC_P) gj = ny - 1; else if (a.bcy == BC_FD) { gj = 0; ok = false; } else { gj = 0; neg = (yl == END_D); }
       } else if (gj == ny) {
-        if (a.bcy == BC_P) gj = 0; else { gj = ny - 1; neg = (yh == END_D); }
+        if (a.bcy == BC_P) gj = 0; else if (a.bcy == BC_FD) { gj = 0; ok = false; } else { gj = ny - 1; neg = (yh == END_D); }
       } else if (gj > ny) {
         ok = false;
       }
@@ -580,9 +605,9 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 8 ? 2 : 3) residual_acc_kerne
       ok = true;
       neg = false;
       if (gi < 0) {
-        if (a.bcx == BC_P) gi = nx - 1; else { gi = 0; neg = (xl == END_D); }
+        if (a.bcx == BC_P) gi = nx - 1; else if (a.bcx == BC_FD) { gi = 0; ok = false; } else { gi = 0; neg = (xl == END_D); }
       } else if (gi == nx) {
-        if (a.bcx == BC_P) gi = 0; else { gi = nx - 1; neg = (xh == END_D); }
+        if (a.bcx == BC_P) gi = 0; else if (a.bcx == BC_FD) { gi = 0; ok = false; } else { gi = nx - 1; neg = (xh == END_D); }
       } else if (gi > nx) {
         ok = false;
       }
@@ -683,7 +708,8 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 8 ? 2 : 3) residual_acc_kerne
     cidx[m] = (ty * RPT + m + 1) * AW + 4 + tx;
     in[m] = (i < nx) && (jb + m < ny);
   }
-  const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny);
+  const bool interior = (x0 + RTX <= nx) && (y0 + TY <= ny) && !(a.bcx == BC_FD && x0 == 0) &&
+                        !(a.bcy == BC_FD && y0 == 0);
   const size_t col = (size_t)jb * nx + i;
   auto load_base = [&](int k, float2* bv, auto full_tag) {
     constexpr bool FULL = decltype(full_tag)::value;
@@ -743,9 +769,10 @@ __global__ void __launch_bounds__(RTHREADS, RPT >= 8 ? 2 : 3) residual_acc_kerne
 #pragma unroll
       for (int m = 0; m < RPT; ++m) {
         const int ci = cidx[m];
-        const float xm = Rc[ci - 1], xp = Rc[ci + 1];
-        const float ym = (m == 0) ? Rc[ci - AW] : zc[m > 0 ? m - 1 : 0];
-        const float yp = (m == RPT - 1) ? Rc[ci + AW] : zc[m + 1 < RPT ? m + 1 : 0];
+        float xm = Rc[ci - 1], xp = Rc[ci + 1];
+        float ym = (m == 0) ? Rc[ci - AW] : zc[m > 0 ? m - 1 : 0];
+        float yp = (m == RPT - 1) ? Rc[ci + AW] : zc[m + 1 < RPT ? m + 1 : 0];
+        if (!FULL) face_rows(a, i, jb + m, zc[m], xm, xp, ym, yp);
         float acc = sig, lo = 0.f;
         auto term = [&](float u, df wt) {
           const float a2 = __fmaf_rn(u, wt.h, acc);
@@ -846,6 +873,23 @@ cudaError_t launch_kind(const ResidArgs& b, dim3 grid, cudaStream_t st) {
 }
 template <int RPT>
 cudaError_t launch_rpt(const ResidArgs& b, int kind, dim3 grid, cudaStream_t st) {
+  if (kind & RK_FACE) {  // plans with x or y face unknowns (never singular)
+    if constexpr (RPT == 2) {
+      switch (kind & ~RK_FACE) {
+        case RK_SPLIT3: return launch_kind<RPT, RK_SPLIT3 | RK_FACE>(b, grid, st);
+        case RK_SPLIT3 | RK_SHIFT: return launch_kind<RPT, RK_SPLIT3 | RK_SHIFT | RK_FACE>(b, grid, st);
+        case RK_SPLIT3 | RK_U32 | RK_FIRST: return launch_kind<RPT, RK_SPLIT3 | RK_U32 | RK_FIRST | RK_FACE>(b, grid, st);
+        case RK_SPLIT3 | RK_U32 | RK_FIRST | RK_SHIFT:
+          return launch_kind<RPT, RK_SPLIT3 | RK_U32 | RK_FIRST | RK_SHIFT | RK_FACE>(b, grid, st);
+        default: break;
+      }
+    }
+    switch (kind & ~RK_FACE) {
+      case RK_U32 | RK_FIRST: return launch_kind<RPT, RK_U32 | RK_FIRST | RK_FACE>(b, grid, st);
+      case RK_U32 | RK_FIRST | RK_SHIFT: return launch_kind<RPT, RK_U32 | RK_FIRST | RK_SHIFT | RK_FACE>(b, grid, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if constexpr (RPT == 2) {  // the three-level passes run with two rows per thread only
     switch (kind) {
       case RK_SPLIT3: return launch_kind<RPT, RK_SPLIT3>(b, grid, st);
@@ -907,6 +951,7 @@ cudaError_t launch_resid_acc(const ResidArgs& b0, int pass, cudaStream_t st) {
 }
 cudaError_t launch_resid(const ResidArgs& b0, int kind, int reset_f, cudaStream_t st) {
   reset_red_kernel<<<1, 1, 0, st>>>(b0.red, b0.skip, reset_f);
+  if (b0.bcx == BC_FD || b0.bcy == BC_FD) kind |= RK_FACE;
   const ResidShape s = resid_shape(b0.nx, b0.ny, b0.nz, (kind & RK_SPLIT3) ? RS_SPLIT3 : RS_PASS0);
   ResidArgs b = b0;
   b.zchunk = s.zchunk;

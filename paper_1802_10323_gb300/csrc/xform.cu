@@ -28,7 +28,8 @@ int pick_lines(int n, int axis, int nx, int nlines) {
 
 template <class T, class TI, class TO, bool FWD>
 cudaError_t launch_xform(XformArgs<T> a, cudaStream_t st) {
-  a.L = pick_lines<T>(a.n, a.axis, a.nx, a.nlines);
+  // (pick_lines sizes the buffers for m = n/2; a face-centred line's FFT has m = n)
+  a.L = pick_lines<T>(a.m == a.n ? 2 * a.n : a.n, a.axis, a.nx, a.nlines);
   const size_t smem = 2 * (size_t)a.L * (a.m + 1) * sizeof(cplx<T>);
   int grid = (a.axis == 0) ? (a.nlines + a.L - 1) / a.L : a.nz * (a.nx / a.L);
   auto k = xform_kernel<T, TI, TO, FWD>;

@@ -11,6 +11,12 @@
 //   ND  (DCT-IV): u_r = (a_2r + i a_{n−1−2r}) e^{−iπr/n}, U = FFT_m(u),
 //        X_2k = 2 Re(c_k), X_{n−1−2k} = −2 Im(c_k), c_k = e^{−iπ(4k+1)/4n} U_k;
 //        DCT-IV is its own inverse up to 2n.
+//   FD  (x/y face unknowns, DST-I of the interior, the wall entry copied): the odd
+//        extension y of length 2n (y_0 = y_n = 0, y_t = a_t, y_{2n−t} = −a_t) is a
+//        real sequence whose DFT is Y_k = −2i Σ_t a_t sin(πtk/n); it is done as an
+//        FFT of m = n complex points z_j = y_2j + i y_2j+1 and the real-DFT split
+//        Y_k = E_k + e^{−iπk/n} O_k, giving X_k = −Im(Y_k). DST-I is its own inverse
+//        up to 2n, so the backward transform is the same with the factor 1/(2n).
 // Backward transforms include Table 1's normalisation (1/n or 1/2n).
 //
 // One CTA transforms L lines. x-lines are contiguous rows of the
@@ -55,9 +61,11 @@ __device__ __forceinline__ void bfly3(cplx<T>* v) {
 }
 
 // One Stockham stage of radix R over L lines of m points (row stride ld).
+// tw is the 8n-entry table e^{−2πi t/(8n)}; ω_m^x = tw[twm·x] with twm = 8n/m
+// (16 for the m = n/2 FFTs, 8 for the m = n FFT of a face-centred line).
 template <class T, int R, bool INV>
 __device__ __forceinline__ void stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst,
-                                      int L, int m, int ld, int Ns, const cplx<T>* __restrict__ tw) {
+                                      int L, int m, int ld, int Ns, const cplx<T>* __restrict__ tw, int twm) {
   const int nb = m / R;
   const int tws = m / (Ns * R);
   for (int idx = threadIdx.x; idx < L * nb; idx += blockDim.x) {
@@ -71,7 +79,7 @@ __device__ __forceinline__ void stage(const cplx<T>* __restrict__ src, cplx<T>* 
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cplx<T> w = tw[16 * (r * k * tws)];
+        cplx<T> w = tw[twm * (r * k * tws)];
         if (INV) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
@@ -139,7 +147,15 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
 
   // ---- 2. pre-processing: reals (bufB) -> m complex points (bufA) ---------------
   const int bc = a.bc;
-  if (FWD) {
+  if (bc == BC_FD) {  // both directions: z_j = (y_2j, y_2j+1) of the odd extension (m = n)
+    for (int idx = threadIdx.x; idx < L * m; idx += blockDim.x) {
+      const int l = idx / m, j = idx - l * m;
+      const T* x = rB + l * ldr;
+      auto y = [&](int t) -> T { return (t == 0 || t == n) ? (T)0 : (t < n ? x[t] : -x[2 * n - t]); };
+      bufA[l * ld + j] = cplx<T>{y(2 * j), y(2 * j + 1)};
+      if (j == 0) bufA[l * ld + m] = cplx<T>{x[0], (T)0};  // the wall entry, in the slot no stage writes
+    }
+  } else if (FWD) {
     for (int idx = threadIdx.x; idx < L * m; idx += blockDim.x) {
       const int l = idx / m, p = idx - l * m;
       const T* x = rB + l * ldr;
@@ -217,18 +233,19 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
   cplx<T>* src = bufA;
   cplx<T>* dst = bufB;
   {
-    const bool inv = !FWD && !bc_iv(bc);
+    const bool inv = !FWD && !bc_iv(bc) && bc != BC_FD;
+    const int twm = (8 * n) / m;
     int Ns = 1;
     for (int s = 0; s < a.nstages; ++s) {
       const int R = a.radix[s];
       if (inv) {
-        if (R == 4) stage<T, 4, true>(src, dst, L, m, ld, Ns, tw);
-        else if (R == 2) stage<T, 2, true>(src, dst, L, m, ld, Ns, tw);
-        else stage<T, 3, true>(src, dst, L, m, ld, Ns, tw);
+        if (R == 4) stage<T, 4, true>(src, dst, L, m, ld, Ns, tw, twm);
+        else if (R == 2) stage<T, 2, true>(src, dst, L, m, ld, Ns, tw, twm);
+        else stage<T, 3, true>(src, dst, L, m, ld, Ns, tw, twm);
       } else {
-        if (R == 4) stage<T, 4, false>(src, dst, L, m, ld, Ns, tw);
-        else if (R == 2) stage<T, 2, false>(src, dst, L, m, ld, Ns, tw);
-        else stage<T, 3, false>(src, dst, L, m, ld, Ns, tw);
+        if (R == 4) stage<T, 4, false>(src, dst, L, m, ld, Ns, tw, twm);
+        else if (R == 2) stage<T, 2, false>(src, dst, L, m, ld, Ns, tw, twm);
+        else stage<T, 3, false>(src, dst, L, m, ld, Ns, tw, twm);
       }
       __syncthreads();
       cplx<T>* t = src;
@@ -241,7 +258,23 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
   T* rO = reinterpret_cast<T*>(dst);
 
   // ---- 4. post-processing: m complex points -> n reals --------------------------
-  if (FWD) {
+  if (bc == BC_FD) {  // X_k = −Im(Y_k), k = 1 … n−1 (× 1/2n backward); the wall entry copied
+    const T sc = FWD ? (T)1 : (T)1 / (T)(2 * n);
+    for (int idx = threadIdx.x; idx < L * n; idx += blockDim.x) {
+      const int l = idx / n, k = idx - l * n;
+      const cplx<T>* Z = src + l * ld;
+      T* o = rO + l * ldr;
+      if (k == 0) {  // the wall entry (saved beside the FFT data by the pre-processing)
+        o[0] = bufA[l * ld + m].x;
+        continue;
+      }
+      const cplx<T> Zk = Z[k], Zmk = Z[m - k];
+      const cplx<T> E = cscale(cadd(Zk, conj_(Zmk)), (T)0.5);
+      const cplx<T> O = cscale(mul_mi(csub(Zk, conj_(Zmk))), (T)0.5);
+      const cplx<T> Y = cadd(E, cmul(tw[4 * k], O));
+      o[k] = -Y.y * sc;
+    }
+  } else if (FWD) {
     const int np = bc_iv(bc) ? m : (m / 2 + 1);
     for (int idx = threadIdx.x; idx < L * np; idx += blockDim.x) {
       const int l = idx / np, k = idx - l * np;
