@@ -74,7 +74,16 @@ def source_hash():
 
 
 FP64_FLOPS_PER_POINT = 126      # plain FP64 solve at n = 1024 (see the fp64_solve roofline)
-NS_FP64_OPS_PER_CELL = 126      # the RK3 predictor kernel, FP64 fields (see the rk3_step roofline)
+# Algorithmic FP64 flops per cell of the RK3 predictor (AD^k of the three components and
+# the predictor update, counted from the stencils of the substep, not from a kernel):
+#   advection: u·u, v·v, w·w at the cell centre (average, square) 3 × 3; their differences
+#     3 × 2; the three edge products (two averages, a product, the ¼) 3 × 4; the six
+#     edge-product differences 6 × 2; three terms summed per component 3 × 2      = 45
+#   diffusion: per component x and y second differences 2 × 3, the stretched z one 6,
+#     summed 2                                                       3 × 14      = 42
+#   AD = −adv + ν·lap: 3; predictor u* = u + Δt(α AD + β AD' − γ G p) with the
+#     pressure gradient difference: 3 × 6                              3 + 18      = 21
+NS_FLOPS_PER_CELL = 108
 NUM_SMS_GB300 = 152
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64
 
@@ -143,8 +152,9 @@ def make_input(n, seed, device):
     return f.contiguous(), zf, dx, dy
 
 
-def cpu_oracle_rate(nz_sample=None, target_s=15.0):
-    """Mpts/s of the FP64 oracle solve on a 1024 × 1024 × nz_sample slab of the workload."""
+def cpu_oracle_rate(nz_sample=None, target_s=15.0, keep=None):
+    """Mpts/s of the FP64 oracle solve on a 1024 × 1024 × nz_sample slab of the workload.
+    keep: a dict that receives the slab's f, the oracle's solution and the grid."""
     import numpy as np
     from oracle import solve as S
     from paper_1802_10323_gb300 import synth
@@ -156,12 +166,15 @@ def cpu_oracle_rate(nz_sample=None, target_s=15.0):
         f = synth.divergence_rhs(u, v, w, dx, dy, zf)
         del u, v, w
         t0 = time.perf_counter()
-        S.solve(f, dx, dy, zf, *BCS)
-        return time.perf_counter() - t0
+        q = S.solve(f, dx, dy, zf, *BCS)
+        dt = time.perf_counter() - t0
+        if keep is not None:
+            keep.update(f=f, q=q, zf=zf, dx=dx, dy=dy, nz=nzs)
+        return dt
 
     if nz_sample is None:
         t8 = run(8)
-        nz_sample = int(min(256, max(8, 8 * target_s / max(t8, 1e-3))) // 8 * 8)
+        nz_sample = int(min(256, max(16, 8 * target_s / max(t8, 1e-3))) // 8 * 8)
     t = run(nz_sample)
     pts = GRID["nx"] * GRID["ny"] * nz_sample
     cores = len(os.sched_getaffinity(0))
@@ -174,6 +187,67 @@ def cpu_oracle_rate(nz_sample=None, target_s=15.0):
                       f"1024x1024x{nz_sample} slab of the channel workload "
                       f"(same x/y sizes, BCs, tanh z), {t:.1f} s; BLAS={blas}, "
                       f"threads={cores}"}
+
+
+def scipy_cpu_rate(slab):
+    """A library CPU solve of the oracle's slab for context ("library CPU", not the
+    oracle): scipy.fft real FFTs along the periodic x and y (the same eigenvalues
+    of Table 1 in the standard complex layout) and a vectorised Thomas sweep along
+    the Neumann z, FP64, on the host's cores. Returns Mpts/s and its error against
+    the oracle's solution."""
+    import numpy as np
+    import scipy.fft as sfft
+    f, q, zf, dx, dy = slab["f"], slab["q"], slab["zf"], slab["dx"], slab["dy"]
+    nz, ny, nx = f.shape
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    fh = sfft.rfft2(f, axes=(1, 2), workers=cores)             # [nz][ny][nx/2+1] complex
+    kx = np.arange(nx // 2 + 1)
+    ky = np.concatenate([np.arange(ny // 2 + 1), np.arange(ny // 2 + 1 - ny, 0)])
+    lam = (-4 * np.sin(np.pi * kx / nx) ** 2 / dx ** 2)[None, :] + (-4 * np.sin(np.pi * ky / ny) ** 2 / dy ** 2)[:, None]
+    dzf = np.diff(zf)
+    dzc = 0.5 * (dzf[1:] + dzf[:-1])
+    a = np.zeros(nz)
+    c = np.zeros(nz)
+    a[1:] = 1.0 / (dzf[1:] * dzc)
+    c[:-1] = 1.0 / (dzf[:-1] * dzc)
+    b = -(a + c)
+    # (0, 0): the singular column, pinned and mean-free (Δz^f-weighted), as the oracle
+    d = fh[:, 0, 0].real.copy()
+    d -= (dzf * d).sum() / dzf.sum()
+    lam00 = lam[0, 0]
+    lam[0, 0] = 1.0                                            # any nonzero value; replaced below
+    cp = np.zeros((nz,) + lam.shape)
+    dp = np.zeros_like(fh)
+    den = b[0] + lam
+    cp[0] = c[0] / den
+    dp[0] = fh[0] / den
+    for k in range(1, nz):
+        den = b[k] + lam - a[k] * cp[k - 1]
+        cp[k] = c[k] / den
+        dp[k] = (fh[k] - a[k] * dp[k - 1]) / den
+    x = np.empty_like(fh)
+    x[-1] = dp[-1]
+    for k in range(nz - 2, -1, -1):
+        x[k] = dp[k] - cp[k] * x[k + 1]
+    s = np.zeros(nz)                                           # the singular column
+    cc, dd = np.zeros(nz), np.zeros(nz)
+    den = b[1] + lam00
+    cc[1], dd[1] = c[1] / den, d[1] / den
+    for k in range(2, nz):
+        den = b[k] + lam00 - a[k] * cc[k - 1]
+        cc[k], dd[k] = c[k] / den, (d[k] - a[k] * dd[k - 1]) / den
+    s[-1] = dd[-1]
+    for k in range(nz - 2, 0, -1):
+        s[k] = dd[k] - cc[k] * s[k + 1]
+    s -= (dzf * s).sum() / dzf.sum()
+    x[:, 0, 0] = s
+    p = sfft.irfft2(x, s=(ny, nx), axes=(1, 2), workers=cores)
+    t = time.perf_counter() - t0
+    return {"value": nx * ny * nz / t / 1e6, "unit": "Mpts/s", "cores": cores, "kind": "library CPU (scipy.fft)",
+            "max_rel_err_vs_oracle": float(np.abs(p - q).max() / np.abs(q).max()),
+            "sample": f"the oracle's {nx}x{ny}x{nz} slab: scipy.fft rfft2/irfft2 in x and y, vectorised "
+                      f"Thomas in z, FP64, {t:.2f} s"}
 
 
 class Ranks:
@@ -346,6 +420,17 @@ def bench_ours(args):
     p64 = torch.empty_like(f)
     plan64.solve(f, p64)
     torch.cuda.synchronize()
+    # the FP64 pipe's measured rate (the FP64 solve and the RK3 predictor are bound by it),
+    # with the SM clocks sampled while the probe runs
+    ck = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    time.sleep(0.25)
+    tfl, pms = lib.probe_fp64(iters=400000)
+    time.sleep(0.25)
+    pclk = ck.stop() if ck else None
+    fp64_peak = {"tflops": tfl, "probe_ms": pms, "clocks": pclk,
+                 "source": f"measured: ps_probe_fp64 (FP64 FMA chains on every SM, {pms:.0f} ms, "
+                           f"SM clock median {pclk['sm_mhz'] if pclk else None} MHz)",
+                 "nominal_tflops": FP64_NOMINAL_TFLOPS}
     k64 = max(1, args.fp64_steps)
     plan64.profile(True)
     e0.record(stream)
@@ -417,12 +502,10 @@ def bench_ours(args):
     if not args.no_long and args.n == 1024 and not args.nz:
         from paper_1802_10323_gb300 import synth
         nl = (8192, 8192, 16)
-        zl = synth.tanh_faces(nl[2], 1.0, 1.5)
-        gl = torch.Generator(device=dev)
-        gl.manual_seed(GRID["seed"])
-        fl = torch.randn((nl[2], nl[1], nl[0]), generator=gl, device=dev, dtype=torch.float64)
-        fl -= fl.mean()
-        planl = lib.Plan(nl[0], nl[1], nl[2], 6.0 / nl[0], 3.0 / nl[1], zf=zl, bcs=BCS,
+        # the headline's right-hand side (divergence of a Gaussian staggered velocity) on
+        # the same 6 x 3 x 1 channel box with 8192 x 8192 x 16 cells
+        fl, zl, dxl, dyl = make_input(nl, GRID["seed"], dev)
+        planl = lib.Plan(nl[0], nl[1], nl[2], dxl, dyl, zf=zl, bcs=BCS,
                          precision="fp32_refine", rtol=RTOL, max_iter=MAX_ITER)
         pl_ = torch.empty_like(fl)
         infl = lib.info_tensor(dev)
@@ -451,8 +534,10 @@ def bench_ours(args):
                               "unit": "GB/s", "frac": achl / peak, "avg_launch_ms": avgl,
                               "algorithmic_bytes_per_launch": bpp[doml] * ptsl},
                  "rel_residual": il.rel_residual, "status": il.status,
-                 "workload": "8192x8192x16 (x and y lines of 8192, the shared-memory transform kernel), "
-                             "6x3x1 box, P/P/NN tanh z, f ~ N(0,1) mean removed (Philox seed 3), FP32+refine to 1e-10"}
+                 "kernels_ms_per_step": {k: v[3] / kl for k, v in profl.items() if v[1]},
+                 "workload": "8192x8192x16 (x and y lines of 8192: the one-line-per-CTA transform kernel, "
+                             "y lines through plane transposes), 6x3x1 box, P/P/NN tanh z, "
+                             "f = div(Gaussian staggered velocity) (Philox seed 3), FP32+refine to 1e-10"}
         planl.close()
         del fl, pl_, planl
         torch.cuda.empty_cache()
@@ -497,17 +582,16 @@ def bench_ours(args):
         cells5 = n5[0] * n5[1] * n5[2]
         pl5, pa5, _, pm5 = prof5["ns_predict"]
         pred_ms = pm5 / max(pa5, 1)
-        fp64_rate = 2 * NUM_SMS_GB300 * 2.07e9 / 1e12   # FP64 operations per second (T), max clock
         ns = {"value": job_rate(world, n5[0] * n5[1] * n5[2], ms5), "unit": "Mpts/s (cells x RK3 steps)",
               "ms_per_rk3_step": ms5, "grid": list(n5), "last_solve_status": i5.status,
-              # the fused predictor is bound by the FP64 pipe: ≈ 126 FP64 operations per cell
-              # (counted from the kernel source) against 2 per clock per SM
-              "roofline": {"bound": "fp64", "kernel": "ns_predict", "ops_per_cell": NS_FP64_OPS_PER_CELL,
+              # the fused predictor is bound by the FP64 pipe: its algorithmic flops (the
+              # stencils' count, NS_FLOPS_PER_CELL) against the measured FP64 FMA rate
+              "roofline": {"bound": "fp64", "kernel": "ns_predict", "flops_per_cell": NS_FLOPS_PER_CELL,
                            "avg_launch_ms": pred_ms,
-                           "achieved": NS_FP64_OPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12,
-                           "peak": fp64_rate, "unit": "T FP64 ops/s",
-                           "peak_source": "2 FP64 operations per clock per SM (probe) x 152 SMs x 2.07 GHz",
-                           "frac": NS_FP64_OPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12 / fp64_rate},
+                           "achieved": NS_FLOPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12,
+                           "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
+                           "peak_source": fp64_peak["source"],
+                           "frac": NS_FLOPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12 / fp64_peak["tflops"]},
               "kernels_ms_per_step": {k: v[3] / k5 for k, v in prof5.items() if v[0]},
               "last_solve_rel_residual": i5.rel_residual,
               "workload": "3 substeps of ps_ns_substep (predictor, divergence, refined solve to 1e-10, "
@@ -578,8 +662,30 @@ def bench_ours(args):
         bt.close()
 
     cpu = None
+    vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_oracle_rate()
+        slab = {}
+        cpu = cpu_oracle_rate(keep=slab)
+        cpu["library_cpu"] = scipy_cpu_rate(slab)
+        # the FP64 and refined GPU solves of the same slab (same x/y lines, BCs, tanh z)
+        # against the oracle's solution, element by element
+        import numpy as np
+        fs = torch.as_tensor(slab["f"], device=dev).contiguous()
+        vs_oracle = {"slab": [GRID["nx"], GRID["ny"], slab["nz"]],
+                     "input": "f = div(Gaussian staggered velocity) (PCG64 seed 3) on the slab's own tanh z"}
+        for prec in ("fp64", "fp32_refine"):
+            pls = lib.Plan(GRID["nx"], GRID["ny"], slab["nz"], slab["dx"], slab["dy"], zf=slab["zf"], bcs=BCS,
+                           precision=prec, rtol=RTOL, max_iter=MAX_ITER)
+            infs = lib.info_tensor(dev)
+            ps_ = pls.solve(fs, info=infs)
+            torch.cuda.synchronize()
+            got = ps_.cpu().numpy()
+            vs_oracle[prec] = {"max_rel_err": float(np.abs(got - slab["q"]).max() / np.abs(slab["q"]).max()),
+                               "status": lib.read_info(infs).status}
+            pls.close()
+            del ps_
+        del fs
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {
@@ -593,21 +699,25 @@ def bench_ours(args):
                        "l2": "no flush: every field (8.6 GB at 1024^3) exceeds the 126 MB L2",
                        "parallelism": f"replicas x{world}"},
             "refine": {"iterations": inf.iterations, "rel_residual": inf.rel_residual,
-                       "status": inf.status},
+                       "status": inf.status,
+                       "max_rel_err_vs_oracle": vs_oracle["fp32_refine"]["max_rel_err"] if vs_oracle else None},
             "fp64_solve": {"value": job_rate(world, N, ms64), "unit": "Mpts/s",
                            "ms_per_step": ms64, "max_rel_diff_vs_refined": diff,
+                           "max_rel_err_vs_oracle": vs_oracle["fp64"]["max_rel_err"] if vs_oracle else None,
+                           "vs_oracle": vs_oracle,
                            # FP64-ALU bound on this part: four transforms (≈ 2.5·log2 n + 4 flops
                            # per point each) and the Thomas sweep (≈ 9), ≈ 126 flops per point at
                            # n = 1024, against the nominal FP64 rate; and its 80 B/pt against HBM
                            "roofline_fp64": {"bound": "fp64", "flops_per_point": FP64_FLOPS_PER_POINT,
                                              "achieved": FP64_FLOPS_PER_POINT * N / (ms64 * 1e-3) / 1e12,
-                                             "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                                             "peak_source": "nominal (no measured FP64 peak)",
+                                             "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
+                                             "peak_source": fp64_peak["source"],
                                              "frac": FP64_FLOPS_PER_POINT * N / (ms64 * 1e-3) / 1e12
-                                             / FP64_NOMINAL_TFLOPS,
+                                             / fp64_peak["tflops"],
                                              "hbm_frac": 80 * N / (ms64 * 1e-3) / 1e9 / peak},
                            "kernels": {k: v[3] / k64 for k, v in prof64.items() if v[0]}},
             "speedup_vs_fp64": ms64 / ms_max,
+            "fp64_peak": fp64_peak,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "algorithmic_bytes_per_launch": bytes_launch,

@@ -270,6 +270,16 @@ ps_status ps_profile_enable(ps_plan* plan, int enable);
 /* Fill up to `max` entries (one per kernel kind), set *count, clear the window. */
 ps_status ps_profile_read(ps_plan* plan, ps_kernel_stat* stats, int max, int* count);
 
+/* ---- Measurement utility (the paper has no counterpart) -----------------------
+ * FP64 FMA throughput of the current device, in TFLOP/s (two FLOPs per FMA): one
+ * launch of 8·(SM count) CTAs of 256 threads, each running eight independent
+ * chains of `iters` FP64 fused multiply-adds, timed with CUDA events on `stream`
+ * (after one short warm-up launch); *ms receives the timed launch's duration.
+ * Synchronises the stream and allocates a small device buffer; not for the
+ * solve path. The denominator of the plain FP64 solve's roofline, which is bound
+ * by the FP64 pipe (1/64 of the FP32 rate on GB300), not by HBM. */
+ps_status ps_probe_fp64(int iters, double* tflops, double* ms, void* stream);
+
 /* ---- Batched solve: many independent grids, one persistent launch ----------
  * Each grid is an independent problem of §2.1 with its own sizes, spacings,
  * z faces and BC pairs. */

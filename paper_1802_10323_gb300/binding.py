@@ -77,6 +77,7 @@ _SIGS = {
     "ps_batch_destroy": [_vp],
     "ps_batch_autotune": [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)],
     "ps_batch_configure": [_vp, _d, _i],
+    "ps_probe_fp64": [_i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -115,6 +116,13 @@ def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def probe_fp64(iters=20000, stream=None):
+    """Measured FP64 FMA throughput of the current device: (TFLOP/s, ms of the timed launch)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ps_probe_fp64(int(iters), ctypes.byref(tf), ctypes.byref(ms), _stream_ptr(stream)))
+    return tf.value, ms.value
 
 
 def info_tensor(device="cuda"):
