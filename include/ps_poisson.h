@@ -270,6 +270,14 @@ ps_status ps_profile_enable(ps_plan* plan, int enable);
 /* Fill up to `max` entries (one per kernel kind), set *count, clear the window. */
 ps_status ps_profile_read(ps_plan* plan, ps_kernel_stat* stats, int max, int* count);
 
+/* ---- Fault injection for tests (the paper has no counterpart) ----------------
+ * The next `count` device allocations of ps_plan_create / ps_plan_create_helmholtz
+ * / ps_batch_create fail on the host as if cudaMalloc had returned
+ * cudaErrorMemoryAllocation (no device memory is touched): the create call returns
+ * PS_OUT_OF_MEMORY, leaves *out NULL and frees what it had made. 0 disarms.
+ * PS_INVALID_ARG for a negative count. Process-wide. */
+ps_status ps_inject_alloc_failures(int count);
+
 /* ---- Measurement utility (the paper has no counterpart) -----------------------
  * FP64 FMA throughput of the current device, in TFLOP/s (two FLOPs per FMA): one
  * launch of 8·(SM count) CTAs of 256 threads, each running eight independent

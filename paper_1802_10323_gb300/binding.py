@@ -78,6 +78,7 @@ _SIGS = {
     "ps_batch_autotune": [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)],
     "ps_batch_configure": [_vp, _d, _i],
     "ps_probe_fp64": [_i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp],
+    "ps_inject_alloc_failures": [_i],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -116,6 +117,11 @@ def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def inject_alloc_failures(count):
+    """Test hook: the next `count` plan/batch device allocations fail on the host."""
+    _check(_lib.ps_inject_alloc_failures(int(count)))
 
 
 def probe_fp64(iters=20000, stream=None):

@@ -509,7 +509,7 @@ ps_status build_tables(ps_batch* b) {
   const size_t bytes = a256(sizeof(BGrid) * G) + a256(sizeof(int4) * tasks.size()) +
                        2 * a256(sizeof(int) * (size_t)G * S) + 2 * a256(sizeof(int) * S);
   char* dev = nullptr;
-  cudaError_t e = cudaMalloc(&dev, bytes);
+  cudaError_t e = take_injected_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&dev, bytes);
   if (e != cudaSuccess) return bfail(b, PS_OUT_OF_MEMORY, "cudaMalloc of batch tables failed");
   b->dev = dev;
   size_t off = 0;

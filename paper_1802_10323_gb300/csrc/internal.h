@@ -20,6 +20,9 @@ __host__ __device__ inline bool bc_iv(int bc) { return bc == BC_ND || bc == BC_D
 constexpr int kMaxN = 8192;
 constexpr int kMaxStages = 12;
 extern thread_local char g_launch_diag[256];  // configuration of the last failed launch
+// Test hook (ps_inject_alloc_failures): true while injected device-allocation failures
+// remain; each call consumes one.
+bool take_injected_alloc_failure();
 
 // Arguments of one batch of line transforms (x or y).
 template <class T>

@@ -10,6 +10,7 @@
 
 #include <new>
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -172,6 +173,8 @@ struct ps_plan {
 };
 
 namespace {
+
+std::atomic<int> g_inject_alloc{0};
 
 ps_status fail(ps_plan* p, ps_status st, const char* msg) {
   if (p) snprintf(p->err, sizeof(p->err), "%s", msg);
@@ -632,6 +635,13 @@ ps_status check_solve_args(ps_plan* p, const void* f, const void* out, const voi
 namespace ps {
 void set_plan_error(ps_plan* plan, const char* msg) { fail(plan, PS_OK, msg); }
 
+bool take_injected_alloc_failure() {
+  int c = g_inject_alloc.load();
+  while (c > 0)
+    if (g_inject_alloc.compare_exchange_weak(c, c - 1)) return true;
+  return false;
+}
+
 double ps_plan_internal_alpha(const ps_plan* p) { return p->alpha; }
 
 void ps_plan_internal_tables(const ps_plan* p, const cplx<float>** twx, const cplx<float>** twy,
@@ -820,7 +830,7 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
   bytes += 6 * align256(nz * sizeof(double)) + 6 * align256(nz * sizeof(float)) +
            2 * align256(nz * sizeof(float2)) + align256(3 * nz * sizeof(float2));
   char* dev = nullptr;
-  cudaError_t e = cudaMalloc(&dev, bytes);
+  cudaError_t e = take_injected_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&dev, bytes);
   if (e != cudaSuccess) {
     delete p;
     char buf[200];
@@ -1240,5 +1250,11 @@ ps_status ps_plan_destroy(ps_plan* plan) {
 }
 
 const char* ps_last_error(const ps_plan* plan) { return plan ? plan->err : g_create_err; }
+
+ps_status ps_inject_alloc_failures(int count) {
+  if (count < 0) return PS_INVALID_ARG;
+  g_inject_alloc.store(count);
+  return PS_OK;
+}
 
 }  // extern "C"

@@ -88,3 +88,18 @@ def test_helmholtz_shift_validated(binding, alpha):
 def test_ns_substep_null_plan(binding):
     assert binding.ps_ns_substep(None, 1, 1e-3, 0.0, None, None, None, None, None, None, None, None,
                                  None) == binding.PS_INVALID_ARG
+
+
+def test_injected_allocation_failure(binding):
+    """A host-injected allocation failure (the stand-in for an out-of-memory device)
+    makes ps_plan_create return PS_OUT_OF_MEMORY cleanly: a NULL plan and a message,
+    one injection consumed per create; a negative count is refused. No device is
+    touched, so this runs without a GPU."""
+    assert binding.ps_inject_alloc_failures(-1) == binding.PS_INVALID_ARG
+    assert binding.ps_inject_alloc_failures(2) == binding.PS_OK
+    for prec in (0, 2):
+        h = ctypes.c_void_p(12345)
+        st = binding.ps_plan_create(ctypes.byref(h), 8, 8, 8, 1.0, 1.0, None, 1.0, 0, 0, 1, prec, 1e-10, 3)
+        assert st == binding.PS_OUT_OF_MEMORY and not h.value
+        assert b"cudaMalloc" in binding.ps_last_error(None)
+    assert binding.ps_inject_alloc_failures(0) == binding.PS_OK
