@@ -17,10 +17,12 @@ axis being the face on the low side of cell i; the stack is (3, n_z, n_y, n_x).
 Readings (the paper names second-order central differences on the staggered
 grid and gives no stencil):
 
-* x and y are periodic; z is periodic or bounded by no-slip walls (the
-  Neumann pressure axis of the projection). On walls w = 0 on the wall faces
-  (face 0 stored, the top face implicit), and the tangential components have a
-  ghost cell mirrored across the wall with the opposite sign (zero on the wall).
+* Each axis is periodic or bounded by no-slip walls at both ends (the Neumann
+  pressure axis of the projection; the paper's duct and cavity cases of Table 3
+  have walls on x and y). On a wall axis the normal component is 0 on the wall
+  faces (face 0 stored, the top face implicit), and the tangential components
+  have a ghost cell mirrored across the wall with the opposite sign (zero on the
+  wall), one cell width away. x and y are uniform, z may be stretched.
 * Advection in divergence form, ∂(u_i u_j)/∂x_j, with arithmetic averages for
   every interpolation (to cell centres for the normal products, to cell edges
   for the cross products); the derivative of a flux is the difference over the
@@ -29,8 +31,8 @@ grid and gives no stencil):
 * Viscous term: the finite-volume second differences of Eq. 4 applied to each
   component on its own control volume (for w: flux differences over Δz^f
   between z faces, divided by the centre distance).
-* On a wall face AD is not formed: w there stays 0 (the predictor and the
-  projection leave it unchanged).
+* On a wall face AD is not formed: the normal component there stays 0 (the
+  predictor and the projection leave it unchanged).
 
 With these choices the advective flux form conserves momentum exactly, and for a
 discretely divergence-free field it does no work on uniform spacings; on the
@@ -48,32 +50,21 @@ BETA = (0.0, -17.0 / 60.0, -5.0 / 12.0)
 
 
 def _check(bcs):
-    if bcs[0] != "P" or bcs[1] != "P" or bcs[2] not in ("P", "NN"):
-        raise ValueError("the Navier–Stokes substep needs periodic x and y, and a periodic or wall z")
+    if any(b not in ("P", "NN") for b in bcs):
+        raise ValueError("the Navier–Stokes substep needs each axis periodic or bounded by walls (NN)")
 
 
-def _xm(a):
-    return np.roll(a, 1, axis=2)
+class _Axis:
+    """Neighbours of cell-centred and face quantities along one axis of the
+    [n_z][n_y][n_x] arrays, under that axis's rule: periodic (wrap), or no-slip walls
+    at both ends (the normal component is 0 on the wall faces, face 0 stored and the
+    top face implicit; a tangential component has a ghost cell mirrored across the
+    wall with the opposite sign, one cell width away)."""
 
-
-def _xp(a):
-    return np.roll(a, -1, axis=2)
-
-
-def _ym(a):
-    return np.roll(a, 1, axis=1)
-
-
-def _yp(a):
-    return np.roll(a, -1, axis=1)
-
-
-class _Z:
-    """z neighbours of cell-centred and z-face arrays under the z boundary rule."""
-
-    def __init__(self, zf, bcz):
-        self.per = bcz == "P"
-        self.dzf, dzc = metrics(zf)
+    def __init__(self, faces, bc, axis):
+        self.per = bc == "P"
+        self.axis = axis                     # array axis: 2 = x, 1 = y, 0 = z
+        self.dzf, dzc = metrics(faces)
         n = len(self.dzf)
         wrap = 0.5 * (self.dzf[0] + self.dzf[-1])
         # centre distance below cell k (k−1 to k) and above it (k to k+1)
@@ -81,72 +72,90 @@ class _Z:
         self.hup = np.concatenate([dzc, [wrap if self.per else self.dzf[-1]]])
         self.n = n
 
+    def col(self, v):
+        """A per-index vector broadcast along this axis."""
+        shape = [1, 1, 1]
+        shape[self.axis] = -1
+        return np.reshape(v, shape)
+
+    def _sl(self, a, s):
+        idx = [slice(None)] * a.ndim
+        idx[self.axis] = s
+        return a[tuple(idx)]
+
     def cm(self, a):
-        """Cell-centred quantity at k−1 (wall: the mirrored ghost −a_0)."""
+        """Cell-centred quantity at index −1 (wall: the mirrored ghost −a_0)."""
         if self.per:
-            return np.roll(a, 1, axis=0)
-        return np.concatenate([-a[:1], a[:-1]], axis=0)
+            return np.roll(a, 1, axis=self.axis)
+        return np.concatenate([-self._sl(a, slice(0, 1)), self._sl(a, slice(0, -1))], axis=self.axis)
 
     def cp(self, a):
-        """Cell-centred quantity at k+1 (wall: the ghost −a_{n−1})."""
+        """Cell-centred quantity at index +1 (wall: the ghost −a_{n−1})."""
         if self.per:
-            return np.roll(a, -1, axis=0)
-        return np.concatenate([a[1:], -a[-1:]], axis=0)
+            return np.roll(a, -1, axis=self.axis)
+        return np.concatenate([self._sl(a, slice(1, None)), -self._sl(a, slice(-1, None))], axis=self.axis)
 
     def fp(self, w):
-        """z-face quantity at face k+1 (wall: the implicit top face, 0)."""
+        """Face quantity at face +1 (wall: the implicit top face, 0)."""
         if self.per:
-            return np.roll(w, -1, axis=0)
-        return np.concatenate([w[1:], np.zeros_like(w[:1])], axis=0)
+            return np.roll(w, -1, axis=self.axis)
+        return np.concatenate([self._sl(w, slice(1, None)), np.zeros_like(self._sl(w, slice(0, 1)))],
+                              axis=self.axis)
 
     def fm(self, w):
-        """z-face quantity at face k−1 (used for faces k ≥ 1 only on walls)."""
+        """Face quantity at face −1 (used for faces ≥ 1 only on walls)."""
         if self.per:
-            return np.roll(w, 1, axis=0)
-        return np.concatenate([np.zeros_like(w[:1]), w[:-1]], axis=0)
+            return np.roll(w, 1, axis=self.axis)
+        return np.concatenate([np.zeros_like(self._sl(w, slice(0, 1))), self._sl(w, slice(0, -1))],
+                              axis=self.axis)
+
+    def wall_face(self, a):
+        """a with its face 0 set to 0 (the wall face of the normal component)."""
+        if self.per:
+            return a
+        a = a.copy()
+        idx = [slice(None)] * a.ndim
+        idx[self.axis] = 0
+        a[tuple(idx)] = 0.0
+        return a
 
 
 def advection_diffusion(u3, nu, dx, dy, zf, bcs):
-    """AD = −∂(u_i u_j)/∂x_j + ν∇²u_i at the faces of each component (shape (3, n_z, n_y, n_x))."""
+    """AD = −∂(u_i u_j)/∂x_j + ν∇²u_i at the faces of each component (shape (3, n_z, n_y, n_x)).
+
+    Component c sits on the faces normal to its axis; its control volume spans the
+    cell widths along the other two axes and the centre distance across its own
+    face. For each axis d the flux of u_c through the volume's d faces is
+    differenced over the volume's extent along d: advection with arithmetic
+    averages (the normal product u_c² at cell centres when d = c; the cross product
+    on the (c, d) cell edge otherwise, the same product for u_d's equation),
+    diffusion the finite-volume second difference of Eq. 4."""
     _check(bcs)
     zf = np.asarray(zf, dtype=np.float64)
-    Z = _Z(zf, bcs[2])
-    u, v, w = (np.asarray(c, dtype=np.float64) for c in u3)
-    if not Z.per:
-        w = w.copy()
-        w[0] = 0.0
-    dzf = Z.dzf[:, None, None]
-    hdn = Z.hdn[:, None, None]
-    hup = Z.hup[:, None, None]
-
-    # edge products (arithmetic averages of the two neighbours across the edge)
-    uv = 0.5 * (u + _ym(u)) * 0.5 * (v + _xm(v))          # x face i, y face j
-    uw = 0.5 * (u + Z.cm(u)) * 0.5 * (w + _xm(w))         # x face i, z face k
-    vw = 0.5 * (v + Z.cm(v)) * 0.5 * (w + _ym(w))         # y face j, z face k
-
-    # x momentum at x face i (cells j, k)
-    ucc = 0.5 * (u + _xp(u))                               # u at the centre of cell i
-    adv_u = (ucc ** 2 - _xm(ucc ** 2)) / dx + (_yp(uv) - uv) / dy + (Z.fp(uw) - uw) / dzf
-    lap_u = ((_xp(u) - 2 * u + _xm(u)) / dx ** 2 + (_yp(u) - 2 * u + _ym(u)) / dy ** 2
-             + ((Z.cp(u) - u) / hup - (u - Z.cm(u)) / hdn) / dzf)
-
-    # y momentum at y face j
-    vcc = 0.5 * (v + _yp(v))
-    adv_v = (_xp(uv) - uv) / dx + (vcc ** 2 - _ym(vcc ** 2)) / dy + (Z.fp(vw) - vw) / dzf
-    lap_v = ((_xp(v) - 2 * v + _xm(v)) / dx ** 2 + (_yp(v) - 2 * v + _ym(v)) / dy ** 2
-             + ((Z.cp(v) - v) / hup - (v - Z.cm(v)) / hdn) / dzf)
-
-    # z momentum at z face k: control volume between the centres of cells k−1 and k
-    wcc = 0.5 * (w + Z.fp(w))                              # w at the centre of cell k
-    dzf_m = np.roll(Z.dzf, 1)[:, None, None]               # Δz^f_{k−1} (k ≥ 1; periodic wraps)
-    adv_w = (_xp(uw) - uw) / dx + (_yp(vw) - vw) / dy + (wcc ** 2 - np.roll(wcc ** 2, 1, axis=0)) / hdn
-    lap_w = ((_xp(w) - 2 * w + _xm(w)) / dx ** 2 + (_yp(w) - 2 * w + _ym(w)) / dy ** 2
-             + ((Z.fp(w) - w) / dzf - (w - Z.fm(w)) / dzf_m) / hdn)
-
-    ad = np.stack([-adv_u + nu * lap_u, -adv_v + nu * lap_v, -adv_w + nu * lap_w])
-    if not Z.per:
-        ad[2, 0] = 0.0                                     # wall face: w stays 0
-    return ad
+    nx, ny = np.shape(u3)[3], np.shape(u3)[2]
+    axes = {0: _Axis(zf, bcs[2], 0), 1: _Axis(np.arange(ny + 1) * dy, bcs[1], 1),
+            2: _Axis(np.arange(nx + 1) * dx, bcs[0], 2)}
+    comp_axis = (2, 1, 0)                              # u on x faces, v on y faces, w on z faces
+    u = [axes[comp_axis[c]].wall_face(np.asarray(u3[c], dtype=np.float64)) for c in range(3)]
+    ad = []
+    for c in range(3):
+        A = axes[comp_axis[c]]
+        uc = u[c]
+        adv = np.zeros_like(uc)
+        lap = np.zeros_like(uc)
+        for d in range(3):
+            if d == c:
+                cc = 0.5 * (uc + A.fp(uc))                                 # u_c at the cell centre above the face
+                adv += (cc ** 2 - np.roll(cc ** 2, 1, axis=A.axis)) / A.col(A.hdn)
+                dzf_m = np.roll(A.dzf, 1)                                  # width of the cell below the face
+                lap += ((A.fp(uc) - uc) / A.col(A.dzf) - (uc - A.fm(uc)) / A.col(dzf_m)) / A.col(A.hdn)
+            else:
+                B = axes[comp_axis[d]]
+                e = 0.5 * (uc + B.cm(uc)) * 0.5 * (u[d] + A.cm(u[d]))    # the (c, d) edge below, along d
+                adv += (B.fp(e) - e) / B.col(B.dzf)
+                lap += ((B.cp(uc) - uc) / B.col(B.hup) - (uc - B.cm(uc)) / B.col(B.hdn)) / B.col(B.dzf)
+        ad.append(A.wall_face(-adv + nu * lap))         # on a wall face AD is not formed: u_c stays 0
+    return np.stack(ad)
 
 
 def substep(u3, p, ad_prev, k, dt, nu, dx, dy, zf, bcs):

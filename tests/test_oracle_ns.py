@@ -9,6 +9,9 @@
   converges at second order to −∂(w²)/∂z and the viscous part to
   −ν((2π)² + π²)w on the tanh grid (the w equation's own metrics: the centre
   distance across a z face, the cell widths between z faces).
+* Walls on x and y: ν∂²/∂x² of sin(πx) across x walls (and the same along y)
+  converges at second order, and so do the advective and viscous parts of the
+  normal component u = sin(πx) sin(2πz) between x walls.
 * Conservation: the flux form sums to zero over each component's control volumes
   (momentum; with walls, the viscous part of u and v to the two discrete wall
   shear fluxes, and w's flux of w² and of ∂w/∂z to its values at the cells
@@ -79,20 +82,69 @@ def test_wall_diffusion_second_order_on_tanh_grid():
     assert err[1] < 0.3 * err[0] and err[2] < 0.3 * err[1], err
 
 
-def _wall_flux(ns, u3, c, nu, dzf):
-    """What the fluxes of component c leave behind at the walls when the control
-    volumes of a wall-bounded z are summed (the interior faces telescope away).
+def _faces(shape, dx, dy, zf):
+    """Face coordinates per array axis (0 = z, 1 = y, 2 = x)."""
+    nz, ny, nx = shape
+    return {0: np.asarray(zf, dtype=np.float64), 1: np.arange(ny + 1) * dy, 2: np.arange(nx + 1) * dx}
 
-    u, v: the viscous flux through the mirrored ghost, −2u/Δz^f at each wall.
-    w (faces 1 … n−1): the flux of w² at the cell centres next to the walls,
-    with the centre value the mean of the two faces of the cell (wall faces 0),
-    and the viscous flux (w_1 − w_0)/Δz^f_0, (w_n − w_{n−1})/Δz^f_{n−1}.
+
+def _bc(bcs, a):
+    return {2: bcs[0], 1: bcs[1], 0: bcs[2]}[a]
+
+
+def _widths(c, bcs, faces, shape):
+    """Extent of component c's control volumes along each array axis, broadcast: the
+    cell width across the other axes, the centre distance across its own face (the
+    wall face, which carries no equation, gets 0)."""
+    ca = (2, 1, 0)[c]
+    out = {}
+    for a in (0, 1, 2):
+        dzf, dzc = O.metrics(faces[a])
+        per = _bc(bcs, a) == "P"
+        if a == ca:
+            w = np.concatenate([[0.5 * (dzf[0] + dzf[-1]) if per else 0.0], dzc])
+        else:
+            w = dzf
+        sh = [1, 1, 1]
+        sh[a] = -1
+        out[a] = w.reshape(sh)
+    return out
+
+
+def _volume(c, bcs, faces, shape):
+    w = _widths(c, bcs, faces, shape)
+    return w[0] * w[1] * w[2]
+
+
+def _wall_flux(ns, u3, c, nu, bcs, faces):
+    """What the fluxes of component c leave behind at the walls when its control
+    volumes are summed (the interior faces telescope away), weighted by the face
+    areas of the volumes:
+
+    across the walls of another axis d: the viscous flux through the mirrored ghost,
+    −2u/Δ^f at each wall (the advective edge products vanish there, u_d = 0);
+    across the walls of its own axis (faces 1 … n−1): the flux of u_c² at the cell
+    centres next to the walls (the centre value the mean of the two faces of the
+    cell, the wall faces 0) and the viscous flux (u_1 − u_0)/Δ^f_0, (u_n − u_{n−1})/Δ^f_{n−1}.
     """
-    if c < 2:
-        return nu * (-2 * u3[c, -1] / dzf[-1] - 2 * u3[c, 0] / dzf[0]).sum()
-    w = u3[2]
-    top, bot = 0.5 * w[-1], 0.5 * w[1]
-    return (-(top ** 2 - bot ** 2) + nu * (-w[-1] / dzf[-1] - w[1] / dzf[0])).sum()
+    ca = (2, 1, 0)[c]
+    uc = np.asarray(u3[c], dtype=np.float64)
+    w = _widths(c, bcs, faces, uc.shape)
+    total = 0.0
+    for d in (0, 1, 2):
+        if _bc(bcs, d) == "P":
+            continue
+        dzf, _ = O.metrics(faces[d])
+        others = [a for a in (0, 1, 2) if a != d]
+        area = np.take(w[others[0]] * w[others[1]] * np.ones_like(uc), 0, axis=d)
+        if d != ca:
+            top, bot = np.take(uc, -1, axis=d), np.take(uc, 0, axis=d)
+            total += (area * nu * (-2 * top / dzf[-1] - 2 * bot / dzf[0])).sum()
+        else:
+            top, first = np.take(uc, -1, axis=d), np.take(uc, 1, axis=d)
+            flux = -((0.5 * top) ** 2 - (0.5 * first) ** 2) + nu * (-top / dzf[-1] - first / dzf[0])
+            total += (area * flux).sum()
+    return total
 
 
 def _w_errors(ns, nz):
@@ -129,15 +181,16 @@ def test_w_momentum_second_order_on_tanh_grid():
 def _w_balance(ns):
     nz, ny, nx, dx, dy = 12, 6, 8, 0.4, 0.3
     zf = synth.tanh_faces(nz, 1.0, 1.5)
-    dzf, dzc = O.metrics(zf)
+    bcs = ("P", "P", "NN")
     u3 = np.random.default_rng(11).standard_normal((3, nz, ny, nx))
     u3[2, 0] = 0.0
-    hdn = np.concatenate([[dzf[0]], dzc])[:, None, None]
+    faces = _faces((nz, ny, nx), dx, dy, zf)
+    vol = _volume(2, bcs, faces, (nz, ny, nx))
     for nu in (0.0, 0.7):
-        ad = ns.advection_diffusion(u3, nu, dx, dy, zf, ("P", "P", "NN"))
-        s = (hdn[1:] * ad[2, 1:]).sum()
-        wall = _wall_flux(ns, u3, 2, nu, dzf)
-        assert abs(s - wall) < 1e-11 * np.abs(hdn * ad[2]).sum(), (nu, s, wall)
+        ad = ns.advection_diffusion(u3, nu, dx, dy, zf, bcs)
+        s = (vol * ad[2]).sum()
+        wall = _wall_flux(ns, u3, 2, nu, bcs, faces)
+        assert abs(s - wall) < 1e-11 * np.abs(vol * ad[2]).sum(), (nu, s, wall)
 
 
 def test_w_momentum_balance_on_tanh_grid():
@@ -146,33 +199,84 @@ def test_w_momentum_balance_on_tanh_grid():
 
 def _random_div_free(shape, zf, bcs, seed, dx, dy):
     u3 = np.random.default_rng(seed).standard_normal((3,) + shape)
+    if bcs[0] != "P":
+        u3[0, :, :, 0] = 0.0
+    if bcs[1] != "P":
+        u3[1, :, 0, :] = 0.0
     if bcs[2] != "P":
         u3[2, 0] = 0.0
     return AD.project(u3, dx, dy, zf, *bcs)
 
 
-@pytest.mark.parametrize("bcs,stretched", [(("P", "P", "P"), False), (("P", "P", "NN"), True),
-                                           (("P", "P", "NN"), False)])
+CONS = [(("P", "P", "P"), False), (("P", "P", "NN"), True), (("P", "P", "NN"), False),
+        (("NN", "P", "NN"), True), (("NN", "NN", "P"), False), (("P", "NN", "NN"), False),
+        (("NN", "NN", "NN"), True), (("NN", "NN", "NN"), False)]
+
+
+@pytest.mark.parametrize("bcs,stretched", CONS, ids=["-".join(b) + ("-tanh" if st else "") for b, st in CONS])
 def test_momentum_and_energy_conservation(bcs, stretched):
     nz, ny, nx, dx, dy = 10, 8, 12, 0.4, 0.3
     zf = synth.tanh_faces(nz, 1.0, 1.5) if stretched else O.uniform_faces(nz, 0.1)
     u3 = _random_div_free((nz, ny, nx), zf, bcs, 5, dx, dy)
-    dzf, dzc = O.metrics(zf)
-    hdn = np.concatenate([[0.5 * (dzf[0] + dzf[-1]) if bcs[2] == "P" else dzf[0]], dzc])
-    vol = [dzf[:, None, None], dzf[:, None, None], hdn[:, None, None]]
-    if bcs[2] != "P":
-        vol[2] = vol[2].copy()
-        vol[2][0] = 0.0                      # the wall face carries no momentum
+    faces = _faces((nz, ny, nx), dx, dy, zf)
+    vol = [_volume(c, bcs, faces, (nz, ny, nx)) for c in range(3)]
     for nu in (0.0, 0.7):
         ad = NS.advection_diffusion(u3, nu, dx, dy, zf, bcs)
         for c in (0, 1, 2):                  # periodic directions: momentum conserved,
             s = (vol[c] * ad[c]).sum()       # but for the fluxes through the walls
-            wall = _wall_flux(NS, u3, c, nu, dzf) if bcs[2] != "P" else 0.0
+            wall = _wall_flux(NS, u3, c, nu, bcs, faces)
             assert abs(s - wall) < 1e-11 * np.abs(vol[c] * ad[c]).sum(), (c, nu, s, wall)
         if nu == 0.0 and not stretched:  # exact on uniform spacings only (arithmetic averages)
             work = sum((vol[c] * u3[c] * ad[c]).sum() for c in range(3))
             scale = sum(np.abs(vol[c] * u3[c] * ad[c]).sum() for c in range(3))
             assert abs(work) < 1e-11 * scale, (work, scale)
+
+
+def test_wall_diffusion_along_x_and_y():
+    """ν∂²v/∂x² of v = sin(πx) between walls on x (tangential to them: the mirrored
+    ghost is exact), and ν∂²u/∂y² of u = sin(πy) between walls on y, converge at
+    second order."""
+    err = {"x": [], "y": []}
+    for n in (16, 32, 64):
+        h = 1.0 / n
+        xc = (np.arange(n) + 0.5) * h
+        zf = O.uniform_faces(4, 0.25)
+        v = np.broadcast_to(np.sin(np.pi * xc)[None, None, :], (4, 4, n)).copy()
+        u3 = np.stack([np.zeros_like(v), v, np.zeros_like(v)])
+        ad = NS.advection_diffusion(u3, 1.0, h, 0.25, zf, ("NN", "P", "P"))
+        err["x"].append(np.abs(ad[1, 0, 0] + np.pi ** 2 * np.sin(np.pi * xc)).max())
+        u = np.broadcast_to(np.sin(np.pi * xc)[None, :, None], (4, n, 4)).copy()
+        u3 = np.stack([u, np.zeros_like(u), np.zeros_like(u)])
+        ad = NS.advection_diffusion(u3, 1.0, 0.25, h, zf, ("P", "NN", "P"))
+        err["y"].append(np.abs(ad[0, 0, :, 0] + np.pi ** 2 * np.sin(np.pi * xc)).max())
+    for e in err.values():
+        assert e[1] < 0.3 * e[0] and e[2] < 0.3 * e[1], err
+
+
+def _u_errors(ns, n):
+    """AD_u's advective and viscous parts for u = sin(πx)·sin(2πz) on x faces between
+    walls on x (zero on both), v = w = 0, periodic y and z: −∂(u²)/∂x and
+    −ν(π² + 4π²)u."""
+    h = 1.0 / n
+    xf = np.arange(n) * h
+    zc = (np.arange(n) + 0.5) * h
+    Z, _, X = np.meshgrid(zc, np.arange(2), xf, indexing="ij")
+    u = np.sin(np.pi * X) * np.sin(2 * np.pi * Z)
+    u3 = np.stack([u, np.zeros_like(u), np.zeros_like(u)])
+    zf = O.uniform_faces(n, h)
+    bcs = ("NN", "P", "P")
+    ad0 = ns.advection_diffusion(u3, 0.0, h, 0.5, zf, bcs)[0]
+    ad1 = ns.advection_diffusion(u3, 1.0, h, 0.5, zf, bcs)[0]
+    adv = -np.pi * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Z) ** 2
+    lap = -(np.pi ** 2 + 4 * np.pi ** 2) * u
+    inner = (slice(None), slice(None), slice(1, None))   # face 0 is the wall
+    return np.abs(ad0 - adv)[inner].max(), np.abs((ad1 - ad0) - lap)[inner].max()
+
+
+def test_u_momentum_between_x_walls_second_order():
+    e = np.array([_u_errors(NS, n) for n in (16, 32, 64)])
+    for part in (0, 1):
+        assert e[1, part] < 0.3 * e[0, part] and e[2, part] < 0.3 * e[1, part], e
 
 
 def _tg2(n, t, nu):
@@ -218,10 +322,10 @@ def _mutant(old, new):
 
 
 W_SLIPS = [
-    # viscous w flux below face k divided by Δz^f_k instead of Δz^f_{k−1}
-    ("- (w - Z.fm(w)) / dzf_m) / hdn)", "- (w - Z.fm(w)) / dzf) / hdn)"),
-    # flux difference of w² taken over the cell width instead of the centre distance
-    ("np.roll(wcc ** 2, 1, axis=0)) / hdn", "np.roll(wcc ** 2, 1, axis=0)) / dzf"),
+    # viscous flux below a face divided by the width of the cell above it, not below it
+    ("(uc - A.fm(uc)) / A.col(dzf_m)", "(uc - A.fm(uc)) / A.col(A.dzf)"),
+    # flux difference of u_c² taken over the cell width instead of the centre distance
+    ("np.roll(cc ** 2, 1, axis=A.axis)) / A.col(A.hdn)", "np.roll(cc ** 2, 1, axis=A.axis)) / A.col(A.dzf)"),
 ]
 
 
@@ -246,21 +350,25 @@ def test_unmutated_copy_passes_the_w_pins():
 
 
 def test_planted_mistakes_are_caught(monkeypatch):
-    """A wall ghost with the wrong sign fails the wall-diffusion pin; RK3 without its
-    β_k terms fails the Taylor–Green pin."""
-    orig_cm = NS._Z.cm
+    """A wall ghost with the wrong sign fails the wall-diffusion pins (z, and x/y);
+    RK3 without its β_k terms fails the Taylor–Green pin."""
+    orig_cm = NS._Axis.cm
 
     def cm_plus(self, a):
         out = orig_cm(self, a)
         if not self.per:
             out = out.copy()
-            out[0] = a[0]
+            idx = [slice(None)] * out.ndim
+            idx[self.axis] = 0
+            out[tuple(idx)] = a[tuple(idx)]
         return out
 
-    monkeypatch.setattr(NS._Z, "cm", cm_plus)
+    monkeypatch.setattr(NS._Axis, "cm", cm_plus)
     with pytest.raises(AssertionError):
         test_wall_diffusion_second_order_on_tanh_grid()
-    monkeypatch.setattr(NS._Z, "cm", orig_cm)
+    with pytest.raises(AssertionError):
+        test_wall_diffusion_along_x_and_y()
+    monkeypatch.setattr(NS._Axis, "cm", orig_cm)
     monkeypatch.setattr(NS, "BETA", (0.0, 0.0, 0.0))
     with pytest.raises(AssertionError):
         test_rk3_taylor_green_decay_and_divergence()
