@@ -217,9 +217,10 @@ const char* ps_last_error(const ps_plan* plan);
  * on the staggered layout of the projection operators above. AD is second-order
  * central: advection in divergence form with arithmetic averages, the viscous term
  * the finite-volume second differences of Eq. 4, each on its component's control
- * volume. The plan must be a Poisson plan (α = 0) with periodic x and y and a
- * periodic or NEUMANN_NEUMANN z; the latter means no-slip walls: w = 0 on the wall
- * faces, tangential ghosts mirrored with the opposite sign.
+ * volume. The plan must be a Poisson plan (α = 0) with each axis PERIODIC or
+ * NEUMANN_NEUMANN; the latter means no-slip walls on that axis (the duct and cavity
+ * cases of Table 3 have them on x and y): the normal component is 0 on the wall
+ * faces, tangential ghosts are mirrored with the opposite sign.
  *   u      3·N stacked faces [u | v | w]: u^k in, u^{k+1} out (divergence-free).
  *   ustar  3·N scratch (u*), distinct from u.
  *   ad     3·N: AD^{k−1} in (not read when k = 1), AD^k out (in place).

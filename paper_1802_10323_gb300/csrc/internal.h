@@ -164,7 +164,7 @@ cudaError_t launch_projection(int op, const ProjArgs<T>& a, const void* x0, cons
 template <class T>
 struct NsArgs {
   int nx, ny, nz;
-  int per_z;                // z periodic (else no-slip walls)
+  int per_x, per_y, per_z;  // axis periodic (else no-slip walls at both ends)
   T idx, idy, idx2, idy2;   // 1/Δx, 1/Δy, 1/Δx², 1/Δy²
   T qx, qy;                 // ¼/Δx, ¼/Δy (flux differences of products of two sums)
   const T* idzf;

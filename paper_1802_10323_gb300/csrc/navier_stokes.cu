@@ -14,14 +14,19 @@
 // the normal products at cell centres, the cross products on cell edges — and the
 // flux differences taken over each component's control volume (Δ across a cell, the
 // centre distance across a z face); the viscous term is the finite-volume second
-// difference of Eq. 4 on the same control volumes. x and y are periodic; z is
-// periodic, or bounded by no-slip walls: w = 0 on the wall faces (face 0 stored, the
-// top face implicit) and the tangential components see a ghost cell mirrored across
-// the wall with the opposite sign. On a wall face AD is not formed and w stays 0.
+// difference of Eq. 4 on the same control volumes. Each axis is periodic, or bounded
+// by no-slip walls (the duct and cavity cases of Table 3 have walls on x and y): the
+// normal component is 0 on the wall faces (face 0 stored, the top face implicit) and
+// the tangential components see a ghost cell mirrored across the wall with the
+// opposite sign, one cell width away. On a wall face AD is not formed and the normal
+// component stays 0. x and y are uniform, z may be stretched.
 //
 // One thread per cell forms the three face values of that cell (x face i, y face j,
 // z face k); x is the fastest index, so every neighbour load of a warp is a
-// contiguous row segment, and the 3×3×3 neighbourhoods overlap in L1/L2.
+// contiguous row segment, and the 3×3×3 neighbourhoods overlap in L1/L2. Every
+// neighbour goes through one loader that applies the axis rules (wrap, mirrored
+// ghost, or the zero wall face), so the flux formulas below are those of the
+// periodic box.
 #include "internal.h"
 
 namespace ps {
@@ -41,58 +46,79 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
     const int i = (int)(g % nx);
     const size_t t = g / nx;
     const int j = (int)(t % ny), k = (int)(t / ny);
-    // periodic x and y neighbours (offsets from g)
-    const long dxm = (i > 0) ? -1 : (long)(nx - 1), dxp = (i + 1 < nx) ? 1 : -(long)(nx - 1);
-    const long dym = (j > 0) ? -(long)sy : (long)((ny - 1) * sy), dyp = (j + 1 < ny) ? (long)sy : -(long)((ny - 1) * sy);
-    // z neighbours: the plane below / above, whether they exist (walls) and the wrap
-    const bool per = a.per_z != 0;
-    const bool has_dn = k > 0 || per, has_up = k + 1 < nz || per;
-    const long dzm = (k > 0) ? -(long)sz : (long)((nz - 1) * sz);
-    const long dzp = (k + 1 < nz) ? (long)sz : -(long)((nz - 1) * sz);
+    // per axis (0 = x, 1 = y, 2 = z): periodic flag, index, length and stride
+    const bool per[3] = {a.per_x != 0, a.per_y != 0, a.per_z != 0};
+    const int idx3[3] = {i, j, k}, len[3] = {nx, ny, nz};
+    const long str[3] = {1, (long)sy, (long)sz};
+    // Value of component C (normal to axis ca) at the neighbour (ox, oy, oz) ∈ {−1, 0, 1}³.
+    // Along a periodic axis the index wraps; along a wall axis an index beyond either
+    // end is the mirrored ghost (−1 times the boundary cell) for a tangential component
+    // and 0 for the normal one (the implicit top wall face), and the normal component's
+    // own wall face 0 is 0.
+    auto ld = [&](const T* __restrict__ C, int ca, int ox, int oy, int oz) -> T {
+      const int o[3] = {ox, oy, oz};
+      long off = 0;
+      T sgn = (T)1;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const int q = idx3[ax] + o[ax];
+        if (q < 0 || q >= len[ax]) {
+          if (per[ax]) {
+            off += (long)o[ax] * str[ax] + (q < 0 ? (long)len[ax] * str[ax] : -(long)len[ax] * str[ax]);
+          } else {
+            if (ax == ca) return (T)0;
+            sgn = -sgn;  // the ghost of the boundary cell (offset dropped)
+          }
+        } else {
+          if (ax == ca && q == 0 && !per[ax]) return (T)0;
+          off += (long)o[ax] * str[ax];
+        }
+      }
+      return sgn * C[(long)g + off];
+    };
+    const bool wall_u = !per[0] && i == 0, wall_v = !per[1] && j == 0, wall_w = !per[2] && k == 0;
     const T idzf = a.idzf[k];
     // 1/(centre distance) below and above cell k; walls: the ghost sits one Δz^f away
-    const T ihdn = (k > 0) ? a.idzc[k] : (per ? a.idzc[0] : a.idzf[0]);
-    const T ihup = (k + 1 < nz) ? a.idzc[k + 1] : (per ? a.idzc[0] : a.idzf[nz - 1]);
-
-    // loads (W on the wall face 0 is taken as 0; cell-centred ghosts are −value)
-    auto Wv = [&](long off, int kk) -> T { return (!per && kk == 0) ? (T)0 : W[g + off]; };
-    const T uc = U[g], vc = V[g], wc = Wv(0, k);
+    const T ihdn = (k > 0) ? a.idzc[k] : (per[2] ? a.idzc[0] : a.idzf[0]);
+    const T ihup = (k + 1 < nz) ? a.idzc[k + 1] : (per[2] ? a.idzc[0] : a.idzf[nz - 1]);
+    const T idzf_m = a.idzf[k > 0 ? k - 1 : nz - 1];
+    const T uc = ld(U, 0, 0, 0, 0), vc = ld(V, 1, 0, 0, 0), wc = ld(W, 2, 0, 0, 0);
 
     // Every flux below is a product of two sums of neighbours (an average each): the two
     // factors ½ go into one factor ¼ on the flux difference (q* = ¼/Δ), and the normal
     // term d(ū²) = ((a + b)² − (c + a)²)/4 is formed as (b − c)(b + 2a + c)/4.
     // ---------------- x momentum at x face i ----------------
-    T adu;
-    {
-      const T uxp = U[g + dxp], uxm = U[g + dxm];
-      const T uyp = U[g + dyp], uym = U[g + dym];
-      const T uzp = has_up ? U[g + dzp] : -uc, uzm = has_dn ? U[g + dzm] : -uc;
+    T adu = (T)0;
+    if (!wall_u) {
+      const T uxp = ld(U, 0, 1, 0, 0), uxm = ld(U, 0, -1, 0, 0);
+      const T uyp = ld(U, 0, 0, 1, 0), uym = ld(U, 0, 0, -1, 0);
+      const T uzp = ld(U, 0, 0, 0, 1), uzm = ld(U, 0, 0, 0, -1);
       const T duu = (uxp - uxm) * (uxp + 2 * uc + uxm) * a.qx;
       // uv on the y faces j and j+1 of this x face
-      const T uv0 = (uc + uym) * (vc + V[g + dxm]);
-      const T uv1 = (uyp + uc) * (V[g + dyp] + V[g + dyp + dxm]);
+      const T uv0 = (uc + uym) * (vc + ld(V, 1, -1, 0, 0));
+      const T uv1 = (uyp + uc) * (ld(V, 1, 0, 1, 0) + ld(V, 1, -1, 1, 0));
       const T duv = (uv1 - uv0) * a.qy;
-      // uw on the z faces k and k+1 of this x face (k = 0 on a wall: w = 0)
-      const T uw0 = has_dn ? (uc + uzm) * (wc + Wv(dxm, k)) : (T)0;
-      const T uw1 = has_up ? (uzp + uc) * (Wv(dzp, k + 1 < nz ? k + 1 : 0) + Wv(dzp + dxm, k + 1 < nz ? k + 1 : 0)) : (T)0;
+      // uw on the z faces k and k+1 of this x face
+      const T uw0 = (uc + uzm) * (wc + ld(W, 2, -1, 0, 0));
+      const T uw1 = (uzp + uc) * (ld(W, 2, 0, 0, 1) + ld(W, 2, -1, 0, 1));
       const T duw = (uw1 - uw0) * ((T)0.25 * idzf);
       const T lap = (uxp - 2 * uc + uxm) * a.idx2 + (uyp - 2 * uc + uym) * a.idy2 +
                     ((uzp - uc) * ihup - (uc - uzm) * ihdn) * idzf;
       adu = a.nu * lap - (duu + duv + duw);
     }
     // ---------------- y momentum at y face j ----------------
-    T adv;
-    {
-      const T vxp = V[g + dxp], vxm = V[g + dxm];
-      const T vyp = V[g + dyp], vym = V[g + dym];
-      const T vzp = has_up ? V[g + dzp] : -vc, vzm = has_dn ? V[g + dzm] : -vc;
+    T adv = (T)0;
+    if (!wall_v) {
+      const T vxp = ld(V, 1, 1, 0, 0), vxm = ld(V, 1, -1, 0, 0);
+      const T vyp = ld(V, 1, 0, 1, 0), vym = ld(V, 1, 0, -1, 0);
+      const T vzp = ld(V, 1, 0, 0, 1), vzm = ld(V, 1, 0, 0, -1);
       const T dvv = (vyp - vym) * (vyp + 2 * vc + vym) * a.qy;
       // uv on the x faces i and i+1 of this y face
-      const T uv0 = (uc + U[g + dym]) * (vc + vxm);
-      const T uv1 = (U[g + dxp] + U[g + dxp + dym]) * (vxp + vc);
+      const T uv0 = (uc + ld(U, 0, 0, -1, 0)) * (vc + vxm);
+      const T uv1 = (ld(U, 0, 1, 0, 0) + ld(U, 0, 1, -1, 0)) * (vxp + vc);
       const T duv = (uv1 - uv0) * a.qx;
-      const T vw0 = has_dn ? (vc + vzm) * (wc + Wv(dym, k)) : (T)0;
-      const T vw1 = has_up ? (vzp + vc) * (Wv(dzp, k + 1 < nz ? k + 1 : 0) + Wv(dzp + dym, k + 1 < nz ? k + 1 : 0)) : (T)0;
+      const T vw0 = (vc + vzm) * (wc + ld(W, 2, 0, -1, 0));
+      const T vw1 = (vzp + vc) * (ld(W, 2, 0, 0, 1) + ld(W, 2, 0, -1, 1));
       const T dvw = (vw1 - vw0) * ((T)0.25 * idzf);
       const T lap = (vxp - 2 * vc + vxm) * a.idx2 + (vyp - 2 * vc + vym) * a.idy2 +
                     ((vzp - vc) * ihup - (vc - vzm) * ihdn) * idzf;
@@ -100,21 +126,18 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
     }
     // ---------------- z momentum at z face k ----------------
     T adw = (T)0;
-    if (has_dn) {  // not on a wall face
-      const int kup = k + 1 < nz ? k + 1 : 0;
-      const T wzp = has_up ? Wv(dzp, kup) : (T)0;
-      const int kdn = k > 0 ? k - 1 : nz - 1;
-      const T wzm = Wv(dzm, kdn);
-      const T wxp = Wv(dxp, k), wxm = Wv(dxm, k), wyp = Wv(dyp, k), wym = Wv(dym, k);
+    if (!wall_w) {
+      const T wzp = ld(W, 2, 0, 0, 1), wzm = ld(W, 2, 0, 0, -1);
+      const T wxp = ld(W, 2, 1, 0, 0), wxm = ld(W, 2, -1, 0, 0);
+      const T wyp = ld(W, 2, 0, 1, 0), wym = ld(W, 2, 0, -1, 0);
       const T dww = (wzp - wzm) * (wzp + 2 * wc + wzm) * ((T)0.25 * ihdn);
       // uw on the x faces i and i+1 of this z face (u averaged over cells k−1 and k)
-      const T uw0 = (uc + U[g + dzm]) * (wc + wxm);
-      const T uw1 = (U[g + dxp] + U[g + dxp + dzm]) * (wxp + wc);
+      const T uw0 = (uc + ld(U, 0, 0, 0, -1)) * (wc + wxm);
+      const T uw1 = (ld(U, 0, 1, 0, 0) + ld(U, 0, 1, 0, -1)) * (wxp + wc);
       const T duw = (uw1 - uw0) * a.qx;
-      const T vw0 = (vc + V[g + dzm]) * (wc + wym);
-      const T vw1 = (V[g + dyp] + V[g + dyp + dzm]) * (wyp + wc);
+      const T vw0 = (vc + ld(V, 1, 0, 0, -1)) * (wc + wym);
+      const T vw1 = (ld(V, 1, 0, 1, 0) + ld(V, 1, 0, 1, -1)) * (wyp + wc);
       const T dvw = (vw1 - vw0) * a.qy;
-      const T idzf_m = a.idzf[kdn];
       const T lap = (wxp - 2 * wc + wxm) * a.idx2 + (wyp - 2 * wc + wym) * a.idy2 +
                     ((wzp - wc) * idzf - (wc - wzm) * idzf_m) * ihdn;
       adw = a.nu * lap - (duw + dvw + dww);
@@ -122,15 +145,15 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
 
     // ---------------- predictor (2a) ----------------
     const T pc = p[g];
-    const T gpx = (pc - p[g + dxm]) * a.idx;
-    const T gpy = (pc - p[g + dym]) * a.idy;
-    const T gpz = has_dn ? (pc - p[g + dzm]) * ihdn : (T)0;
+    const T gpx = wall_u ? (T)0 : (pc - p[g + (i > 0 ? -1 : nx - 1)]) * a.idx;
+    const T gpy = wall_v ? (T)0 : (pc - p[g + (j > 0 ? -(long)sy : (long)((ny - 1) * sy))]) * a.idy;
+    const T gpz = wall_w ? (T)0 : (pc - p[g + (k > 0 ? -(long)sz : (long)((nz - 1) * sz))]) * ihdn;
     const T bu = a.beta != (T)0 ? ad_prev[g] : (T)0;
     const T bv = a.beta != (T)0 ? ad_prev[g + N] : (T)0;
     const T bw = a.beta != (T)0 ? ad_prev[g + 2 * N] : (T)0;
-    ustar[g] = uc + a.dt * (a.alpha * adu + a.beta * bu - a.gamma * gpx);
-    ustar[g + N] = vc + a.dt * (a.alpha * adv + a.beta * bv - a.gamma * gpy);
-    ustar[g + 2 * N] = has_dn ? wc + a.dt * (a.alpha * adw + a.beta * bw - a.gamma * gpz) : W[g];
+    ustar[g] = wall_u ? U[g] : uc + a.dt * (a.alpha * adu + a.beta * bu - a.gamma * gpx);
+    ustar[g + N] = wall_v ? V[g] : vc + a.dt * (a.alpha * adv + a.beta * bv - a.gamma * gpy);
+    ustar[g + 2 * N] = wall_w ? W[g] : wc + a.dt * (a.alpha * adw + a.beta * bw - a.gamma * gpz);
     ad_out[g] = adu;
     ad_out[g + N] = adv;
     ad_out[g + 2 * N] = adw;

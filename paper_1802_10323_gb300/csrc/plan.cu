@@ -1184,9 +1184,9 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
   if (k < 1 || k > 3) return fail(plan, PS_INVALID_ARG, "the RK3 substep k must be 1, 2 or 3");
   if (!(dt > 0.0) || !std::isfinite(dt) || !(nu >= 0.0) || !std::isfinite(nu))
     return fail(plan, PS_INVALID_ARG, "dt must be > 0 and nu >= 0 (finite)");
-  if (plan->bcx != PS_BC_PERIODIC || plan->bcy != PS_BC_PERIODIC ||
-      (plan->bcz != PS_BC_PERIODIC && plan->bcz != PS_BC_NEUMANN_NEUMANN))
-    return fail(plan, PS_INVALID_ARG, "the substep needs periodic x and y, and a periodic or Neumann (wall) z");
+  auto pw = [](int b) { return b == PS_BC_PERIODIC || b == PS_BC_NEUMANN_NEUMANN; };
+  if (!pw(plan->bcx) || !pw(plan->bcy) || !pw(plan->bcz))
+    return fail(plan, PS_INVALID_ARG, "the substep needs each axis periodic or Neumann (no-slip walls)");
   if (plan->alpha != 0.0) return fail(plan, PS_INVALID_ARG, "the substep needs a Poisson plan (alpha = 0)");
   static const double kAlpha[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
   static const double kBeta[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
@@ -1199,6 +1199,8 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
     a.nx = plan->nx;
     a.ny = plan->ny;
     a.nz = plan->nz;
+    a.per_x = plan->bcx == PS_BC_PERIODIC;
+    a.per_y = plan->bcy == PS_BC_PERIODIC;
     a.per_z = plan->bcz == PS_BC_PERIODIC;
     a.idx = (T)(1.0 / plan->dx);
     a.idy = (T)(1.0 / plan->dy);

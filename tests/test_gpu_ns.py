@@ -1,8 +1,8 @@
 """GPU parity of the RK3 fractional step around the solve (§2, Eqs. 2a–2d):
 ps_ns_substep against the FP64 oracle (oracle/navier_stokes.py), substep by
-substep — u^{k+1}, p^{k+1/2}, Φ and AD^k — on periodic and wall-bounded
-(stretched) grids, for FP64, refined and FP32 plans; the result is discretely
-divergence-free.
+substep — u^{k+1}, p^{k+1/2}, Φ and AD^k — on periodic and wall-bounded grids
+(walls on z, stretched or not; on y and z as in a duct; on every axis; on x only),
+for FP64, refined and FP32 plans; the result is discretely divergence-free.
 """
 
 import numpy as np
@@ -22,6 +22,10 @@ def _setup(shape, bcs, stretched, seed):
     zf = synth.tanh_faces(nz, 1.0, 1.5) if stretched else O.uniform_faces(nz, 0.6 / nz)
     rng = np.random.default_rng(seed)
     u3 = rng.standard_normal((3,) + shape)
+    if bcs[0] != "P":
+        u3[0, :, :, 0] = 0.0
+    if bcs[1] != "P":
+        u3[1, :, 0, :] = 0.0
     if bcs[2] != "P":
         u3[2, 0] = 0.0
     u3 = AD.project(u3, dx, dy, zf, *bcs)
@@ -29,8 +33,11 @@ def _setup(shape, bcs, stretched, seed):
     return u3, p, dx, dy, zf
 
 
+# periodic box, channel (walls on z), duct (walls on y and z), cavity-like box
+# (walls on every axis), walls on x only
 CASES = [((8, 12, 16), ("P", "P", "P"), False), ((10, 8, 12), ("P", "P", "NN"), True),
-         ((12, 16, 8), ("P", "P", "NN"), False)]
+         ((12, 16, 8), ("P", "P", "NN"), False), ((10, 12, 16), ("P", "NN", "NN"), True),
+         ((8, 12, 12), ("NN", "NN", "NN"), True), ((6, 8, 18), ("NN", "P", "P"), False)]
 
 
 # u and AD at the path's precision; p and Φ come straight out of the solve, whose solution
@@ -38,7 +45,7 @@ CASES = [((8, 12, 16), ("P", "P", "P"), False), ((10, 8, 12), ("P", "P", "NN"), 
 # condition number (~10^4 at these sizes), while u only sees the small correction G·Φ'
 @pytest.mark.parametrize("precision,tol,tol_p", [("fp64", 1e-12, 1e-12), ("fp32_refine", 1e-9, 2e-8),
                                                  ("fp32", 2e-5, 3e-4)])
-@pytest.mark.parametrize("shape,bcs,stretched", CASES, ids=["x".join(map(str, c[0])) + "-" + c[1][2] +
+@pytest.mark.parametrize("shape,bcs,stretched", CASES, ids=["x".join(map(str, c[0])) + "-" + "-".join(c[1]) +
                                                              ("-tanh" if c[2] else "") for c in CASES])
 def test_rk3_substeps_match_oracle(lib, shape, bcs, stretched, precision, tol, tol_p):
     import torch
