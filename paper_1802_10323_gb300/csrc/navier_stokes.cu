@@ -26,14 +26,49 @@
 // contiguous row segment, and the 3×3×3 neighbourhoods overlap in L1/L2. Every
 // neighbour goes through one loader that applies the axis rules (wrap, mirrored
 // ghost, or the zero wall face), so the flux formulas below are those of the
-// periodic box.
+// periodic box; which axes are periodic is a template argument, so the periodic box
+// compiles to plain wrapped offsets.
 #include "internal.h"
 
 namespace ps {
 
 namespace {
 
-template <class T>
+// One axis of the loader: the neighbour offsets of this cell along the axis (wrapped
+// when periodic; 0 past a wall, where the mirrored ghost of the boundary cell is read)
+// and whether the cell touches the low or the high wall.
+struct NbAxis {
+  long om, op;
+  int idx, n;
+};
+
+template <bool PER>
+__device__ __forceinline__ NbAxis nb_axis(int idx, int n, long str) {
+  NbAxis a;
+  a.idx = idx;
+  a.n = n;
+  if (PER) {
+    a.om = idx > 0 ? -str : (long)(n - 1) * str;
+    a.op = idx + 1 < n ? str : -(long)(n - 1) * str;
+  } else {
+    a.om = idx > 0 ? -str : 0;
+    a.op = idx + 1 < n ? str : 0;
+  }
+  return a;
+}
+
+// Contribution of offset o ∈ {−1, 0, 1} along one wall axis: returns false when the
+// value is 0 (the normal component ca == this axis on a wall face, stored or implicit)
+// and flips s for the ghost of a tangential component.
+template <bool PER>
+__device__ __forceinline__ bool nb_rule(const NbAxis& a, bool normal, int o, int& s) {
+  if (PER) return true;
+  if (normal) return !(o < 0 ? a.idx <= 1 : (o == 0 ? a.idx == 0 : a.idx + 1 >= a.n));
+  if ((o < 0 && a.idx == 0) || (o > 0 && a.idx + 1 == a.n)) s = -s;
+  return true;
+}
+
+template <class T, bool PX, bool PY, bool PZ>
 __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* __restrict__ u3,
                                                          const T* __restrict__ p, const T* ad_prev,
                                                          T* __restrict__ ustar, T* ad_out) {
@@ -46,41 +81,28 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
     const int i = (int)(g % nx);
     const size_t t = g / nx;
     const int j = (int)(t % ny), k = (int)(t / ny);
-    // per axis (0 = x, 1 = y, 2 = z): periodic flag, index, length and stride
-    const bool per[3] = {a.per_x != 0, a.per_y != 0, a.per_z != 0};
-    const int idx3[3] = {i, j, k}, len[3] = {nx, ny, nz};
-    const long str[3] = {1, (long)sy, (long)sz};
+    const NbAxis ax_x = nb_axis<PX>(i, nx, 1), ax_y = nb_axis<PY>(j, ny, (long)sy),
+                 ax_z = nb_axis<PZ>(k, nz, (long)sz);
     // Value of component C (normal to axis ca) at the neighbour (ox, oy, oz) ∈ {−1, 0, 1}³.
     // Along a periodic axis the index wraps; along a wall axis an index beyond either
     // end is the mirrored ghost (−1 times the boundary cell) for a tangential component
     // and 0 for the normal one (the implicit top wall face), and the normal component's
     // own wall face 0 is 0.
     auto ld = [&](const T* __restrict__ C, int ca, int ox, int oy, int oz) -> T {
-      const int o[3] = {ox, oy, oz};
-      long off = 0;
-      T sgn = (T)1;
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        const int q = idx3[ax] + o[ax];
-        if (q < 0 || q >= len[ax]) {
-          if (per[ax]) {
-            off += (long)o[ax] * str[ax] + (q < 0 ? (long)len[ax] * str[ax] : -(long)len[ax] * str[ax]);
-          } else {
-            if (ax == ca) return (T)0;
-            sgn = -sgn;  // the ghost of the boundary cell (offset dropped)
-          }
-        } else {
-          if (ax == ca && q == 0 && !per[ax]) return (T)0;
-          off += (long)o[ax] * str[ax];
-        }
-      }
-      return sgn * C[(long)g + off];
+      const long off = (ox < 0 ? ax_x.om : ox > 0 ? ax_x.op : 0) + (oy < 0 ? ax_y.om : oy > 0 ? ax_y.op : 0) +
+                       (oz < 0 ? ax_z.om : oz > 0 ? ax_z.op : 0);
+      int s = 1;
+      const bool keep = nb_rule<PX>(ax_x, ca == 0, ox, s) && nb_rule<PY>(ax_y, ca == 1, oy, s) &&
+                        nb_rule<PZ>(ax_z, ca == 2, oz, s);
+      if (!keep) return (T)0;
+      const T v = C[(long)g + off];
+      return s < 0 ? -v : v;
     };
-    const bool wall_u = !per[0] && i == 0, wall_v = !per[1] && j == 0, wall_w = !per[2] && k == 0;
+    const bool wall_u = !PX && i == 0, wall_v = !PY && j == 0, wall_w = !PZ && k == 0;
     const T idzf = a.idzf[k];
     // 1/(centre distance) below and above cell k; walls: the ghost sits one Δz^f away
-    const T ihdn = (k > 0) ? a.idzc[k] : (per[2] ? a.idzc[0] : a.idzf[0]);
-    const T ihup = (k + 1 < nz) ? a.idzc[k + 1] : (per[2] ? a.idzc[0] : a.idzf[nz - 1]);
+    const T ihdn = (k > 0) ? a.idzc[k] : (PZ ? a.idzc[0] : a.idzf[0]);
+    const T ihup = (k + 1 < nz) ? a.idzc[k + 1] : (PZ ? a.idzc[0] : a.idzf[nz - 1]);
     const T idzf_m = a.idzf[k > 0 ? k - 1 : nz - 1];
     const T uc = ld(U, 0, 0, 0, 0), vc = ld(V, 1, 0, 0, 0), wc = ld(W, 2, 0, 0, 0);
 
@@ -185,9 +207,21 @@ template <class T>
 cudaError_t launch_ns_predict(const NsArgs<T>& a, const void* u3, const void* p, const void* ad_prev,
                               void* ustar, void* ad_out, cudaStream_t st) {
   const size_t N = (size_t)a.nx * a.ny * a.nz;
-  ns_predict_kernel<T><<<grid_for(N), 256, 0, st>>>(a, static_cast<const T*>(u3), static_cast<const T*>(p),
-                                                    static_cast<const T*>(ad_prev), static_cast<T*>(ustar),
-                                                    static_cast<T*>(ad_out));
+  const int sel = (a.per_x ? 1 : 0) | (a.per_y ? 2 : 0) | (a.per_z ? 4 : 0);
+  auto go = [&](auto k) {
+    k<<<grid_for(N), 256, 0, st>>>(a, static_cast<const T*>(u3), static_cast<const T*>(p),
+                                   static_cast<const T*>(ad_prev), static_cast<T*>(ustar), static_cast<T*>(ad_out));
+  };
+  switch (sel) {
+    case 0: go(ns_predict_kernel<T, false, false, false>); break;
+    case 1: go(ns_predict_kernel<T, true, false, false>); break;
+    case 2: go(ns_predict_kernel<T, false, true, false>); break;
+    case 3: go(ns_predict_kernel<T, true, true, false>); break;
+    case 4: go(ns_predict_kernel<T, false, false, true>); break;
+    case 5: go(ns_predict_kernel<T, true, false, true>); break;
+    case 6: go(ns_predict_kernel<T, false, true, true>); break;
+    default: go(ns_predict_kernel<T, true, true, true>); break;
+  }
   return cudaGetLastError();
 }
 
