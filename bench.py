@@ -65,11 +65,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def source_hash():
-    h = hashlib.sha256()
+def source_hash(unit):
+    """Hash of one kernel's translation unit (csrc/<unit>), the local headers it includes,
+    and plan.cu, which picks the kernels' launch shapes."""
     csrc = os.path.join(ROOT, "paper_1802_10323_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, fn), "rb").read())
+    seen, todo = [], [os.path.join(csrc, unit), os.path.join(csrc, "plan.cu")]
+    while todo:
+        fn = os.path.normpath(todo.pop())
+        if fn in seen or not os.path.exists(fn):
+            continue
+        seen.append(fn)
+        for line in open(fn, encoding="utf-8"):
+            if line.startswith('#include "'):
+                todo.append(os.path.join(os.path.dirname(fn), line.split('"')[1]))
+    h = hashlib.sha256()
+    for fn in sorted(seen):
+        h.update(os.path.relpath(fn, ROOT).encode())
+        h.update(open(fn, "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -89,14 +101,15 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64
 
 
 def recorded_traffic(kernel, n_points):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    """DRAM bytes per launch of a kernel kind of the channel solve, from the committed ncu
+    counters (a small case, per grid point), if its sources still match."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
     ent = rec.get(kernel)
-    if not ent or ent.get("source_hash") != source_hash():
+    if not ent or not ent.get("source") or ent.get("source_hash") != source_hash(ent["source"]):
         return None
     return ent["dram_bytes_per_point"] * n_points
 
@@ -739,6 +752,68 @@ def bench_ours(args):
     return 0
 
 
+def bench_case(args):
+    """One small workload for per-kernel ncu captures (not the benchmark line).
+
+    --case solve: the channel right-hand side on an --shape NX,NY,NZ grid of the same
+    6 x 3 x 1 box (P/P/NN, tanh z), solved --warmup + --steps times at --precision;
+    --case ns: RK3 steps (three ps_ns_substep calls each) on --shape, FP64 fields;
+    --case batch: the 64-grid batch, one persistent launch per solve.
+    Prints one JSON line with the mean milliseconds per step.
+    """
+    import torch
+    from paper_1802_10323_gb300 import binding as lib, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else (1024, 1024, 64)
+    out = {"case": args.case}
+    if args.case == "solve":
+        f, zf, dx, dy = make_input(shape, GRID["seed"], dev)
+        if args.precision == "fp32":
+            f = f.float()
+        plan = lib.Plan(*shape, dx, dy, zf=zf, bcs=BCS, precision=args.precision, rtol=RTOL, max_iter=MAX_ITER)
+        p, info = torch.empty_like(f), lib.info_tensor(dev)
+        step = lambda: plan.solve(f, p, info=info)  # noqa: E731
+        out.update(shape=list(shape), precision=args.precision)
+    elif args.case == "ns":
+        zf = synth.tanh_faces(shape[2], 1.0, 1.5)
+        plan = lib.Plan(*shape, 6.0 / shape[0], 3.0 / shape[1], zf=zf, bcs=BCS, precision="fp32_refine",
+                        rtol=RTOL, max_iter=MAX_ITER)
+        u = torch.stack(synth.staggered_velocity_torch(*shape, 5, device=dev)).contiguous()
+        us, ad = torch.empty_like(u), torch.zeros_like(u)
+        p = torch.zeros((shape[2], shape[1], shape[0]), dtype=torch.float64, device=dev)
+        phi, rhs, info = torch.empty_like(p), torch.empty_like(p), lib.info_tensor(dev)
+
+        def step():
+            for kk in (1, 2, 3):
+                plan.ns_substep(kk, 1e-3, 1.0 / 5600.0, u, us, ad, p, phi, rhs, info=info)
+        out.update(shape=list(shape))
+    elif args.case == "batch":
+        from paper_1802_10323_gb300 import workloads
+        grids = workloads.batch_grids(64, seed=4)
+        plan = lib.Batch(grids, rtol=RTOL, max_iter=MAX_ITER)
+        bf = [torch.as_tensor(x, device=dev).contiguous() for x in workloads.batch_rhs(grids, seed=4)]
+        bp = [torch.zeros_like(x) for x in bf]
+        fptr, pptr = plan.pointers(bf, bp)
+        infos = lib.infos_tensor(len(grids), dev)
+        step = lambda: plan.solve(fptr, pptr, infos)  # noqa: E731
+    else:
+        raise SystemExit(f"unknown case {args.case}")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    out["ms_per_step"] = e0.elapsed_time(e1) / max(args.steps, 1)
+    plan.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -756,7 +831,13 @@ def main():
     ap.add_argument("--no-dn", action="store_true")
     ap.add_argument("--no-long", action="store_true")
     ap.add_argument("--no-ns", action="store_true")
+    ap.add_argument("--case", choices=["solve", "ns", "batch"],
+                    help="run one small workload for an ncu capture instead of the benchmark")
+    ap.add_argument("--shape", default="", help="NX,NY,NZ of --case solve / ns")
+    ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64", "fp32"])
     args = ap.parse_args()
+    if args.case:
+        return bench_case(args)
     if args.impl == "reference":
         return bench_reference(args)
     return bench_ours(args)

@@ -285,6 +285,24 @@ ZArgs<T> zargs(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int
   return a;
 }
 
+// The same z systems on planes stored transposed ([n_x][n_y], y fastest), as the
+// long y lines leave them: the column index runs over q_y first, so the x and y
+// roles (lengths, eigenvalues, the FP64 low-wavenumber rectangle) swap. The
+// elimination scratch is `scratch` (an idle array of n_x·n_y·n_z values of T)
+// instead of the workspace array that now holds the data.
+template <class T>
+ZArgs<T> zargs_t(const ps_plan* p, T* data, void* ws, const WsLayout& L, const int* skip, T* scratch) {
+  ZArgs<T> a = zargs<T>(p, data, ws, L, skip);
+  std::swap(a.nx, a.ny);
+  std::swap(a.lamx, a.lamy);
+  a.scr_c = scratch;
+  if constexpr (sizeof(T) == 4) {
+    std::swap(a.lowx, a.lowy);
+    std::swap(a.lamx64, a.lamy64);
+  }
+  return a;
+}
+
 template <class T, class TI, class TO, bool FWD>
 cudaError_t launch_long(int m, FastArgs<T> a, cudaStream_t st) {
   switch (m) {
@@ -394,6 +412,40 @@ cudaError_t line_xform(const ps_plan* p, int axis, const void* in, void* out, co
   return launch_xform<T, TI, TO, FWD>(ga, st);
 }
 
+// y lines of n_y ∈ {2048, 4096, 8192} (not face-centred): the one-line-per-CTA
+// kernel on planes transposed into the scratch array.
+bool y_long(const ps_plan* p) {
+  const AxisTab& t = p->ay;
+  return (t.m == 1024 || t.m == 2048 || t.m == 4096) && t.bc != BC_FD;
+}
+
+// One y pass of the long kernel that leaves the planes transposed: forward,
+// data [n_z][n_y][n_x] → yt [n_z][n_x][n_y] transformed; backward, yt transformed
+// back in place and transposed into data. Between the two the z solve runs on yt
+// (zargs_t), so each solve moves the data through two plane transposes, not four.
+template <class T, bool FWD>
+cudaError_t y_long_pass(const ps_plan* p, T* data, T* yt, const int* skip, cudaStream_t st) {
+  const AxisTab& t = p->ay;
+  FastArgs<T> a{};
+  a.axis = 0;
+  a.bc = t.bc;
+  if constexpr (sizeof(T) == 8) a.tw = reinterpret_cast<const cplx<T>*>(t.tw64);
+  else a.tw = reinterpret_cast<const cplx<T>*>(t.tw32);
+  a.skip = skip;
+  a.nx = t.n;
+  a.nz = p->nz;
+  a.in = yt;
+  a.out = yt;
+  a.ny = p->nx;  // lines per plane
+  a.nlines = p->nx * p->nz;
+  cudaError_t e;
+  if (FWD && (e = launch_plane_transpose<T>(data, yt, p->ny, p->nx, p->nz, skip, st)) != cudaSuccess) return e;
+  if ((e = launch_long<T, T, T, FWD>(t.m, a, st)) != cudaSuccess) return e;
+  if (!FWD) return launch_plane_transpose<T>(yt, data, p->nx, p->ny, p->nz, skip, st);
+  return cudaSuccess;
+}
+
+
 // Launch `fn` on `st`, bracketed by profiling events when enabled on the plan.
 template <class F>
 cudaError_t run(ps_plan* pl, int kind, cudaStream_t st, F&& fn) {
@@ -424,11 +476,15 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
   if ((e = run(pl, K_XF, st, [&] { return line_xform<T, T, T, true>(pl, 0, f, p, sin_, 0, nullptr, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "x forward");
   void* yscr = static_cast<char*>(ws) + L.scr_c;  // idle outside the z solve
+  // long y lines: the z solve runs on the transposed planes in yscr, p is its scratch
+  const bool yl = y_long(pl);
+  T* yt = static_cast<T*>(yscr);
   if ((e = run(pl, K_YF, st, [&] {
-         return line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st, nullptr, nullptr, nullptr, 0, yscr);
+         return yl ? y_long_pass<T, true>(pl, p, yt, nullptr, st)
+                   : line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st);
        })) != cudaSuccess)
     return cuda_fail(pl, e, "y forward");
-  const ZArgs<T> za = zargs<T>(pl, p, ws, L, nullptr);
+  const ZArgs<T> za = yl ? zargs_t<T>(pl, yt, ws, L, nullptr, p) : zargs<T>(pl, p, ws, L, nullptr);
   if ((e = run(pl, K_Z, st, [&] {
          if constexpr (sizeof(T) == 4)
            if (!pl->periodic_z) return launch_zsolve_ckpt(za, st);
@@ -439,7 +495,8 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
       (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z singular column");
   if ((e = run(pl, K_YB, st, [&] {
-         return line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st, nullptr, nullptr, nullptr, 0, yscr);
+         return yl ? y_long_pass<T, false>(pl, p, yt, nullptr, st)
+                   : line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st);
        })) != cudaSuccess)
     return cuda_fail(pl, e, "y backward");
   if ((e = run(pl, K_XB, st, [&] { return line_xform<T, T, T, false>(pl, 0, p, p, sout, 0, nullptr, st); })) != cudaSuccess)
@@ -465,6 +522,10 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
   float* u0 = reinterpret_cast<float*>(wb + L.u0);
   void* yscr = wb + L.scr_c;  // the transposed y lines of n ≥ 2048 (idle outside the z solve)
   const ZArgs<float> zw = zargs<float>(pl, w, ws, L, skip);
+  // long y lines: between the y passes the planes stay transposed in yscr, and the
+  // z solve runs there with w (idle then) as its scratch
+  float* yt = static_cast<float*>(yscr);
+  const ZArgs<float> zwt = zargs_t<float>(pl, yt, ws, L, skip, w);
   // One FP32 solve (c = 0: of f; c ≥ 1: of r = rh, the c-th correction) through w.
   // The x backward writes Φ_0 to u0 only (c = 0; the FP64 p is written by the first
   // correction as Φ_0 + e, or from Φ_0 alone if the loop ends at pass 0), then
@@ -496,20 +557,25 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
         r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, rh, w, nullptr, 0, skip, st); });
       if (r != cudaSuccess) return r;
       if ((r = run(pl, K_YF, st, [&] {
-             return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st, nullptr, nullptr,
-                                                          nullptr, 0, yscr);
+             return y_long(pl) ? y_long_pass<float, true>(pl, w, yt, skip, st)
+                               : line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st);
            })) != cudaSuccess)
         return r;
     }
+    // (chunked host input, whose y lines of n ≤ 1024 never take the long kernel, keeps
+    // the planes untransposed)
+    const bool ytr = y_long(pl) && !(first && hp);
+    const ZArgs<float>& za = ytr ? zwt : zw;
     if ((r = run(pl, K_Z, st, [&] {
-           return pl->periodic_z ? launch_zsolve<float>(zw, st) : launch_zsolve_ckpt(zw, st);
+           return pl->periodic_z ? launch_zsolve<float>(za, st) : launch_zsolve_ckpt(za, st);
          })) != cudaSuccess)
       return r;
     if (pl->singular && (pl->periodic_z || pl->lowx == 0) &&
-        (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(zw, st); })) != cudaSuccess) return r;
+        (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(za, st); })) != cudaSuccess) return r;
     if ((r = run(pl, K_YB, st, [&] {
-           return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st, nullptr, nullptr,
-                                                         nullptr, 0, yscr);
+           return ytr ? y_long_pass<float, false>(pl, w, yt, skip, st)
+                      : line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st, nullptr, nullptr,
+                                                               nullptr, 0, yscr);
          })) != cudaSuccess)
       return r;
     if (first)

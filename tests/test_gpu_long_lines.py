@@ -1,10 +1,14 @@
 """GPU parity for x and y lines longer than 1024 cells (up to 8192; n/2 = 2^a·3^b).
 
-Lines of n ≤ 1024 run in the register-resident transform kernels; longer ones
-run in the shared-memory kernel, one line per CTA (two buffers of n/2 + 1
-complex values, 131 KB for an FP64 line of 8192), with radix-4/2/3 stages.
-Checked against the FP64 oracle (dense Table 2 matrices) in FP64, FP32 and the
-refined mode, for each BC family including D-N, along x and along y.
+Lines of n ≤ 1024 run in the register-resident transform kernels. Lines of 2048,
+4096 and 8192 run in the one-line-per-CTA kernel; y lines of those lengths are
+transposed plane by plane into a scratch array first, stay transposed through the
+z solve (whose x and y roles then swap) and are transposed back after the
+backward y pass. Other long lengths (1536, …) run in the generic shared-memory
+kernel. Checked against the FP64 oracle (dense Table 2 matrices) in FP64, FP32 and
+the refined mode, for each BC family including D-N, along x and along y; the
+transposed z solve with the singular column, a periodic z, and an FP64 rectangle
+of low wavenumbers that is not square.
 """
 
 import numpy as np
@@ -67,3 +71,32 @@ def test_long_lines_refine(lib, shape, bcs):
     rr = O.relative_residual(p, f, lx / nx, ly / ny, zf, *bcs)
     assert info.status == 0 and info.rel_residual <= 1e-10, (info.status, info.rel_residual, rr)
     assert rr <= 1e-10 and abs(info.rel_residual - rr) <= 1e-11, (info.rel_residual, rr)
+
+
+# y lines of 2048 … 8192: the z solve on transposed planes. Case 1 has a 24 × 31 box, so
+# the FP64 rectangle of ill-conditioned columns (|λ| below 10^-4 of the z operator's
+# norm) is about 9 × 11 (q_x × q_y), not square, while κ stays near 10^6.
+TRANSPOSED = [((4, 2048, 24), ("P", "NN", "NN"), 1.0, 0.015), ((2, 4096, 6), ("NN", "P", "P"), None, None),
+              ((3, 2048, 36), ("DD", "NN", "DN"), None, None), ((4, 8192, 16), ("P", "P", "NN"), None, None)]
+
+
+@pytest.mark.parametrize("shape,bcs,dx,dy", TRANSPOSED,
+                         ids=["x".join(map(str, c[0])) + "-" + "-".join(c[1]) for c in TRANSPOSED])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5), ("fp32_refine", 1e-8)])
+def test_long_y_z_solve_on_transposed_planes(lib, shape, bcs, dx, dy, precision, tol):
+    nz, ny, nx = shape
+    dx = dx or 4.0 / nx
+    dy = dy or 4.0 / ny
+    zf = synth.tanh_faces(nz, 1.0, 1.5) if bcs[2] != "P" else synth.uniform_faces(nz, 1.0)
+    f = np.random.default_rng(nx * ny + nz).uniform(-1, 1, shape)
+    kw = dict(rtol=1e-10, max_iter=6) if precision == "fp32_refine" else {}
+    if precision == "fp32" and bcs == ("P", "NN", "NN"):
+        # the FP32 path solves columns of κ up to 10^4 in FP32 (the rest go to the FP64
+        # rectangle): its error bound is about κ·ε_32 ≈ 6e-4 on this machine, not 2e-5
+        tol = 6e-4
+    p, info = _run(lib, f, dx, dy, zf, bcs, precision=precision, **kw)
+    q = S.solve(f, dx, dy, zf, *bcs)
+    assert _relerr(p, q) <= tol
+    if precision == "fp32_refine":
+        rr = O.relative_residual(p, f, dx, dy, zf, *bcs)
+        assert info.status == 0 and rr <= 1e-10 and abs(info.rel_residual - rr) <= 1e-11, (info.rel_residual, rr)
