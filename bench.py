@@ -66,10 +66,10 @@ def peaks():
 
 
 def source_hash(unit):
-    """Hash of one kernel's translation unit (csrc/<unit>), the local headers it includes,
-    and plan.cu, which picks the kernels' launch shapes."""
+    """Hash of one kernel's translation unit (csrc/<unit>, whose launcher sets the launch
+    shape) and the local headers it includes."""
     csrc = os.path.join(ROOT, "paper_1802_10323_gb300", "csrc")
-    seen, todo = [], [os.path.join(csrc, unit), os.path.join(csrc, "plan.cu")]
+    seen, todo = [], [os.path.join(csrc, unit)]
     while todo:
         fn = os.path.normpath(todo.pop())
         if fn in seen or not os.path.exists(fn):
