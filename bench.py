@@ -752,6 +752,78 @@ def bench_ours(args):
     return 0
 
 
+def _time_ms(fn, warmup, steps):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_configs(args, dev):
+    """The small configurations beside the 1024^3 channel (timing only; their parity
+    against the oracle is asserted by the GPU tests):
+      C1  32^3 unit cube, P/P/NN uniform z, f ~ U[-1,1] (PCG64 seed 0), FP64;
+      C2  256^3 unit cube, x, y in {P, NN, DD, ND} (16 pairs), NN tanh z, manufactured
+          f + 10 % noise (seed 100 + pair), FP64 and FP32+refine to 1e-10;
+      C5  512x256x256 channel box, P/P/NN tanh z, FP32 projection forward + backward
+          (u* ~ N(0,1) on faces, seed 5; loss = sum(weights * P(u*)), weights seed 6)."""
+    import itertools
+    import torch
+    from paper_1802_10323_gb300 import autograd, binding as lib, synth
+    w_, k_ = max(args.warmup, 3), max(args.steps, 10)
+    out = {"case": "configs"}
+    zf1 = synth.uniform_faces(32, 1.0)
+    f1 = torch.as_tensor(synth.uniform_noise((32, 32, 32), 0), device=dev)
+    plan1 = lib.Plan(32, 32, 32, 1 / 32, 1 / 32, zf=zf1, bcs=("P", "P", "NN"), precision="fp64")
+    p1 = torch.empty_like(f1)
+    ms1 = _time_ms(lambda: plan1.solve(f1, p1), w_, 20 * k_)
+    plan1.close()
+    out["C1"] = {"ms_per_solve": ms1, "mpts_s": 32 ** 3 / (ms1 * 1e-3) / 1e6, "precision": "fp64"}
+    n = 256
+    zf2 = synth.tanh_faces(n, 1.0, 1.5)
+    c2 = {}
+    for prec in ("fp64", "fp32_refine"):
+        tot = 0.0
+        worst = 0.0
+        for idx, bxy in enumerate(itertools.product(("P", "NN", "DD", "ND"), repeat=2)):
+            bcs = (bxy[0], bxy[1], "NN")
+            _, f = synth.manufactured(n, n, 1.0, 1.0, zf2, bcs, noise=0.1, seed=100 + idx)
+            ft = torch.as_tensor(f, device=dev).contiguous()
+            pl = lib.Plan(n, n, n, 1 / n, 1 / n, zf=zf2, bcs=bcs, precision=prec, rtol=RTOL, max_iter=MAX_ITER)
+            pt, info = torch.empty_like(ft), lib.info_tensor(dev)
+            ms = _time_ms(lambda: pl.solve(ft, pt, info=info), w_, k_)
+            tot += ms
+            if prec == "fp32_refine":
+                worst = max(worst, lib.read_info(info).rel_residual)
+            pl.close()
+        c2[prec] = {"ms_per_solve_mean": tot / 16, "mpts_s": 16 * n ** 3 / (tot * 1e-3) / 1e6}
+        if prec == "fp32_refine":
+            c2[prec]["max_rel_residual"] = worst
+    out["C2"] = c2
+    n5 = (512, 256, 256)
+    z5 = synth.tanh_faces(n5[2], 1.0, 1.5)
+    proj = autograd.Projection(*n5, 6.0 / n5[0], 3.0 / n5[1], zf=z5, bcs=("P", "P", "NN"), precision="fp32")
+    us = torch.stack(synth.staggered_velocity_torch(*n5, 5, device=dev)).float().contiguous().requires_grad_(True)
+    wts = torch.randn(us.shape, generator=torch.Generator(device=dev).manual_seed(6), device=dev, dtype=torch.float32)
+
+    def step():
+        us.grad = None
+        (wts * proj(us)).sum().backward()
+    ms5 = _time_ms(step, w_, k_)
+    proj.close()
+    cells = n5[0] * n5[1] * n5[2]
+    out["C5"] = {"ms_per_fwd_bwd": ms5, "mcells_s": cells / (ms5 * 1e-3) / 1e6, "precision": "fp32"}
+    print(json.dumps(out))
+    return 0
+
+
 def bench_case(args):
     """One small workload for per-kernel ncu captures (not the benchmark line).
 
@@ -788,6 +860,8 @@ def bench_case(args):
             for kk in (1, 2, 3):
                 plan.ns_substep(kk, 1e-3, 1.0 / 5600.0, u, us, ad, p, phi, rhs, info=info)
         out.update(shape=list(shape))
+    elif args.case == "configs":
+        return bench_configs(args, dev)
     elif args.case == "batch":
         from paper_1802_10323_gb300 import workloads
         grids = workloads.batch_grids(64, seed=4)
@@ -831,7 +905,7 @@ def main():
     ap.add_argument("--no-dn", action="store_true")
     ap.add_argument("--no-long", action="store_true")
     ap.add_argument("--no-ns", action="store_true")
-    ap.add_argument("--case", choices=["solve", "ns", "batch"],
+    ap.add_argument("--case", choices=["solve", "ns", "batch", "configs"],
                     help="run one small workload for an ncu capture instead of the benchmark")
     ap.add_argument("--shape", default="", help="NX,NY,NZ of --case solve / ns")
     ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64", "fp32"])
