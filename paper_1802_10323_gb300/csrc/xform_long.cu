@@ -26,6 +26,11 @@
 // data, instead of strided loads that would fetch one 32-byte sector per value.
 #include "xform_units.cuh"
 
+// threads per SM the FP32 kernels are compiled for (their register cap)
+#ifndef PS_LONG_THREADS
+#define PS_LONG_THREADS 1024
+#endif
+
 namespace ps {
 namespace lng {
 
@@ -38,7 +43,6 @@ struct LShape {
 };
 
 __host__ __device__ constexpr int lpad(int i) { return i + (i >> 4); }   // complex buffer
-__host__ __device__ constexpr int rpad(int e) { return e + (e >> 5); }   // real line
 
 // Twiddle tables of one CTA (every entry a value of the 8n-entry table
 // e^{−2πi t/(8n)}, so exact up to one complex product where two are combined):
@@ -134,18 +138,23 @@ __device__ __forceinline__ void fft_line(cplx<T> (&v)[16], cplx<T>* buf, const L
 
 template <class T, int M>
 __host__ __device__ constexpr size_t long_smem() {
-  // twiddle tables, the complex buffer (padded), the real line (padded)
-  return (size_t)LTab<T, M>::ENTRIES * sizeof(cplx<T>) + (size_t)(lpad(M) + 1) * sizeof(cplx<T>) +
-         (size_t)(rpad(2 * M) + 2) * sizeof(T);
+  // twiddle tables and the complex exchange buffer (padded)
+  return (size_t)LTab<T, M>::ENTRIES * sizeof(cplx<T>) + (size_t)(lpad(M) + 1) * sizeof(cplx<T>);
 }
 
 // Makhoul index map (as xform_dev.cuh): position j of v ↔ position of a.
 __device__ __forceinline__ int mk(int j, int n, int m) { return j < m ? 2 * j : 2 * n - 1 - 2 * j; }
 
 // a.nlines lines of n = 2M contiguous reals; line ln belongs to plane ln / a.ny
-// (for the per-plane scale). Output modes as the row kernels (FastArgs).
+// (for the per-plane scale). Output modes as the row kernels (FastArgs). The first
+// stage's operands are read straight from the line in global memory (each lane a
+// consecutive pair or a mirrored position, so a warp's loads cover contiguous
+// 256-byte spans), and the post-processing writes each output value straight to
+// global memory: the only shared buffer is the complex exchange of the FFT. All
+// reads of a line happen before the first stage's barrier and all writes after
+// the last, so in == out is safe.
 template <class T, class TI, class TO, int M, bool FWD>
-__global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / LShape<M>::NT)
+__global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG_THREADS) / LShape<M>::NT)
     xform_long_kernel(FastArgs<T> a) {
   using S = LShape<M>;
   constexpr int N = 2 * M, NT = S::NT, E = S::E, RL = S::radix(S::NST - 1);
@@ -154,11 +163,9 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
   LTab<T, M> tb;
   tb.carve(reinterpret_cast<cplx<T>*>(smem_raw), a.tw);
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw) + LTab<T, M>::ENTRIES;  // [lpad(M) + 1]
-  T* rbuf = reinterpret_cast<T*>(buf + lpad(M) + 1);                           // [rpad(N) + 1]
   const int b = threadIdx.x;
   tb.fill(b, NT);
   const cplx<T> tw1 = a.tw[1];  // e^{−2πi/(8n)}: the ND post-twiddle is tw(4k)·tw1
-  auto RB = [&](int e) -> T& { return rbuf[rpad(e)]; };
   const int bc = a.bc;
   // no __restrict__: in and out may be the same array
   const TI* in = static_cast<const TI*>(a.in);
@@ -174,34 +181,85 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
         for (int o = b * 128; o < N * (int)sizeof(TI); o += NT * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + o));
       }
     }
-    __syncthreads();  // tables ready; the previous line's buffers are no longer read
-    {  // 16-byte loads, 128 bytes of each thread in flight at once
-      const T sc = (FWD && a.plane_scale) ? a.plane_scale[z] : (T)1;
-      constexpr int V = 16 / sizeof(TI);   // values per vector
-      constexpr int NV = N / (V * NT);     // vectors per thread
-      constexpr int KV = NV < 8 ? NV : 8;  // vectors per round
-      static_assert(N % (V * NT) == 0 && NV % KV == 0, "whole vectors per thread");
-#pragma unroll
-      for (int i0 = 0; i0 < NV; i0 += KV) {
-        TI val[KV * V];
-#pragma unroll
-        for (int i = 0; i < KV; ++i) {
-          const int e = V * (b + (i0 + i) * NT);
-          if constexpr (V == 4) {
-            const float4 q = *reinterpret_cast<const float4*>(in + g0 + e);
-            val[V * i] = q.x; val[V * i + 1] = q.y; val[V * i + 2] = q.z; val[V * i + 3] = q.w;
-          } else {
-            const double2 q = *reinterpret_cast<const double2*>(in + g0 + e);
-            val[V * i] = q.x; val[V * i + 1] = q.y;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < KV; ++i)
-#pragma unroll
-          for (int u = 0; u < V; ++u) RB(V * (b + (i0 + i) * NT) + u) = ld_cvt<T, TI>::f(val[V * i + u]) * sc;
+    const TI* src = in + g0;
+    const T sci = (FWD && a.plane_scale) ? a.plane_scale[z] : (T)1;
+    const T sco = (!FWD && a.plane_scale) ? a.plane_scale[z] : (T)1;
+    // the line is read once: evict-first loads, so that the twiddle table stays in L1
+    auto X = [&](int e) -> T { return ld_cvt<T, TI>::f(__ldcs(src + e)) * sci; };
+    // a consecutive pair (e even): one 8- or 16-byte load
+    auto X2 = [&](int e) -> cplx<T> {
+      if constexpr (sizeof(TI) == 4) {
+        const float2 q = __ldcs(reinterpret_cast<const float2*>(src + e));
+        return {ld_cvt<T, TI>::f(q.x) * sci, ld_cvt<T, TI>::f(q.y) * sci};
+      } else {
+        const double2 q = __ldcs(reinterpret_cast<const double2*>(src + e));
+        return {ld_cvt<T, TI>::f(q.x) * sci, ld_cvt<T, TI>::f(q.y) * sci};
       }
-    }
-    __syncthreads();
+    };
+    // one output value at position e of the line, with the output modes of the row
+    // kernels (plane scale; FP64 out with a widened FP32 base or accumulation, the
+    // FP32 copy, the max-abs of the new values; or plain / accumulated T)
+    auto emit = [&](int e, T val) {
+      const size_t g = g0 + e;
+      const T vs = val * sco;
+      if constexpr (sizeof(TO) == 8) {
+        const TO d = st_cvt<TO, T>::f(vs);
+        amax = max(amax, (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull);
+        if (out) {
+          TO x = d;
+          if constexpr (sizeof(T) == 4) {
+            if (a.base32) x = widen_f32(a.base32[g]) + d;
+            else if (a.accumulate) x = out[g] + d;
+          } else if (a.accumulate) {
+            x = out[g] + d;
+          }
+          out[g] = x;
+        }
+        if constexpr (sizeof(T) == 4)
+          if (a.out2) a.out2[g] = vs;
+      } else {
+        TO x = st_cvt<TO, T>::f(vs);
+        if (a.accumulate) x = out[g] + x;
+        __stcs(out + g, x);
+      }
+    };
+    // two consecutive output values (e even): the same modes with 8- and 16-byte accesses
+    auto emit2 = [&](int e, T val0, T val1) {
+      const size_t g = g0 + e;
+      const T s0 = val0 * sco, s1 = val1 * sco;
+      if constexpr (sizeof(TO) == 8) {
+        const TO d0 = st_cvt<TO, T>::f(s0), d1 = st_cvt<TO, T>::f(s1);
+        amax = max(amax, max((unsigned long long)__double_as_longlong(d0) & 0x7FFFFFFFFFFFFFFFull,
+                             (unsigned long long)__double_as_longlong(d1) & 0x7FFFFFFFFFFFFFFFull));
+        if (out) {
+          TO x0 = d0, x1 = d1;
+          bool acc = a.accumulate != 0;
+          if constexpr (sizeof(T) == 4) {
+            if (a.base32) {
+              const float2 q = *reinterpret_cast<const float2*>(a.base32 + g);
+              x0 = widen_f32(q.x) + d0;
+              x1 = widen_f32(q.y) + d1;
+              acc = false;
+            }
+          }
+          if (acc) {
+            const double2 q = *reinterpret_cast<const double2*>(out + g);
+            x0 = q.x + d0;
+            x1 = q.y + d1;
+          }
+          *reinterpret_cast<double2*>(out + g) = make_double2(x0, x1);
+        }
+        if constexpr (sizeof(T) == 4)
+          if (a.out2) *reinterpret_cast<float2*>(a.out2 + g) = make_float2(s0, s1);
+      } else {
+        TO x0 = st_cvt<TO, T>::f(s0), x1 = st_cvt<TO, T>::f(s1);
+        if (a.accumulate) {
+          x0 = out[g] + x0;
+          x1 = out[g + 1] + x1;
+        }
+        __stcs(reinterpret_cast<float2*>(out + g), make_float2(x0, x1));
+      }
+    };
     cplx<T> v[E];
     if (FWD) {
       // ---- pre-processing gathered into the first stage's operands z_p, p = b + r·NT ----
@@ -210,13 +268,13 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
         const int p = b + r * NT;
         cplx<T> zz;
         if (bc == BC_P) {
-          zz = {RB(2 * p), RB(2 * p + 1)};
+          zz = X2(2 * p);
         } else if (bc_iv(bc)) {  // DN: the reversed line, the two reals swap
-          const T e0 = RB(2 * p), e1 = RB(N - 1 - 2 * p);
+          const T e0 = X(2 * p), e1 = X(N - 1 - 2 * p);
           zz = cmul(bc == BC_DN ? cplx<T>{e1, e0} : cplx<T>{e0, e1}, tb.pp(1, p));
         } else {
           const int j0 = 2 * p, j1 = 2 * p + 1;
-          T v0 = RB(mk(j0, N, M)), v1 = RB(mk(j1, N, M));
+          T v0 = X(mk(j0, N, M)), v1 = X(mk(j1, N, M));
           if (bc == BC_DD) {
             if (j0 >= M) v0 = -v0;
             if (j1 >= M) v1 = -v1;
@@ -225,6 +283,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
         }
         v[r] = zz;
       }
+      __syncthreads();  // the tables are ready; the previous line's buffer reads are done
       fft_line<T, M, false, 0, 1>(v, buf, tb, b);
       // ---- post-processing: pair k with M − k through the complex buffer ----
       __syncthreads();
@@ -237,8 +296,8 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
 #pragma unroll 4
         for (int k = b; k < M; k += NT) {
           const cplx<T> c = cmul(cmul(tb.pp(1, k), tw1), buf[lpad(k)]);
-          RB(2 * k) = (T)2 * c.x;
-          RB(N - 1 - 2 * k) = (T)-2 * c.y;
+          emit(2 * k, (T)2 * c.x);
+          emit(N - 1 - 2 * k, (T)-2 * c.y);
         }
       } else {
 #pragma unroll 4
@@ -250,19 +309,19 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
           const cplx<T> Vk = cadd(Ek, B), Vmk = conj_(csub(Ek, B));  // k = 0: Vmk is V_M
           if (bc == BC_P) {
             if (k == 0) {
-              RB(0) = Vk.x;
-              RB(N - 1) = Vmk.x;
+              emit(0, Vk.x);
+              emit(N - 1, Vmk.x);
             } else {
-              RB(2 * k - 1) = Vk.x;
-              RB(2 * k) = -Vk.y;
+              emit(2 * k - 1, Vk.x);
+              emit(2 * k, -Vk.y);
               if (2 * k != M) {
-                RB(2 * (M - k) - 1) = Vmk.x;
-                RB(2 * (M - k)) = -Vmk.y;
+                emit(2 * (M - k) - 1, Vmk.x);
+                emit(2 * (M - k), -Vmk.y);
               }
             }
           } else {
             const bool rev = (bc == BC_DD);
-            auto put = [&](int qq, T val) { RB(rev ? (N - 1 - qq) : qq) = val; };
+            auto put = [&](int qq, T val) { emit(rev ? (N - 1 - qq) : qq, val); };
             if (k == 0) {
               put(0, (T)2 * Vk.x);
               put(M, (T)1.41421356237309504880 * Vmk.x);
@@ -281,26 +340,27 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
       }
     } else {
       // ---- backward pre-processing: reals → the M complex points (pairs k, M − k) ----
+      __syncthreads();  // the tables are ready; the previous line's buffer reads are done
       if (bc_iv(bc)) {
 #pragma unroll 4
-        for (int k = b; k < M; k += NT) buf[lpad(k)] = cmul(cplx<T>{RB(2 * k), RB(N - 1 - 2 * k)}, tb.pp(1, k));
+        for (int k = b; k < M; k += NT) buf[lpad(k)] = cmul(cplx<T>{X(2 * k), X(N - 1 - 2 * k)}, tb.pp(1, k));
       } else {
 #pragma unroll 4
         for (int k = b; k <= M / 2; k += NT) {
           cplx<T> Vk, Vmk;
           if (bc == BC_P) {
             if (k == 0) {
-              Vk = {RB(0), (T)0};
-              Vmk = {RB(N - 1), (T)0};
+              Vk = {X(0), (T)0};
+              Vmk = {X(N - 1), (T)0};
             } else {
-              Vk = {RB(2 * k - 1), -RB(2 * k)};
-              Vmk = {RB(2 * (M - k) - 1), -RB(2 * (M - k))};
+              Vk = {X(2 * k - 1), -X(2 * k)};
+              Vmk = {X(2 * (M - k) - 1), -X(2 * (M - k))};
             }
           } else {
             // DCT-III via Makhoul: V_q = e^{+iπq/2n} (X_q − i X_{n−q}) / 2, X_n = 0;
             // DST-III: the same on Y_q = X_{n−1−q}
             const bool rev = (bc == BC_DD);
-            auto XQ = [&](int qq) { return qq >= N ? (T)0 : RB(rev ? (N - 1 - qq) : qq); };
+            auto XQ = [&](int qq) { return qq >= N ? (T)0 : X(rev ? (N - 1 - qq) : qq); };
             cplx<T> w = tb.pp(0, k);
             w.y = -w.y;
             Vk = cscale(cmul(w, cplx<T>{XQ(k), -XQ(N - k)}), (T)0.5);
@@ -322,8 +382,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
       for (int r = 0; r < E; ++r) v[r] = buf[lpad(b + r * NT)];
       if (bc_iv(bc)) fft_line<T, M, false, 0, 1>(v, buf, tb, b);  // DCT-IV is its own inverse
       else fft_line<T, M, true, 0, 1>(v, buf, tb, b);
-      // ---- backward post-processing straight from the last stage to the real line ----
-      __syncthreads();  // (the real buffer was last read by the pre-processing)
+      // ---- backward post-processing straight from the last stage to the line ----
       const T inv_m = (T)1 / (T)M;
 #pragma unroll
       for (int q = 0; q < E / RL; ++q) {
@@ -335,11 +394,10 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
             const T s = (T)1 / (T)N;  // 2·(1/2n)
             const cplx<T> c = cmul(cmul(tb.pp(1, k), tw1), zk);
             const T A = s * c.x, B = -s * c.y;  // DN: the two outputs trade places
-            RB(2 * k) = (bc == BC_DN) ? B : A;
-            RB(N - 1 - 2 * k) = (bc == BC_DN) ? A : B;
+            emit(2 * k, (bc == BC_DN) ? B : A);
+            emit(N - 1 - 2 * k, (bc == BC_DN) ? A : B);
           } else if (bc == BC_P) {
-            RB(2 * k) = zk.x * inv_m;
-            RB(2 * k + 1) = zk.y * inv_m;
+            emit2(2 * k, zk.x * inv_m, zk.y * inv_m);
           } else {
             const int i0 = mk(2 * k, N, M), i1 = mk(2 * k + 1, N, M);
             T v0 = zk.x * inv_m, v1 = zk.y * inv_m;
@@ -347,69 +405,8 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
               if (i0 & 1) v0 = -v0;
               if (i1 & 1) v1 = -v1;
             }
-            RB(i0) = v0;
-            RB(i1) = v1;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    // ---- store, with the output modes of the row kernels: V consecutive values per
-    // thread and vector access (16 bytes of the output), the reads of a round first ----
-    {
-      const T sc = (!FWD && a.plane_scale) ? a.plane_scale[z] : (T)1;
-      constexpr int V = 16 / sizeof(TO);
-      constexpr int NV = N / (V * NT);
-      constexpr int KV = NV < 8 ? NV : 8;
-      static_assert(N % (V * NT) == 0 && NV % KV == 0, "whole vectors per thread");
-#pragma unroll
-      for (int i0 = 0; i0 < NV; i0 += KV) {
-        T vv[KV * V];
-        TO old[KV * V];  // the base (FP64 output: widened base32 or the accumulated out)
-#pragma unroll
-        for (int i = 0; i < KV; ++i) {
-          const int e = V * (b + (i0 + i) * NT);
-#pragma unroll
-          for (int u = 0; u < V; ++u) {
-            vv[V * i + u] = RB(e + u) * sc;
-            old[V * i + u] = (TO)0;
-          }
-          if constexpr (sizeof(TO) == 8 && sizeof(T) == 4) {
-            if (a.base32) {
-              const float2 q = *reinterpret_cast<const float2*>(a.base32 + g0 + e);
-              old[V * i] = widen_f32(q.x);
-              old[V * i + 1] = widen_f32(q.y);
-            } else if (out && a.accumulate) {
-              const double2 q = *reinterpret_cast<const double2*>(out + g0 + e);
-              old[V * i] = q.x;
-              old[V * i + 1] = q.y;
-            }
-          } else if (a.accumulate) {
-#pragma unroll
-            for (int u = 0; u < V; ++u) old[V * i + u] = out[g0 + e + u];
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < KV; ++i) {
-          const int e = V * (b + (i0 + i) * NT);
-          TO x[V];
-#pragma unroll
-          for (int u = 0; u < V; ++u) {
-            x[u] = st_cvt<TO, T>::f(vv[V * i + u]);
-            const bool add = (sizeof(TO) == 8 && sizeof(T) == 4) ? (a.base32 != nullptr || a.accumulate != 0)
-                                                                   : (a.accumulate != 0);
-            if (add) x[u] = old[V * i + u] + x[u];
-          }
-          if constexpr (sizeof(TO) == 8) {
-#pragma unroll
-            for (int u = 0; u < V; ++u)
-              amax = max(amax, (unsigned long long)__double_as_longlong(st_cvt<TO, T>::f(vv[V * i + u])) &
-                                   0x7FFFFFFFFFFFFFFFull);
-            if (out) *reinterpret_cast<double2*>(out + g0 + e) = make_double2(x[0], x[1]);
-            if constexpr (sizeof(T) == 4)
-              if (a.out2) *reinterpret_cast<float2*>(a.out2 + g0 + e) = make_float2(vv[V * i], vv[V * i + 1]);
-          } else {
-            *reinterpret_cast<float4*>(out + g0 + e) = make_float4(x[0], x[1], x[2], x[3]);
+            emit(i0, v0);
+            emit(i1, v1);
           }
         }
       }
@@ -424,27 +421,41 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : 768) / 
 }
 
 // Transpose of every z plane: src [n_z][rows][cols] → dst [n_z][cols][rows], tiles of
-// 32 × 32 through shared memory (one pad column), 32 × 8 threads, four rows each.
+// 64 × 64 through shared memory (one pad column), 32 × 8 threads, each moving pairs of
+// consecutive values (8- or 16-byte accesses: rows and cols are even) in eight rows.
 template <class T>
 __global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ src, T* __restrict__ dst, int rows,
                                                         int cols, const int* skip) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   if (skip && *skip) return;
-  __shared__ T tile[32][33];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  extern __shared__ __align__(16) unsigned char tsm[];
+  T(*tile)[65] = reinterpret_cast<T(*)[65]>(tsm);  // [64][65]
+  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
   const size_t plane = (size_t)rows * cols;
   const T* s = src + (size_t)blockIdx.z * plane;
   T* d = dst + (size_t)blockIdx.z * plane;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  T2 q[8];
 #pragma unroll
-  for (int j = 0; j < 32; j += 8) {
-    const int r = r0 + ty + j, c = c0 + tx;
-    if (r < rows && c < cols) tile[ty + j][tx] = s[(size_t)r * cols + c];
+  for (int j = 0; j < 8; ++j) {
+    const int r = r0 + ty + 8 * j, c = c0 + 2 * tx;
+    if (r < rows && c < cols) q[j] = __ldcs(reinterpret_cast<const T2*>(s + (size_t)r * cols + c));
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    tile[ty + 8 * j][2 * tx] = q[j].x;
+    tile[ty + 8 * j][2 * tx + 1] = q[j].y;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < 32; j += 8) {
-    const int c = c0 + ty + j, r = r0 + tx;
-    if (r < rows && c < cols) d[(size_t)c * rows + r] = tile[tx][ty + j];
+  for (int j = 0; j < 8; ++j) {
+    const int c = c0 + ty + 8 * j, r = r0 + 2 * tx;
+    if (r < rows && c < cols) {
+      T2 o;
+      o.x = tile[2 * tx][ty + 8 * j];
+      o.y = tile[2 * tx + 1][ty + 8 * j];
+      __stcs(reinterpret_cast<T2*>(d + (size_t)c * rows + r), o);
+    }
   }
 }
 
@@ -476,8 +487,10 @@ template <class T>
 cudaError_t launch_plane_transpose(const T* src, T* dst, int rows, int cols, int nz, const int* skip,
                                    cudaStream_t st) {
   if (nz <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
-  const dim3 grid((cols + 31) / 32, (rows + 31) / 32, nz);
-  lng::transpose_kernel<T><<<grid, dim3(32, 8), 0, st>>>(src, dst, rows, cols, skip);
+  if ((rows | cols) & 1) return cudaErrorInvalidValue;  // pairs of consecutive values
+  const dim3 grid((cols + 63) / 64, (rows + 63) / 64, nz);
+  const size_t smem = 64 * 65 * sizeof(T);  // ≤ 33 KB: no opt-in needed
+  lng::transpose_kernel<T><<<grid, dim3(32, 8), smem, st>>>(src, dst, rows, cols, skip);
   return cudaGetLastError();
 }
 
