@@ -28,11 +28,59 @@
 // ghost, or the zero wall face), so the flux formulas below are those of the
 // periodic box; which axes are periodic is a template argument, so the periodic box
 // compiles to plain wrapped offsets.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace ps {
 
 namespace {
+
+// ---- the arithmetic of the predictor ------------------------------------------------
+// FP32 fields are evaluated in float. FP64 fields are evaluated in double-float (ddf:
+// an unevaluated sum hi + lo of two floats, ~48 significant bits, with the TwoSum and
+// FMA-product arithmetic of common.cuh): an FP64 operation issues at 1/64 of the FP32
+// rate on this part, so the ~110 operations per cell of the predictor kept the FP64
+// pipe saturated (86 %) while HBM idled. The FP64 inputs are split on their bit
+// patterns (no FP64 instruction); only the outputs are formed in FP64: AD^k rounded
+// once, and u* = u^k + (its increment) with one FP64 add.
+struct ddf {
+  float h, l;
+};
+__device__ __forceinline__ ddf operator+(ddf a, ddf b) {
+  const df r = df_add(df{a.h, a.l}, df{b.h, b.l});
+  return {r.h, r.l};
+}
+__device__ __forceinline__ ddf operator-(ddf a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ ddf operator-(ddf a, ddf b) { return a + (-b); }
+__device__ __forceinline__ ddf operator*(ddf a, ddf b) {
+  const df r = df_mul(df{a.h, a.l}, df{b.h, b.l});
+  return {r.h, r.l};
+}
+template <class N>
+struct Num;
+template <>
+struct Num<float> {
+  static __device__ __forceinline__ float in(float x) { return x; }
+  static __device__ __forceinline__ float out(float x) { return x; }
+  static __device__ __forceinline__ float zero() { return 0.f; }
+  static __device__ __forceinline__ float scale(float x, float pow2) { return x * pow2; }
+};
+template <>
+struct Num<ddf> {
+  static __device__ __forceinline__ ddf in(double x) {
+    ddf r;
+    split_f64(x, r.h, r.l);
+    return r;
+  }
+  static __device__ __forceinline__ double out(ddf x) { return widen_f32(x.h) + widen_f32(x.l); }
+  static __device__ __forceinline__ ddf zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ ddf scale(ddf x, float pow2) { return {x.h * pow2, x.l * pow2}; }  // exact
+};
+// the number type of the predictor for fields of type T
+template <class T>
+using NumOf = typename std::conditional<sizeof(T) == 8, ddf, float>::type;
+
 
 // One axis of the loader: the neighbour offsets of this cell along the axis (wrapped
 // when periodic; 0 past a wall, where the mirrored ghost of the boundary cell is read)
@@ -72,12 +120,18 @@ template <class T, bool PX, bool PY, bool PZ>
 __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* __restrict__ u3,
                                                          const T* __restrict__ p, const T* ad_prev,
                                                          T* __restrict__ ustar, T* ad_out) {
+  using N = NumOf<T>;
+  using X = Num<N>;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const size_t sy = (size_t)nx, sz = (size_t)nx * ny, N = sz * nz;
+  const size_t sy = (size_t)nx, sz = (size_t)nx * ny, Ncell = sz * nz;
   const T* __restrict__ U = u3;
-  const T* __restrict__ V = u3 + N;
-  const T* __restrict__ W = u3 + 2 * N;
-  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+  const T* __restrict__ V = u3 + Ncell;
+  const T* __restrict__ W = u3 + 2 * Ncell;
+  const N idx = X::in(a.idx), idy = X::in(a.idy), idx2 = X::in(a.idx2), idy2 = X::in(a.idy2);
+  const N qx = X::in(a.qx), qy = X::in(a.qy), nu = X::in(a.nu), dt = X::in(a.dt);
+  const N alpha = X::in(a.alpha), beta = X::in(a.beta), gamma = X::in(a.gamma);
+  const bool use_prev = a.beta != (T)0;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < Ncell; g += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(g % nx);
     const size_t t = g / nx;
     const int j = (int)(t % ny), k = (int)(t / ny);
@@ -88,97 +142,102 @@ __global__ void __launch_bounds__(256) ns_predict_kernel(NsArgs<T> a, const T* _
     // end is the mirrored ghost (−1 times the boundary cell) for a tangential component
     // and 0 for the normal one (the implicit top wall face), and the normal component's
     // own wall face 0 is 0.
-    auto ld = [&](const T* __restrict__ C, int ca, int ox, int oy, int oz) -> T {
+    auto ld = [&](const T* __restrict__ C, int ca, int ox, int oy, int oz) -> N {
       const long off = (ox < 0 ? ax_x.om : ox > 0 ? ax_x.op : 0) + (oy < 0 ? ax_y.om : oy > 0 ? ax_y.op : 0) +
                        (oz < 0 ? ax_z.om : oz > 0 ? ax_z.op : 0);
       int s = 1;
       const bool keep = nb_rule<PX>(ax_x, ca == 0, ox, s) && nb_rule<PY>(ax_y, ca == 1, oy, s) &&
                         nb_rule<PZ>(ax_z, ca == 2, oz, s);
-      if (!keep) return (T)0;
-      const T v = C[(long)g + off];
+      if (!keep) return X::zero();
+      const N v = X::in(C[(long)g + off]);
       return s < 0 ? -v : v;
     };
     const bool wall_u = !PX && i == 0, wall_v = !PY && j == 0, wall_w = !PZ && k == 0;
-    const T idzf = a.idzf[k];
+    const N idzf = X::in(a.idzf[k]);
     // 1/(centre distance) below and above cell k; walls: the ghost sits one Δz^f away
-    const T ihdn = (k > 0) ? a.idzc[k] : (PZ ? a.idzc[0] : a.idzf[0]);
-    const T ihup = (k + 1 < nz) ? a.idzc[k + 1] : (PZ ? a.idzc[0] : a.idzf[nz - 1]);
-    const T idzf_m = a.idzf[k > 0 ? k - 1 : nz - 1];
-    const T uc = ld(U, 0, 0, 0, 0), vc = ld(V, 1, 0, 0, 0), wc = ld(W, 2, 0, 0, 0);
+    const N ihdn = X::in((k > 0) ? a.idzc[k] : (PZ ? a.idzc[0] : a.idzf[0]));
+    const N ihup = X::in((k + 1 < nz) ? a.idzc[k + 1] : (PZ ? a.idzc[0] : a.idzf[nz - 1]));
+    const N idzf_m = X::in(a.idzf[k > 0 ? k - 1 : nz - 1]);
+    const N qz = X::scale(idzf, 0.25f), qzc = X::scale(ihdn, 0.25f);
+    const N uc = ld(U, 0, 0, 0, 0), vc = ld(V, 1, 0, 0, 0), wc = ld(W, 2, 0, 0, 0);
+    const N uc2 = X::scale(uc, 2.f), vc2 = X::scale(vc, 2.f), wc2 = X::scale(wc, 2.f);
 
     // Every flux below is a product of two sums of neighbours (an average each): the two
     // factors ½ go into one factor ¼ on the flux difference (q* = ¼/Δ), and the normal
     // term d(ū²) = ((a + b)² − (c + a)²)/4 is formed as (b − c)(b + 2a + c)/4.
     // ---------------- x momentum at x face i ----------------
-    T adu = (T)0;
+    N adu = X::zero();
     if (!wall_u) {
-      const T uxp = ld(U, 0, 1, 0, 0), uxm = ld(U, 0, -1, 0, 0);
-      const T uyp = ld(U, 0, 0, 1, 0), uym = ld(U, 0, 0, -1, 0);
-      const T uzp = ld(U, 0, 0, 0, 1), uzm = ld(U, 0, 0, 0, -1);
-      const T duu = (uxp - uxm) * (uxp + 2 * uc + uxm) * a.qx;
+      const N uxp = ld(U, 0, 1, 0, 0), uxm = ld(U, 0, -1, 0, 0);
+      const N uyp = ld(U, 0, 0, 1, 0), uym = ld(U, 0, 0, -1, 0);
+      const N uzp = ld(U, 0, 0, 0, 1), uzm = ld(U, 0, 0, 0, -1);
+      const N duu = (uxp - uxm) * (uxp + uc2 + uxm) * qx;
       // uv on the y faces j and j+1 of this x face
-      const T uv0 = (uc + uym) * (vc + ld(V, 1, -1, 0, 0));
-      const T uv1 = (uyp + uc) * (ld(V, 1, 0, 1, 0) + ld(V, 1, -1, 1, 0));
-      const T duv = (uv1 - uv0) * a.qy;
+      const N uv0 = (uc + uym) * (vc + ld(V, 1, -1, 0, 0));
+      const N uv1 = (uyp + uc) * (ld(V, 1, 0, 1, 0) + ld(V, 1, -1, 1, 0));
+      const N duv = (uv1 - uv0) * qy;
       // uw on the z faces k and k+1 of this x face
-      const T uw0 = (uc + uzm) * (wc + ld(W, 2, -1, 0, 0));
-      const T uw1 = (uzp + uc) * (ld(W, 2, 0, 0, 1) + ld(W, 2, -1, 0, 1));
-      const T duw = (uw1 - uw0) * ((T)0.25 * idzf);
-      const T lap = (uxp - 2 * uc + uxm) * a.idx2 + (uyp - 2 * uc + uym) * a.idy2 +
+      const N uw0 = (uc + uzm) * (wc + ld(W, 2, -1, 0, 0));
+      const N uw1 = (uzp + uc) * (ld(W, 2, 0, 0, 1) + ld(W, 2, -1, 0, 1));
+      const N duw = (uw1 - uw0) * qz;
+      const N lap = (uxp - uc2 + uxm) * idx2 + (uyp - uc2 + uym) * idy2 +
                     ((uzp - uc) * ihup - (uc - uzm) * ihdn) * idzf;
-      adu = a.nu * lap - (duu + duv + duw);
+      adu = nu * lap - (duu + duv + duw);
     }
     // ---------------- y momentum at y face j ----------------
-    T adv = (T)0;
+    N adv = X::zero();
     if (!wall_v) {
-      const T vxp = ld(V, 1, 1, 0, 0), vxm = ld(V, 1, -1, 0, 0);
-      const T vyp = ld(V, 1, 0, 1, 0), vym = ld(V, 1, 0, -1, 0);
-      const T vzp = ld(V, 1, 0, 0, 1), vzm = ld(V, 1, 0, 0, -1);
-      const T dvv = (vyp - vym) * (vyp + 2 * vc + vym) * a.qy;
+      const N vxp = ld(V, 1, 1, 0, 0), vxm = ld(V, 1, -1, 0, 0);
+      const N vyp = ld(V, 1, 0, 1, 0), vym = ld(V, 1, 0, -1, 0);
+      const N vzp = ld(V, 1, 0, 0, 1), vzm = ld(V, 1, 0, 0, -1);
+      const N dvv = (vyp - vym) * (vyp + vc2 + vym) * qy;
       // uv on the x faces i and i+1 of this y face
-      const T uv0 = (uc + ld(U, 0, 0, -1, 0)) * (vc + vxm);
-      const T uv1 = (ld(U, 0, 1, 0, 0) + ld(U, 0, 1, -1, 0)) * (vxp + vc);
-      const T duv = (uv1 - uv0) * a.qx;
-      const T vw0 = (vc + vzm) * (wc + ld(W, 2, 0, -1, 0));
-      const T vw1 = (vzp + vc) * (ld(W, 2, 0, 0, 1) + ld(W, 2, 0, -1, 1));
-      const T dvw = (vw1 - vw0) * ((T)0.25 * idzf);
-      const T lap = (vxp - 2 * vc + vxm) * a.idx2 + (vyp - 2 * vc + vym) * a.idy2 +
+      const N uv0 = (uc + ld(U, 0, 0, -1, 0)) * (vc + vxm);
+      const N uv1 = (ld(U, 0, 1, 0, 0) + ld(U, 0, 1, -1, 0)) * (vxp + vc);
+      const N duv = (uv1 - uv0) * qx;
+      const N vw0 = (vc + vzm) * (wc + ld(W, 2, 0, -1, 0));
+      const N vw1 = (vzp + vc) * (ld(W, 2, 0, 0, 1) + ld(W, 2, 0, -1, 1));
+      const N dvw = (vw1 - vw0) * qz;
+      const N lap = (vxp - vc2 + vxm) * idx2 + (vyp - vc2 + vym) * idy2 +
                     ((vzp - vc) * ihup - (vc - vzm) * ihdn) * idzf;
-      adv = a.nu * lap - (duv + dvv + dvw);
+      adv = nu * lap - (duv + dvv + dvw);
     }
     // ---------------- z momentum at z face k ----------------
-    T adw = (T)0;
+    N adw = X::zero();
     if (!wall_w) {
-      const T wzp = ld(W, 2, 0, 0, 1), wzm = ld(W, 2, 0, 0, -1);
-      const T wxp = ld(W, 2, 1, 0, 0), wxm = ld(W, 2, -1, 0, 0);
-      const T wyp = ld(W, 2, 0, 1, 0), wym = ld(W, 2, 0, -1, 0);
-      const T dww = (wzp - wzm) * (wzp + 2 * wc + wzm) * ((T)0.25 * ihdn);
+      const N wzp = ld(W, 2, 0, 0, 1), wzm = ld(W, 2, 0, 0, -1);
+      const N wxp = ld(W, 2, 1, 0, 0), wxm = ld(W, 2, -1, 0, 0);
+      const N wyp = ld(W, 2, 0, 1, 0), wym = ld(W, 2, 0, -1, 0);
+      const N dww = (wzp - wzm) * (wzp + wc2 + wzm) * qzc;
       // uw on the x faces i and i+1 of this z face (u averaged over cells k−1 and k)
-      const T uw0 = (uc + ld(U, 0, 0, 0, -1)) * (wc + wxm);
-      const T uw1 = (ld(U, 0, 1, 0, 0) + ld(U, 0, 1, 0, -1)) * (wxp + wc);
-      const T duw = (uw1 - uw0) * a.qx;
-      const T vw0 = (vc + ld(V, 1, 0, 0, -1)) * (wc + wym);
-      const T vw1 = (ld(V, 1, 0, 1, 0) + ld(V, 1, 0, 1, -1)) * (wyp + wc);
-      const T dvw = (vw1 - vw0) * a.qy;
-      const T lap = (wxp - 2 * wc + wxm) * a.idx2 + (wyp - 2 * wc + wym) * a.idy2 +
+      const N uw0 = (uc + ld(U, 0, 0, 0, -1)) * (wc + wxm);
+      const N uw1 = (ld(U, 0, 1, 0, 0) + ld(U, 0, 1, 0, -1)) * (wxp + wc);
+      const N duw = (uw1 - uw0) * qx;
+      const N vw0 = (vc + ld(V, 1, 0, 0, -1)) * (wc + wym);
+      const N vw1 = (ld(V, 1, 0, 1, 0) + ld(V, 1, 0, 1, -1)) * (wyp + wc);
+      const N dvw = (vw1 - vw0) * qy;
+      const N lap = (wxp - wc2 + wxm) * idx2 + (wyp - wc2 + wym) * idy2 +
                     ((wzp - wc) * idzf - (wc - wzm) * idzf_m) * ihdn;
-      adw = a.nu * lap - (duw + dvw + dww);
+      adw = nu * lap - (duw + dvw + dww);
     }
 
     // ---------------- predictor (2a) ----------------
-    const T pc = p[g];
-    const T gpx = wall_u ? (T)0 : (pc - p[g + (i > 0 ? -1 : nx - 1)]) * a.idx;
-    const T gpy = wall_v ? (T)0 : (pc - p[g + (j > 0 ? -(long)sy : (long)((ny - 1) * sy))]) * a.idy;
-    const T gpz = wall_w ? (T)0 : (pc - p[g + (k > 0 ? -(long)sz : (long)((nz - 1) * sz))]) * ihdn;
-    const T bu = a.beta != (T)0 ? ad_prev[g] : (T)0;
-    const T bv = a.beta != (T)0 ? ad_prev[g + N] : (T)0;
-    const T bw = a.beta != (T)0 ? ad_prev[g + 2 * N] : (T)0;
-    ustar[g] = wall_u ? U[g] : uc + a.dt * (a.alpha * adu + a.beta * bu - a.gamma * gpx);
-    ustar[g + N] = wall_v ? V[g] : vc + a.dt * (a.alpha * adv + a.beta * bv - a.gamma * gpy);
-    ustar[g + 2 * N] = wall_w ? W[g] : wc + a.dt * (a.alpha * adw + a.beta * bw - a.gamma * gpz);
-    ad_out[g] = adu;
-    ad_out[g + N] = adv;
-    ad_out[g + 2 * N] = adw;
+    const N pc = X::in(p[g]);
+    const N gpx = wall_u ? X::zero() : (pc - X::in(p[g + (i > 0 ? -1 : nx - 1)])) * idx;
+    const N gpy = wall_v ? X::zero() : (pc - X::in(p[g + (j > 0 ? -(long)sy : (long)((ny - 1) * sy))])) * idy;
+    const N gpz = wall_w ? X::zero() : (pc - X::in(p[g + (k > 0 ? -(long)sz : (long)((nz - 1) * sz))])) * ihdn;
+    N incu = alpha * adu - gamma * gpx, incv = alpha * adv - gamma * gpy, incw = alpha * adw - gamma * gpz;
+    if (use_prev) {
+      incu = incu + beta * X::in(ad_prev[g]);
+      incv = incv + beta * X::in(ad_prev[g + Ncell]);
+      incw = incw + beta * X::in(ad_prev[g + 2 * Ncell]);
+    }
+    ustar[g] = wall_u ? U[g] : U[g] + X::out(dt * incu);
+    ustar[g + Ncell] = wall_v ? V[g] : V[g] + X::out(dt * incv);
+    ustar[g + 2 * Ncell] = wall_w ? W[g] : W[g] + X::out(dt * incw);
+    ad_out[g] = X::out(adu);
+    ad_out[g + Ncell] = X::out(adv);
+    ad_out[g + 2 * Ncell] = X::out(adw);
   }
 }
 
