@@ -37,49 +37,12 @@ namespace ps {
 namespace {
 
 // ---- the arithmetic of the predictor ------------------------------------------------
-// FP32 fields are evaluated in float. FP64 fields are evaluated in double-float (ddf:
-// an unevaluated sum hi + lo of two floats, ~48 significant bits, with the TwoSum and
-// FMA-product arithmetic of common.cuh): an FP64 operation issues at 1/64 of the FP32
-// rate on this part, so the ~110 operations per cell of the predictor kept the FP64
-// pipe saturated (86 %) while HBM idled. The FP64 inputs are split on their bit
-// patterns (no FP64 instruction); only the outputs are formed in FP64: AD^k rounded
-// once, and u* = u^k + (its increment) with one FP64 add.
-struct ddf {
-  float h, l;
-};
-__device__ __forceinline__ ddf operator+(ddf a, ddf b) {
-  const df r = df_add(df{a.h, a.l}, df{b.h, b.l});
-  return {r.h, r.l};
-}
-__device__ __forceinline__ ddf operator-(ddf a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ ddf operator-(ddf a, ddf b) { return a + (-b); }
-__device__ __forceinline__ ddf operator*(ddf a, ddf b) {
-  const df r = df_mul(df{a.h, a.l}, df{b.h, b.l});
-  return {r.h, r.l};
-}
-template <class N>
-struct Num;
-template <>
-struct Num<float> {
-  static __device__ __forceinline__ float in(float x) { return x; }
-  static __device__ __forceinline__ float out(float x) { return x; }
-  static __device__ __forceinline__ float zero() { return 0.f; }
-  static __device__ __forceinline__ float scale(float x, float pow2) { return x * pow2; }
-};
-template <>
-struct Num<ddf> {
-  static __device__ __forceinline__ ddf in(double x) {
-    ddf r;
-    split_f64(x, r.h, r.l);
-    return r;
-  }
-  static __device__ __forceinline__ double out(ddf x) { return widen_f32(x.h) + widen_f32(x.l); }
-  static __device__ __forceinline__ ddf zero() { return {0.f, 0.f}; }
-  static __device__ __forceinline__ ddf scale(ddf x, float pow2) { return {x.h * pow2, x.l * pow2}; }  // exact
-};
-// the number type of the predictor for fields of type T
-template <class T>
-using NumOf = typename std::conditional<sizeof(T) == 8, ddf, float>::type;
+// FP32 fields are evaluated in float, FP64 fields in double-float (NumOf, common.cuh):
+// an FP64 operation issues at 1/64 of the FP32 rate on this part, so the ~110
+// operations per cell of the predictor kept the FP64 pipe saturated (86 %) while HBM
+// idled. The FP64 inputs are split on their bit patterns (no FP64 instruction); only
+// the outputs are formed in FP64: AD^k rounded once, and u* = u^k + (its increment)
+// with one FP64 add.
 
 
 // One axis of the loader: the neighbour offsets of this cell along the axis (wrapped
