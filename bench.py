@@ -96,6 +96,13 @@ FP64_FLOPS_PER_POINT = 126      # plain FP64 solve at n = 1024 (see the fp64_sol
 #   AD = −adv + ν·lap: 3; predictor u* = u + Δt(α AD + β AD' − γ G p) with the
 #     pressure gradient difference: 3 × 6                              3 + 18      = 21
 NS_FLOPS_PER_CELL = 108
+# The predictor on FP64 fields runs in double-float (pairs of floats) on the FP32 pipe, so
+# its binding unit is FP32 instruction issue: thread instructions per cell from ncu
+# (smsp__inst_executed.sum × 32 / cells of one launch, ns_predict_kernel<double, 1, 1, 0>
+# on 512x256x64, profiles/kernels_rk3_512x256x64.md), against the issue peak of
+# 152 SMs × 4 schedulers × 32 lanes per clock.
+NS_PRED_INST_PER_CELL = 2380
+FP32_LANES_PER_SM = 128
 NUM_SMS_GB300 = 152
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64
 
@@ -595,16 +602,24 @@ def bench_ours(args):
         cells5 = n5[0] * n5[1] * n5[2]
         pl5, pa5, _, pm5 = prof5["ns_predict"]
         pred_ms = pm5 / max(pa5, 1)
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        issue_peak = NUM_SMS_GB300 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # T thread-inst/s
+        inst_rate = NS_PRED_INST_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12
+        f64eq = NS_FLOPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12
         ns = {"value": job_rate(world, n5[0] * n5[1] * n5[2], ms5), "unit": "Mpts/s (cells x RK3 steps)",
               "ms_per_rk3_step": ms5, "grid": list(n5), "last_solve_status": i5.status,
-              # the fused predictor is bound by the FP64 pipe: its algorithmic flops (the
-              # stencils' count, NS_FLOPS_PER_CELL) against the measured FP64 FMA rate
-              "roofline": {"bound": "fp64", "kernel": "ns_predict", "flops_per_cell": NS_FLOPS_PER_CELL,
-                           "avg_launch_ms": pred_ms,
-                           "achieved": NS_FLOPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12,
-                           "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
-                           "peak_source": fp64_peak["source"],
-                           "frac": NS_FLOPS_PER_CELL * cells5 / (pred_ms * 1e-3) / 1e12 / fp64_peak["tflops"]},
+              # the fused predictor (double-float arithmetic on FP64 fields) is bound by FP32
+              # instruction issue: ncu's instructions per cell against the issue peak
+              "roofline": {"bound": "alu", "kernel": "ns_predict", "avg_launch_ms": pred_ms,
+                           "inst_per_cell": NS_PRED_INST_PER_CELL, "achieved": inst_rate,
+                           "peak": issue_peak, "unit": "T thread-inst/s",
+                           "peak_source": f"{NUM_SMS_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
+                                          "(median SM clock of the main timed region)",
+                           "frac": inst_rate / issue_peak,
+                           # the same launch as FP64-accurate flops (the stencils' count)
+                           "fp64_equivalent": {"flops_per_cell": NS_FLOPS_PER_CELL, "tflops": f64eq,
+                                               "native_fp64_peak_tflops": fp64_peak["tflops"],
+                                               "frac_of_native_fp64": f64eq / fp64_peak["tflops"]}},
               "kernels_ms_per_step": {k: v[3] / k5 for k, v in prof5.items() if v[0]},
               "last_solve_rel_residual": i5.rel_residual,
               "workload": "3 substeps of ps_ns_substep (predictor, divergence, refined solve to 1e-10, "

@@ -170,6 +170,10 @@ struct NsArgs {
   const T* idzf;
   const T* idzc;
   T nu, dt, alpha, beta, gamma;
+  // FP64 fields: idx, idy, idx2, idy2, qx, qy, nu, dt, alpha, beta, gamma split into
+  // hi + lo floats on the host (the predictor's double-float constants, read as
+  // operands from the parameter bank instead of held in registers)
+  float2 dc[11];
 };
 template <class T>
 cudaError_t launch_ns_predict(const NsArgs<T>& a, const void* u3, const void* p, const void* ad_prev,

@@ -1281,6 +1281,14 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
     a.alpha = (T)al;
     a.beta = (T)be;
     a.gamma = (T)ga;
+    {
+      const double c[11] = {1.0 / plan->dx, 1.0 / plan->dy, 1.0 / (plan->dx * plan->dx),
+                            1.0 / (plan->dy * plan->dy), 0.25 / plan->dx, 0.25 / plan->dy, nu, dt, al, be, ga};
+      for (int q = 0; q < 11; ++q) {
+        const float h = (float)c[q];
+        a.dc[q] = make_float2(h, (float)(c[q] - (double)h));
+      }
+    }
     cudaError_t e;
     if ((e = run(plan, K_NSPRED, st, [&] { return launch_ns_predict<T>(a, u, p, ad, ustar, ad, st); })) !=
         cudaSuccess)
