@@ -153,7 +153,7 @@ __device__ __forceinline__ int mk(int j, int n, int m) { return j < m ? 2 * j : 
 // global memory: the only shared buffer is the complex exchange of the FFT. All
 // reads of a line happen before the first stage's barrier and all writes after
 // the last, so in == out is safe.
-template <class T, class TI, class TO, int M, bool FWD>
+template <class T, class TI, class TO, int M, bool FWD, int OM>
 __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG_THREADS) / LShape<M>::NT)
     xform_long_kernel(FastArgs<T> a) {
   using S = LShape<M>;
@@ -196,34 +196,29 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
         return {ld_cvt<T, TI>::f(q.x) * sci, ld_cvt<T, TI>::f(q.y) * sci};
       }
     };
-    // one output value at position e of the line, with the output modes of the row
-    // kernels (plane scale; FP64 out with a widened FP32 base or accumulation, the
-    // FP32 copy, the max-abs of the new values; or plain / accumulated T)
+    // one output value at position e of the line, in the output mode OM of the row
+    // kernels (plane scale; FP64 out: stored, accumulated, or a widened FP32 base plus
+    // the value, or none, with the FP32 copy and the max-abs of the new values; T out:
+    // stored or accumulated). The mode is a template argument, so each instance
+    // carries only its own store path.
     auto emit = [&](int e, T val) {
       const size_t g = g0 + e;
       const T vs = val * sco;
       if constexpr (sizeof(TO) == 8) {
         const TO d = st_cvt<TO, T>::f(vs);
         amax = max(amax, (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull);
-        if (out) {
-          TO x = d;
-          if constexpr (sizeof(T) == 4) {
-            if (a.base32) x = widen_f32(a.base32[g]) + d;
-            else if (a.accumulate) x = out[g] + d;
-          } else if (a.accumulate) {
-            x = out[g] + d;
-          }
-          out[g] = x;
-        }
+        if constexpr (OM == row::OM_BASE && sizeof(T) == 4) out[g] = widen_f32(a.base32[g]) + d;
+        else if constexpr (OM == row::OM_ACC) out[g] = out[g] + d;
+        else if constexpr (OM == row::OM_STORE) out[g] = d;
         if constexpr (sizeof(T) == 4)
           if (a.out2) a.out2[g] = vs;
       } else {
         TO x = st_cvt<TO, T>::f(vs);
-        if (a.accumulate) x = out[g] + x;
+        if constexpr (OM == row::OM_ACC) x = out[g] + x;
         __stcs(out + g, x);
       }
     };
-    // two consecutive output values (e even): the same modes with 8- and 16-byte accesses
+    // two consecutive output values (e even): the same with 8- and 16-byte accesses
     auto emit2 = [&](int e, T val0, T val1) {
       const size_t g = g0 + e;
       const T s0 = val0 * sco, s1 = val1 * sco;
@@ -231,33 +226,25 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
         const TO d0 = st_cvt<TO, T>::f(s0), d1 = st_cvt<TO, T>::f(s1);
         amax = max(amax, max((unsigned long long)__double_as_longlong(d0) & 0x7FFFFFFFFFFFFFFFull,
                              (unsigned long long)__double_as_longlong(d1) & 0x7FFFFFFFFFFFFFFFull));
-        if (out) {
-          TO x0 = d0, x1 = d1;
-          bool acc = a.accumulate != 0;
-          if constexpr (sizeof(T) == 4) {
-            if (a.base32) {
-              const float2 q = *reinterpret_cast<const float2*>(a.base32 + g);
-              x0 = widen_f32(q.x) + d0;
-              x1 = widen_f32(q.y) + d1;
-              acc = false;
-            }
-          }
-          if (acc) {
-            const double2 q = *reinterpret_cast<const double2*>(out + g);
-            x0 = q.x + d0;
-            x1 = q.y + d1;
-          }
-          *reinterpret_cast<double2*>(out + g) = make_double2(x0, x1);
+        if constexpr (OM == row::OM_BASE && sizeof(T) == 4) {
+          const float2 q = *reinterpret_cast<const float2*>(a.base32 + g);
+          *reinterpret_cast<double2*>(out + g) = make_double2(widen_f32(q.x) + d0, widen_f32(q.y) + d1);
+        } else if constexpr (OM == row::OM_ACC) {
+          const double2 q = *reinterpret_cast<const double2*>(out + g);
+          *reinterpret_cast<double2*>(out + g) = make_double2(q.x + d0, q.y + d1);
+        } else if constexpr (OM == row::OM_STORE) {
+          *reinterpret_cast<double2*>(out + g) = make_double2(d0, d1);
         }
         if constexpr (sizeof(T) == 4)
           if (a.out2) *reinterpret_cast<float2*>(a.out2 + g) = make_float2(s0, s1);
       } else {
         TO x0 = st_cvt<TO, T>::f(s0), x1 = st_cvt<TO, T>::f(s1);
-        if (a.accumulate) {
+        if constexpr (OM == row::OM_ACC) {
           x0 = out[g] + x0;
           x1 = out[g + 1] + x1;
         }
-        __stcs(reinterpret_cast<float2*>(out + g), make_float2(x0, x1));
+        if constexpr (sizeof(TO) == 4) __stcs(reinterpret_cast<float2*>(out + g), make_float2(x0, x1));
+        else __stcs(reinterpret_cast<double2*>(out + g), make_double2(x0, x1));
       }
     };
     cplx<T> v[E];
@@ -461,10 +448,11 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ sr
 
 }  // namespace lng
 
-template <class T, class TI, class TO, int M, bool FWD>
-cudaError_t launch_xform_long(FastArgs<T> a, cudaStream_t st) {
+namespace {
+template <class T, class TI, class TO, int M, bool FWD, int OM>
+cudaError_t launch_long_mode(FastArgs<T> a, cudaStream_t st) {
   using S = lng::LShape<M>;
-  auto k = lng::xform_long_kernel<T, TI, TO, M, FWD>;
+  auto k = lng::xform_long_kernel<T, TI, TO, M, FWD, OM>;
   constexpr size_t smem = lng::long_smem<T, M>();
   static int bps = 0;
   if (bps == 0) {
@@ -481,6 +469,18 @@ cudaError_t launch_xform_long(FastArgs<T> a, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
   k<<<grid, S::NT, smem, st>>>(a);
   return cudaGetLastError();
+}
+}  // namespace
+
+// the output mode from the arguments, as for the row kernels
+template <class T, class TI, class TO, int M, bool FWD>
+cudaError_t launch_xform_long(FastArgs<T> a, cudaStream_t st) {
+  if constexpr (!FWD && sizeof(TO) == 8 && sizeof(T) == 4) {
+    if (a.base32) return launch_long_mode<T, TI, TO, M, FWD, row::OM_BASE>(a, st);
+    if (!a.out) return launch_long_mode<T, TI, TO, M, FWD, row::OM_NONE>(a, st);
+  }
+  if (a.accumulate) return launch_long_mode<T, TI, TO, M, FWD, row::OM_ACC>(a, st);
+  return launch_long_mode<T, TI, TO, M, FWD, row::OM_STORE>(a, st);
 }
 
 template <class T>
