@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
   // no __restrict__: in and out may be the same array
   const TI* in = static_cast<const TI*>(a.in);
   TO* out = static_cast<TO*>(a.out);
-  unsigned long long amax = 0;
+  T tmax = (T)0;  // max |new value| before widening (the bits of its widening order as the values)
   for (int ln = blockIdx.x; ln < a.nlines; ln += gridDim.x) {
     const size_t g0 = (size_t)ln * N;
     const int z = ln / a.ny;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
       const T vs = val * sco;
       if constexpr (sizeof(TO) == 8) {
         const TO d = st_cvt<TO, T>::f(vs);
-        amax = max(amax, (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull);
+        tmax = fmax(tmax, fabs(vs));
         if constexpr (OM == row::OM_BASE && sizeof(T) == 4) out[g] = widen_f32(a.base32[g]) + d;
         else if constexpr (OM == row::OM_ACC) out[g] = out[g] + d;
         else if constexpr (OM == row::OM_STORE) out[g] = d;
@@ -224,8 +224,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
       const T s0 = val0 * sco, s1 = val1 * sco;
       if constexpr (sizeof(TO) == 8) {
         const TO d0 = st_cvt<TO, T>::f(s0), d1 = st_cvt<TO, T>::f(s1);
-        amax = max(amax, max((unsigned long long)__double_as_longlong(d0) & 0x7FFFFFFFFFFFFFFFull,
-                             (unsigned long long)__double_as_longlong(d1) & 0x7FFFFFFFFFFFFFFFull));
+        tmax = fmax(tmax, fmax(fabs(s0), fabs(s1)));
         if constexpr (OM == row::OM_BASE && sizeof(T) == 4) {
           const float2 q = *reinterpret_cast<const float2*>(a.base32 + g);
           *reinterpret_cast<double2*>(out + g) = make_double2(widen_f32(q.x) + d0, widen_f32(q.y) + d1);
@@ -401,7 +400,8 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
   }
   if constexpr (sizeof(TO) == 8) {
     if (a.amax) {
-      for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      for (int o = 16; o > 0; o >>= 1) tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+      const unsigned long long amax = (unsigned long long)__double_as_longlong(st_cvt<double, T>::f(tmax));
       if ((threadIdx.x & 31) == 0 && amax) atomicMax(a.amax, amax);
     }
   }
