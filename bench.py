@@ -428,11 +428,23 @@ def bench_ours(args):
             ie = plan.solve_host(fh, ph, f, p)
             per_call.append(time.perf_counter() - tc)
         t_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e)
+        # the host link alone: the same pinned buffers copied in and out (no solve), as many
+        # times, so that the spread of the calls can be set against the spread of the copies
+        per_copy = []
+        for _ in range(k_e2e):
+            tc = time.perf_counter()
+            f.copy_(fh, non_blocking=True)
+            ph.copy_(p, non_blocking=True)
+            torch.cuda.synchronize()
+            per_copy.append(time.perf_counter() - tc)
         e2e = {"value": job_rate(world, N, t_e2e * 1e3), "unit": "Mpts/s",
                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8 + 32,
                "ms_per_step": t_e2e * 1e3, "calls": k_e2e, "ms_min": min(per_call) * 1e3,
                "ms_max": max(per_call) * 1e3, "ms_median": statistics.median(per_call) * 1e3,
-               "status": ie.status}
+               "status": ie.status,
+               "copies_only": {"what": "f host->device then p device->host, pinned, no solve",
+                               "ms_min": min(per_copy) * 1e3, "ms_median": statistics.median(per_copy) * 1e3,
+                               "ms_max": max(per_copy) * 1e3}}
         del fh, ph
 
     # ---- plain FP64 GPU solve of the same input (the comparison) ----

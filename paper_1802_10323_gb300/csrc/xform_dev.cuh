@@ -354,7 +354,7 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
   __syncthreads();
 
   // ---- 5. store ----------------------------------------------------------------------
-  unsigned long long amax = 0;
+  T tmax = (T)0;  // max |new value| before widening (a 64-bit integer max would use the FP64 pipe)
   for (int idx = threadIdx.x; idx < L * n; idx += blockDim.x) {
     int l, e, z;
     size_t g;
@@ -383,7 +383,7 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
           out[g] = a.accumulate ? out[g] + x : x;
         }
       }
-      amax = max(amax, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+      tmax = fmax(tmax, fabs(v));
       if constexpr (sizeof(T) == 4)
         if (a.out2) a.out2[g] = v;
     } else {
@@ -392,7 +392,8 @@ __device__ void xform_group(const XformArgs<T>& a, int grp, unsigned char* smem_
   }
   if constexpr (sizeof(TO) == 8) {
     if (a.amax) {
-      for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      for (int o = 16; o > 0; o >>= 1) tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+      const unsigned long long amax = (unsigned long long)__double_as_longlong(st_cvt<double, T>::f(tmax));
       if ((threadIdx.x & 31) == 0 && amax) atomicMax(a.amax, amax);
     }
   }

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw) + LTab<T, M>::ENTRIES;  // [lpad(M) + 1]
   const int b = threadIdx.x;
   tb.fill(b, NT);
+  __syncthreads();  // the tables are complete before the first line's gather reads them
   const cplx<T> tw1 = a.tw[1];  // e^{−2πi/(8n)}: the ND post-twiddle is tw(4k)·tw1
   const int bc = a.bc;
   // no __restrict__: in and out may be the same array
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
         }
         v[r] = zz;
       }
-      __syncthreads();  // the tables are ready; the previous line's buffer reads are done
+      __syncthreads();  // the previous line's buffer reads are done
       fft_line<T, M, false, 0, 1>(v, buf, tb, b);
       // ---- post-processing: pair k with M − k through the complex buffer ----
       __syncthreads();
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
       }
     } else {
       // ---- backward pre-processing: reals → the M complex points (pairs k, M − k) ----
-      __syncthreads();  // the tables are ready; the previous line's buffer reads are done
+      __syncthreads();  // the previous line's buffer reads are done
       if (bc_iv(bc)) {
 #pragma unroll 4
         for (int k = b; k < M; k += NT) buf[lpad(k)] = cmul(cplx<T>{X(2 * k), X(N - 1 - 2 * k)}, tb.pp(1, k));
