@@ -100,3 +100,22 @@ def test_long_y_z_solve_on_transposed_planes(lib, shape, bcs, dx, dy, precision,
     if precision == "fp32_refine":
         rr = O.relative_residual(p, f, dx, dy, zf, *bcs)
         assert info.status == 0 and rr <= 1e-10 and abs(info.rel_residual - rr) <= 1e-11, (info.rel_residual, rr)
+
+
+@pytest.mark.parametrize("bcx", ["DN", "ND"])
+def test_long_lines_first_line_of_every_cta(lib, bcx):
+    """Eight x lines of 4096, so each CTA of the long-line kernel does one line and every
+    line is its CTA's first: the forward gather of the DCT-IV family reads the shared
+    twiddle tables right after they are filled. Twenty solves, each against the oracle
+    (a missing barrier there gave wrong first lines now and then)."""
+    import torch
+    shape, bcs = (2, 4, 4096), (bcx, "P", "P")
+    zf = synth.uniform_faces(2, 1.0)
+    f = np.random.default_rng(11).uniform(-1, 1, shape)
+    q = S.solve(f, 4.0 / 4096, 1.0, zf, *bcs)
+    plan = lib.Plan(4096, 4, 2, 4.0 / 4096, 1.0, zf=zf, bcs=bcs, precision="fp32")
+    ft = torch.as_tensor(f, dtype=torch.float32, device="cuda").contiguous()
+    for _ in range(20):
+        p = plan.solve(ft).double().cpu().numpy()
+        assert _relerr(p, q) <= 2e-5
+    plan.close()
