@@ -139,13 +139,14 @@ ps_status ps_plan_create_helmholtz(ps_plan** out, int nx, int ny, int nz, double
 ps_status ps_workspace_bytes(const ps_plan* plan, size_t* bytes);
 
 /* Solve A·p = f (Eq. 4) for FP64 fields (plans with PS_FP64 or
- * PS_FP32_REFINE). f, p: device arrays of nx·ny·nz doubles; p == f (in place)
- * is allowed for PS_FP64 only. ws: workspace of ps_workspace_bytes. stream:
+ * PS_FP32_REFINE). f, p: device arrays of nx·ny·nz doubles, each 16-byte aligned
+ * (the transforms move lines with 16-byte accesses; PS_INVALID_ARG otherwise);
+ * p == f (in place) is allowed for PS_FP64 only. ws: workspace of ps_workspace_bytes. stream:
  * cudaStream_t as void*. info: device ps_info (may be NULL). */
 ps_status ps_solve(ps_plan* plan, const double* f, double* p, void* ws, void* stream,
                    ps_info* info);
 
-/* Same for FP32 fields (plans with PS_FP32). p == f allowed. */
+/* Same for FP32 fields (plans with PS_FP32), f and p 16-byte aligned. p == f allowed. */
 ps_status ps_solve_f32(ps_plan* plan, const float* f, float* p, void* ws, void* stream,
                        ps_info* info);
 
@@ -230,7 +231,8 @@ const char* ps_last_error(const ps_plan* plan);
  * The byte ranges of u, ustar, ad, p, phi, rhs and ws must be pairwise disjoint
  * (PS_INVALID_ARG naming the overlapping pair otherwise).
  * Field types follow the plan (float for PS_FP32, double otherwise); device
- * pointers; enqueued on the stream (four kernels and the solve). */
+ * pointers, each 16-byte aligned (PS_INVALID_ARG otherwise); enqueued on the
+ * stream (four kernels and the solve). */
 ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, void* ustar, void* ad, void* p,
                         void* phi, void* rhs, void* ws, void* stream, ps_info* info);
 

@@ -693,6 +693,8 @@ ps_status check_solve_args(ps_plan* p, const void* f, const void* out, const voi
   if (!f || !out) return fail(p, PS_INVALID_ARG, "null field pointer");
   if (!ws) return fail(p, PS_INVALID_ARG, "null workspace");
   if (((uintptr_t)ws) & 255) return fail(p, PS_INVALID_ARG, "workspace must be 256-byte aligned");
+  // the transform kernels move lines with 16-byte vector accesses
+  if ((((uintptr_t)f) | ((uintptr_t)out)) & 15) return fail(p, PS_INVALID_ARG, "f and p must be 16-byte aligned");
   return PS_OK;
 }
 
@@ -1225,6 +1227,9 @@ ps_status ps_ns_substep(ps_plan* plan, int k, double dt, double nu, void* u, voi
                         void* phi, void* rhs, void* ws, void* stream, ps_info* info) {
   if (!plan) return fail(nullptr, PS_INVALID_ARG, "null plan");
   if (!u || !ustar || !ad || !p || !phi || !rhs || !ws) return fail(plan, PS_INVALID_ARG, "null pointer");
+  if ((((uintptr_t)u) | ((uintptr_t)ustar) | ((uintptr_t)ad) | ((uintptr_t)p) | ((uintptr_t)phi) |
+       ((uintptr_t)rhs)) & 15)
+    return fail(plan, PS_INVALID_ARG, "the substep's arrays must be 16-byte aligned");
   {
     // Every array is read and written at different stages (p += Φ reads phi, the
     // solve overwrites ws and phi, the divergence writes rhs from ustar), so any

@@ -120,3 +120,29 @@ def test_injected_allocation_failure_then_recovery(lib):
     q = S.solve(f, 0.1, 0.1, zf, "P", "P", "NN")
     assert np.abs(p.cpu().numpy() - q).max() <= 1e-12 * np.abs(q).max()
     plan.close()
+
+
+def test_misaligned_fields_are_refused(lib):
+    """f or p off a 16-byte boundary (the transforms move lines with 16-byte accesses) is
+    refused on the host with PS_INVALID_ARG before anything is launched; the plan then
+    solves aligned fields as before."""
+    import torch
+    zf = synth.uniform_faces(8, 1.0)
+    plan = lib.Plan(32, 32, 8, 1 / 32, 1 / 32, zf=zf, bcs=("P", "P", "NN"), precision="fp64")
+    N = 32 * 32 * 8
+    big = torch.zeros(N + 2, dtype=torch.float64, device="cuda")
+    ws = plan.workspace()
+    s = torch.cuda.current_stream().cuda_stream
+    for f_off, p_off in ((1, 0), (0, 1)):
+        fp = ctypes.c_void_p(big.data_ptr() + 8 * f_off)
+        pp = torch.empty(N + 2, dtype=torch.float64, device="cuda")
+        st = lib.ps_solve(plan.handle, fp, ctypes.c_void_p(pp.data_ptr() + 8 * p_off),
+                          ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(s), None)
+        assert st == lib.PS_INVALID_ARG
+    f = np.random.default_rng(3).uniform(-1, 1, (8, 32, 32))
+    f -= f.mean()
+    p = plan.solve(torch.as_tensor(f, device="cuda"))
+    torch.cuda.synchronize()
+    q = S.solve(f, 1 / 32, 1 / 32, zf, "P", "P", "NN")
+    assert np.abs(p.cpu().numpy() - q).max() <= 1e-12 * np.abs(q).max()
+    plan.close()
