@@ -51,7 +51,10 @@ BYTES_PER_POINT = {
                "y_bwd": 4 + 4, "x_bwd_f64store": 4 + 4, "x_bwd_f64base": 4 + 4 + 8 + 4,
                "x_bwd_f64acc": 4 + 8 + 8 + 4, "materialize": 4 + 8,
                "residual_first": 8 + 4 + 8, "residual_first3": 8 + 4 + 8, "residual": 8 + 4 + 8,
-               "residual_check": 8 + 4, "residual_out": 8 + 4 + 8, "residual_exact": 8 + 8 + 4},
+               "residual_check": 8 + 4, "residual_out": 8 + 4 + 8, "residual_exact": 8 + 8 + 4,
+               # plane transposes of long y lines (read and write FP32; traffic beyond the
+               # five-pass model, measured as its own kind)
+               "transpose": 4 + 4},
     "fp64": {"x_fwd": 16, "y_fwd": 16, "z_solve": 16, "y_bwd": 16, "x_bwd": 16},
 }
 

@@ -112,13 +112,13 @@ void split_df(double d, float2* out) {
 // x pass, its storing and accumulating x passes and its check-only residual).
 enum Kind { K_XF = 0, K_XF64IN, K_YF, K_Z, K_ZS, K_YB, K_XB, K_XB64ST, K_XB64ACC, K_RES, K_CHK,
             K_CTL, K_VER, K_RES0, K_RES3, K_XB64BASE, K_MAT, K_RESOUT, K_NSPRED, K_NSPROJ, K_NSPRES,
-            K_NKINDS };
+            K_TRANSP, K_NKINDS };
 static const char* kKindName[K_NKINDS] = {"x_fwd", "x_fwd_f64in", "y_fwd", "z_solve",
                                           "z_singular", "y_bwd", "x_bwd", "x_bwd_f64store",
                                           "x_bwd_f64acc", "residual", "residual_check", "control",
                                           "residual_exact", "residual_first", "residual_first3",
                                           "x_bwd_f64base", "materialize", "residual_out",
-                                          "ns_predict", "ns_projection", "ns_pressure"};
+                                          "ns_predict", "ns_projection", "ns_pressure", "transpose"};
 constexpr int kProfMax = 4096;
 
 struct Prof {
@@ -419,31 +419,6 @@ bool y_long(const ps_plan* p) {
   return (t.m == 1024 || t.m == 2048 || t.m == 4096) && t.bc != BC_FD;
 }
 
-// One y pass of the long kernel that leaves the planes transposed: forward,
-// data [n_z][n_y][n_x] → yt [n_z][n_x][n_y] transformed; backward, yt transformed
-// back in place and transposed into data. Between the two the z solve runs on yt
-// (zargs_t), so each solve moves the data through two plane transposes, not four.
-template <class T, bool FWD>
-cudaError_t y_long_pass(const ps_plan* p, T* data, T* yt, const int* skip, cudaStream_t st) {
-  const AxisTab& t = p->ay;
-  FastArgs<T> a{};
-  a.axis = 0;
-  a.bc = t.bc;
-  if constexpr (sizeof(T) == 8) a.tw = reinterpret_cast<const cplx<T>*>(t.tw64);
-  else a.tw = reinterpret_cast<const cplx<T>*>(t.tw32);
-  a.skip = skip;
-  a.nx = t.n;
-  a.nz = p->nz;
-  a.in = yt;
-  a.out = yt;
-  a.ny = p->nx;  // lines per plane
-  a.nlines = p->nx * p->nz;
-  cudaError_t e;
-  if (FWD && (e = launch_plane_transpose<T>(data, yt, p->ny, p->nx, p->nz, skip, st)) != cudaSuccess) return e;
-  if ((e = launch_long<T, T, T, FWD>(t.m, a, st)) != cudaSuccess) return e;
-  if (!FWD) return launch_plane_transpose<T>(yt, data, p->nx, p->ny, p->nz, skip, st);
-  return cudaSuccess;
-}
 
 
 // Launch `fn` on `st`, bracketed by profiling events when enabled on the plan.
@@ -459,6 +434,38 @@ cudaError_t run(ps_plan* pl, int kind, cudaStream_t st, F&& fn) {
     ++pr.n;
   }
   return e;
+}
+
+// One y pass. Long y lines (y_long): the one-line-per-CTA kernel on planes left
+// transposed — forward, data [n_z][n_y][n_x] → yt [n_z][n_x][n_y] and transformed;
+// backward, yt transformed in place and transposed back into data — so that the z
+// solve between them runs on yt (zargs_t) and each solve pays two plane transposes,
+// not four; the transposes are timed as their own kind. Otherwise `other`.
+template <class T, bool FWD, class F>
+cudaError_t y_pass(ps_plan* pl, Kind kind, bool yl, T* data, T* yt, const int* skip, cudaStream_t st, F&& other) {
+  if (!yl) return run(pl, kind, st, other);
+  const AxisTab& t = pl->ay;
+  FastArgs<T> a{};
+  a.axis = 0;
+  a.bc = t.bc;
+  if constexpr (sizeof(T) == 8) a.tw = reinterpret_cast<const cplx<T>*>(t.tw64);
+  else a.tw = reinterpret_cast<const cplx<T>*>(t.tw32);
+  a.skip = skip;
+  a.nx = t.n;
+  a.nz = pl->nz;
+  a.in = yt;
+  a.out = yt;
+  a.ny = pl->nx;  // lines per plane
+  a.nlines = pl->nx * pl->nz;
+  cudaError_t e;
+  if (FWD && (e = run(pl, K_TRANSP, st, [&] {
+                return launch_plane_transpose<T>(data, yt, pl->ny, pl->nx, pl->nz, skip, st);
+              })) != cudaSuccess)
+    return e;
+  if ((e = run(pl, kind, st, [&] { return launch_long<T, T, T, FWD>(t.m, a, st); })) != cudaSuccess) return e;
+  if (!FWD)
+    return run(pl, K_TRANSP, st, [&] { return launch_plane_transpose<T>(yt, data, pl->nx, pl->ny, pl->nz, skip, st); });
+  return cudaSuccess;
 }
 
 // The plain five-pass solve in one precision, in place on `p` after the first pass.
@@ -479,9 +486,8 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
   // long y lines: the z solve runs on the transposed planes in yscr, p is its scratch
   const bool yl = y_long(pl);
   T* yt = static_cast<T*>(yscr);
-  if ((e = run(pl, K_YF, st, [&] {
-         return yl ? y_long_pass<T, true>(pl, p, yt, nullptr, st)
-                   : line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st);
+  if ((e = y_pass<T, true>(pl, K_YF, yl, p, yt, nullptr, st, [&] {
+         return line_xform<T, T, T, true>(pl, 1, p, p, nullptr, 0, nullptr, st);
        })) != cudaSuccess)
     return cuda_fail(pl, e, "y forward");
   const ZArgs<T> za = yl ? zargs_t<T>(pl, yt, ws, L, nullptr, p) : zargs<T>(pl, p, ws, L, nullptr);
@@ -494,9 +500,8 @@ ps_status solve_plain(ps_plan* pl, const T* f, T* p, void* ws, cudaStream_t st, 
   if (pl->singular && !(sizeof(T) == 4 && !pl->periodic_z && pl->lowx > 0) &&
       (e = run(pl, K_ZS, st, [&] { return launch_zsingular<T>(za, st); })) != cudaSuccess)
     return cuda_fail(pl, e, "z singular column");
-  if ((e = run(pl, K_YB, st, [&] {
-         return yl ? y_long_pass<T, false>(pl, p, yt, nullptr, st)
-                   : line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st);
+  if ((e = y_pass<T, false>(pl, K_YB, yl, p, yt, nullptr, st, [&] {
+         return line_xform<T, T, T, false>(pl, 1, p, p, nullptr, 0, nullptr, st);
        })) != cudaSuccess)
     return cuda_fail(pl, e, "y backward");
   if ((e = run(pl, K_XB, st, [&] { return line_xform<T, T, T, false>(pl, 0, p, p, sout, 0, nullptr, st); })) != cudaSuccess)
@@ -556,9 +561,8 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       else
         r = run(pl, K_XF, st, [&] { return line_xform<float, float, float, true>(pl, 0, rh, w, nullptr, 0, skip, st); });
       if (r != cudaSuccess) return r;
-      if ((r = run(pl, K_YF, st, [&] {
-             return y_long(pl) ? y_long_pass<float, true>(pl, w, yt, skip, st)
-                               : line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st);
+      if ((r = y_pass<float, true>(pl, K_YF, y_long(pl), w, yt, skip, st, [&] {
+             return line_xform<float, float, float, true>(pl, 1, w, w, nullptr, 0, skip, st);
            })) != cudaSuccess)
         return r;
     }
@@ -572,10 +576,9 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       return r;
     if (pl->singular && (pl->periodic_z || pl->lowx == 0) &&
         (r = run(pl, K_ZS, st, [&] { return launch_zsingular<float>(za, st); })) != cudaSuccess) return r;
-    if ((r = run(pl, K_YB, st, [&] {
-           return ytr ? y_long_pass<float, false>(pl, w, yt, skip, st)
-                      : line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st, nullptr, nullptr,
-                                                               nullptr, 0, yscr);
+    if ((r = y_pass<float, false>(pl, K_YB, ytr, w, yt, skip, st, [&] {
+           return line_xform<float, float, float, false>(pl, 1, w, w, nullptr, 0, skip, st, nullptr, nullptr,
+                                                         nullptr, 0, yscr);
          })) != cudaSuccess)
       return r;
     if (first)
