@@ -182,6 +182,14 @@ __global__ void __launch_bounds__(LShape<M>::NT, (sizeof(T) == 8 ? 256 : PS_LONG
         for (int o = b * 128; o < N * (int)sizeof(TI); o += NT * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + o));
       }
     }
+    if constexpr (!FWD && sizeof(TO) == 8 && (OM == row::OM_BASE || OM == row::OM_ACC)) {
+      // the operand of the output stage (the FP32 base, or the FP64 output accumulated
+      // into) is read only after the transform: ask L2 for it now
+      const char* ob = (OM == row::OM_BASE) ? reinterpret_cast<const char*>(a.base32 + g0)
+                                            : reinterpret_cast<const char*>(out + g0);
+      const int obytes = N * ((OM == row::OM_BASE) ? 4 : 8);
+      for (int o = b * 128; o < obytes; o += NT * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(ob + o));
+    }
     const TI* src = in + g0;
     const T sci = (FWD && a.plane_scale) ? a.plane_scale[z] : (T)1;
     const T sco = (!FWD && a.plane_scale) ? a.plane_scale[z] : (T)1;
