@@ -70,12 +70,13 @@ def peaks():
 
 def source_hash(unit):
     """Hash of one kernel's translation unit (csrc/<unit>, whose launcher sets the launch
-    shape) and the local headers it includes."""
+    shape) and the csrc headers it includes (the public C header, which declares the ABI
+    and generates no kernel code, is not followed)."""
     csrc = os.path.join(ROOT, "paper_1802_10323_gb300", "csrc")
     seen, todo = [], [os.path.join(csrc, unit)]
     while todo:
         fn = os.path.normpath(todo.pop())
-        if fn in seen or not os.path.exists(fn):
+        if fn in seen or not os.path.exists(fn) or os.path.dirname(fn) != os.path.normpath(csrc):
             continue
         seen.append(fn)
         for line in open(fn, encoding="utf-8"):
