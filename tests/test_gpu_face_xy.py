@@ -43,7 +43,10 @@ def _relerr(p, q):
 
 CASES = [((6, 8, 12), ("FD", "P", "NN"), 0.0), ((5, 12, 24), ("NN", "FD", "DD"), 0.0),
          ((4, 48, 36), ("FD", "FD", "P"), 0.0), ((6, 16, 96), ("FD", "DN", "FD"), 3.0),
-         ((3, 64, 64), ("DD", "FD", "ND"), 40.0), ((4, 72, 36), ("FD", "NN", "NN"), 0.0)]
+         ((3, 64, 64), ("DD", "FD", "ND"), 40.0), ((4, 72, 36), ("FD", "NN", "NN"), 0.0),
+         # face-centred x with y lines of 2048: the z solve on transposed planes carries the
+         # wall row's eigenvalue in its swapped x/y tables
+         ((3, 2048, 24), ("FD", "P", "NN"), 0.0)]
 IDS = [f"{'x'.join(map(str, s))}-{'-'.join(b)}-a{a:g}" for s, b, a in CASES]
 
 
