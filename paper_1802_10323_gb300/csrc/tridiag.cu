@@ -61,26 +61,38 @@ __device__ __forceinline__ double rcp_newton(double x) {
   return fma(r, e, r);
 }
 
+// Called by all 32 lanes of a warp (t = the warp's first column + lane).
 __device__ void zlow_column(const ZArgs<float>& a, int t) {
   const int nrect = a.lowx * a.lowy;
+  const size_t st = (size_t)a.nx * a.ny;
+  const int nz = a.nz;
+  const int lane = threadIdx.x & 31;
+  // The singular column (0,0) is t = 0: its Δz^f-weighted mean (and, below, its final
+  // shift) is a loop over the whole column, taken by every lane of its warp rather than
+  // by lane 0 alone while the others wait.
+  const bool sing_warp = a.singular && (t >> 5) == 0;
+  double mean = 0.0, wsum = 0.0;
+  if (sing_warp) {  // remove the Δz^f-weighted mean of the right-hand side; Φ̂_0 = 0 pinned
+    for (int k = lane; k < nz; k += 32) {
+      mean += a.dzf64[k] * (double)a.data[k * st];
+      wsum += a.dzf64[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mean += __shfl_xor_sync(0xffffffffu, mean, o);
+      wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    }
+    mean /= wsum;
+  }
+  const unsigned live = __ballot_sync(0xffffffffu, t < nrect);  // lanes with a column
   if (t >= nrect) return;
   const int i = t % a.lowx, j = t / a.lowx;
   const int col = j * a.nx + i;
-  const size_t st = (size_t)a.nx * a.ny;
-  const int nz = a.nz;
   float* d = a.data + col;
   double* cs = a.scr64 + t;                       // [k][nrect]
   double* ds = a.scr64 + (size_t)nz * nrect + t;  // [k][nrect]
   const bool sing = a.singular && col == 0;
+  if (!sing) mean = 0.0;  // (the warp shares column 0's mean; only its own thread uses it)
   const double lam = a.lamx64[i] + a.lamy64[j];
-  double mean = 0.0, wsum = 0.0;
-  if (sing) {  // remove the Δz^f-weighted mean of the right-hand side; Φ̂_0 = 0 pinned
-    for (int k = 0; k < nz; ++k) {
-      mean += a.dzf64[k] * (double)d[k * st];
-      wsum += a.dzf64[k];
-    }
-    mean /= wsum;
-  }
   const int kb = sing ? 1 : 0;
   // forward sweep over chunks of ZL rows, the next chunk's right-hand side in flight
   float cur[ZL], nxt[ZL];
@@ -147,10 +159,14 @@ __device__ void zlow_column(const ZArgs<float>& a, int t) {
       db[u] = dn[u];
     }
   }
-  if (sing) {  // the singular column keeps zero weighted mean
-    const double mx = xs / wsum;
-    d[0] = (float)(-mx);
-    for (int k = 1; k < nz; ++k) d[(size_t)k * st] = (float)(ds[(size_t)k * nrect] - mx);
+  if (sing_warp) {  // the singular column keeps zero weighted mean (its warp's live lanes)
+    const double mx = __shfl_sync(live, xs / wsum, 0);
+    __syncwarp(live);  // lane 0's scratch stores are visible to the lanes reading them below
+    const int rank = __popc(live & ((1u << lane) - 1u)), nl = __popc(live);
+    float* d0 = a.data;
+    const double* ds0 = a.scr64 + (size_t)nz * nrect;  // column t = 0 of the scratch
+    if (rank == 0) d0[0] = (float)(-mx);
+    for (int k = 1 + rank; k < nz; k += nl) d0[(size_t)k * st] = (float)(ds0[(size_t)k * nrect] - mx);
   }
 }
 
