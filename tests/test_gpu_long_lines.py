@@ -119,3 +119,21 @@ def test_long_lines_first_line_of_every_cta(lib, bcx):
         p = plan.solve(ft).double().cpu().numpy()
         assert _relerr(p, q) <= 2e-5
     plan.close()
+
+
+@pytest.mark.parametrize("shape,bcs", [((2, 2048, 8), ("DD", "P", "NN")), ((3, 4096, 6), ("P", "NN", "DN"))],
+                         ids=["2x2048x8-DD-P-NN", "3x4096x6-P-NN-DN"])
+def test_long_y_transpose_solve(lib, shape, bcs):
+    """The transpose solve (the projection's backward) with y lines of 2048/4096: the z
+    solve runs on transposed planes between the y passes, the Δz weighting in x."""
+    import torch
+    from oracle import adjoint as AD
+    nz, ny, nx = shape
+    zf = synth.tanh_faces(nz, 1.0, 1.5)
+    g = np.random.default_rng(nx * ny).uniform(-1, 1, shape)
+    plan = lib.Plan(nx, ny, nz, 4.0 / nx, 4.0 / ny, zf=zf, bcs=bcs, precision="fp64")
+    out = plan.solve_transpose(torch.as_tensor(g, device="cuda").contiguous())
+    torch.cuda.synchronize()
+    q = AD.solve_transpose(g, 4.0 / nx, 4.0 / ny, zf, *bcs)
+    assert _relerr(out.cpu().numpy(), q) <= 1e-12
+    plan.close()
