@@ -12,8 +12,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 template <class T>
 struct cplx {
   T x, y;
@@ -120,48 +118,6 @@ __device__ __forceinline__ df df_from_f64(double d) {
   split_f64(d, r.h, r.l);
   return r;
 }
-
-// ---- double-float numbers with operators ---------------------------------------------
-// ddf: the same hi + lo representation as df, with +, −, × overloaded, so that a
-// kernel body can be written once for a number type N: float for FP32 fields, ddf
-// for FP64 fields (NumOf<T>). Num<N> converts: in() from the field type (FP64 split
-// on its bit pattern), out() to it (one FP64 add for ddf), zero(), and scale() by a
-// power of two (exact).
-struct ddf {
-  float h, l;
-};
-__device__ __forceinline__ ddf operator+(ddf a, ddf b) {
-  const df r = df_add(df{a.h, a.l}, df{b.h, b.l});
-  return {r.h, r.l};
-}
-__device__ __forceinline__ ddf operator-(ddf a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ ddf operator-(ddf a, ddf b) { return a + (-b); }
-__device__ __forceinline__ ddf operator*(ddf a, ddf b) {
-  const df r = df_mul(df{a.h, a.l}, df{b.h, b.l});
-  return {r.h, r.l};
-}
-template <class N>
-struct Num;
-template <>
-struct Num<float> {
-  static __device__ __forceinline__ float in(float x) { return x; }
-  static __device__ __forceinline__ float out(float x) { return x; }
-  static __device__ __forceinline__ float zero() { return 0.f; }
-  static __device__ __forceinline__ float scale(float x, float pow2) { return x * pow2; }
-};
-template <>
-struct Num<ddf> {
-  static __device__ __forceinline__ ddf in(double x) {
-    ddf r;
-    split_f64(x, r.h, r.l);
-    return r;
-  }
-  static __device__ __forceinline__ double out(ddf x) { return widen_f32(x.h) + widen_f32(x.l); }
-  static __device__ __forceinline__ ddf zero() { return {0.f, 0.f}; }
-  static __device__ __forceinline__ ddf scale(ddf x, float pow2) { return {x.h * pow2, x.l * pow2}; }
-};
-template <class T>
-using NumOf = typename std::conditional<sizeof(T) == 8, ddf, float>::type;
 __device__ __forceinline__ float df_to_f32(df a) { return __fadd_rn(a.h, a.l); }
 
 // Wall clock (ns) and an acquire load at GPU scope, for the bounded waits of the

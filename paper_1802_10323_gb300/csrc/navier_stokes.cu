@@ -28,16 +28,15 @@
 // ghost, or the zero wall face), so the flux formulas below are those of the
 // periodic box; which axes are periodic is a template argument, so the periodic box
 // compiles to plain wrapped offsets.
-#include <type_traits>
-
 #include "internal.h"
+#include "number.cuh"
 
 namespace ps {
 
 namespace {
 
 // ---- the arithmetic of the predictor ------------------------------------------------
-// FP32 fields are evaluated in float, FP64 fields in double-float (NumOf, common.cuh):
+// FP32 fields are evaluated in float, FP64 fields in double-float (NumOf, number.cuh):
 // an FP64 operation issues at 1/64 of the FP32 rate on this part, so the ~110
 // operations per cell of the predictor kept the FP64 pipe saturated (86 %) while HBM
 // idled. The FP64 inputs are split on their bit patterns (no FP64 instruction); only
