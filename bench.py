@@ -105,7 +105,7 @@ NS_FLOPS_PER_CELL = 108
 # (smsp__inst_executed.sum × 32 / cells of one launch, ns_predict_kernel<double, 1, 1, 0>
 # on 512x256x64, profiles/kernels_rk3_512x256x64.md), against the issue peak of
 # 152 SMs × 4 schedulers × 32 lanes per clock.
-NS_PRED_INST_PER_CELL = 2142
+NS_PRED_INST_PER_CELL = 1647
 FP32_LANES_PER_SM = 128
 NUM_SMS_GB300 = 152
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64
