@@ -169,6 +169,30 @@ ps_status ps_solve_transpose_f32(ps_plan* plan, const float* g, float* p, void* 
 ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, double* f_dev,
                         double* p_dev, void* ws, void* stream, ps_info* info_host);
 
+/* A sequence of `count` independent solves from host memory with the same plan
+ * (the operator of §2.1, Eq. 4; new right-hand sides), their copies pipelined:
+ * problem s is copied in (f_host[s], nx·ny·nz doubles) while problem s − 1 is
+ * solved, and copied out (to p_host[s]) while problem s + 1 is copied in and
+ * solved, on two internal copy streams beside `stream`; the two directions of
+ * the host link run at once. f_dev[2] and p_dev[2] are two device slots (each
+ * nx·ny·nz doubles, 16-byte aligned, all four disjoint) that problems s and s + 1
+ * alternate between; ws is one workspace (ps_workspace_bytes) shared by the
+ * solves, which run in order on `stream`. info_host (NULL or `count` entries)
+ * receives each solve's ps_info. The host buffers should be pinned for the copies
+ * to overlap (pageable ones are correct but serialise); p_host entries may repeat
+ * (the copies out run in order, the last one wins) and may equal f_host entries
+ * of earlier problems only. The first copies wait for the caller's earlier work
+ * on `stream`; the call returns when every copy and solve has ended. Each p
+ * equals what ps_solve_host returns for the same f. Plans outside the chunked
+ * pipeline (other than PS_FP32_REFINE with x and y lines of 128, 256, 512 or 1024 and
+ * n_x a multiple of 16, n_z ≥ 2) run the problems one after another through
+ * ps_solve_host with slot 0. Errors: PS_INVALID_ARG for a NULL array or pointer,
+ * count < 0, misaligned or overlapping slots; CUDA errors as PS_CUDA_ERROR after
+ * the enqueued work has drained. count = 0 does nothing. */
+ps_status ps_solve_host_seq(ps_plan* plan, int count, const double* const* f_host, double* const* p_host,
+                            double* const* f_dev, double* const* p_dev, void* ws, void* stream,
+                            ps_info* info_host);
+
 /* Solve without a caller-provided workspace (same arguments and results as
  * ps_solve, for PS_FP64 and PS_FP32_REFINE plans). The paper has no
  * counterpart: this is a convenience for callers that cannot allocate device

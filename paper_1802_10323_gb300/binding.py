@@ -61,6 +61,8 @@ _SIGS = {
     "ps_solve_transpose": [_vp, _vp, _vp, _vp, _vp, _vp],
     "ps_solve_transpose_f32": [_vp, _vp, _vp, _vp, _vp, _vp],
     "ps_solve_host": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "ps_solve_host_seq": [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                          ctypes.POINTER(_vp), _vp, _vp, ctypes.POINTER(PsInfo)],
     "ps_plan_destroy": [_vp],
     "ps_solve_static": [_vp, _vp, _vp, _vp, _vp],
     "ps_div": [_vp, _vp, _vp, _vp],
@@ -217,6 +219,20 @@ class Plan:
                                   _vp(f_dev.data_ptr()), _vp(p_dev.data_ptr()), _vp(ws.data_ptr()),
                                   _stream_ptr(stream), ctypes.cast(ctypes.byref(info), _vp)), self.handle)
         return info
+
+    def solve_host_seq(self, f_hosts, p_hosts, f_devs, p_devs, stream=None):
+        """A sequence of solves from host memory, copies pipelined across problems
+        (ps_solve_host_seq): f_hosts, p_hosts lists of host tensors (pinned for
+        overlap), f_devs, p_devs the two device slots. Returns a list of PsInfo."""
+        n = len(f_hosts)
+        if len(p_hosts) != n or len(f_devs) != 2 or len(p_devs) != 2:
+            raise ValueError("f_hosts and p_hosts of one length; two device slots each")
+        ws = self.workspace(f_devs[0].device)
+        arr = lambda ts: (_vp * max(len(ts), 1))(*[t.data_ptr() for t in ts])
+        infos = (PsInfo * max(n, 1))()
+        _check(_lib.ps_solve_host_seq(self.handle, n, arr(f_hosts), arr(p_hosts), arr(f_devs), arr(p_devs),
+                                      _vp(ws.data_ptr()), _stream_ptr(stream), infos), self.handle)
+        return [infos[i] for i in range(n)]
 
     def profile(self, enable=True):
         _check(_lib.ps_profile_enable(self.handle, 1 if enable else 0), self.handle)

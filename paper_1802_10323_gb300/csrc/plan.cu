@@ -136,13 +136,21 @@ struct HostPipe {
   int z[kPipeMax + 1] = {};
   cudaEvent_t in[kPipeMax] = {};   // chunk c of f is on the device
   cudaEvent_t out[kPipeMax] = {};  // chunk c of p = Φ_0 + e written by the first correction
+  bool chunk_out = true;           // the first correction writes p chunk by chunk (records out)
   bool p_recorded = false;
 };
+// ps_solve_host_seq: per device slot, the chunk events of f, the solve's end (f and
+// the slot's p free for the next copy in) and the end of the copy of p out
+constexpr int kSeqComp = kPipeMax, kSeqOut = kPipeMax + 1, kSeqEv = kPipeMax + 2;
 
 struct ps_plan {
   Prof prof;
   cudaStream_t copy_stream = nullptr;          // ps_solve_host: host <-> device copies
   cudaEvent_t pipe_ev[2 * kPipeMax + 1] = {};  // chunks of f in, chunks of p ready, call start
+  cudaStream_t out_stream = nullptr;           // ps_solve_host_seq: device -> host copies
+  cudaEvent_t seq_ev[2][kSeqEv] = {};
+  ps_info* info_pinned = nullptr;              // ps_solve_host_seq: each problem's ps_info
+  int info_cap = 0;
   int nx, ny, nz;
   double dx, dy;
   int bcx, bcy, bcz;
@@ -585,7 +593,7 @@ ps_status solve_refine(ps_plan* pl, const double* f, double* p, void* ws, cudaSt
       return run(pl, K_XB64ST, st, [&] {
         return line_xform<float, float, double, false>(pl, 0, w, nullptr, nullptr, 0, skip, st, &ctrl->pmax, u0);
       });
-    if (hp && c == 1) {  // p is final here unless a later correction runs: chunk by chunk
+    if (hp && hp->chunk_out && c == 1) {  // p is final here unless a later correction runs: chunk by chunk
       for (int ch = 0; ch < hp->nch; ++ch) {
         const int zn = hp->z[ch + 1] - hp->z[ch];
         const size_t off = (size_t)hp->z[ch] * pl->nx * pl->ny;
@@ -1044,6 +1052,14 @@ ps_status ps_solve_transpose_f32(ps_plan* plan, const float* g, float* p, void* 
   return solve_plain<float>(plan, g, p, ws, static_cast<cudaStream_t>(stream), info, true);
 }
 
+// The chunked copy of f feeds the register-resident x and y kernels of the refined
+// solve (chunk c's first x and y passes start as it lands).
+static bool host_pipe_ok(const ps_plan* plan) {
+  return plan->prec == PS_FP32_REFINE && plan->nz >= 2 && plan->ax.bc != BC_FD && plan->ay.bc != BC_FD &&
+         plan->nx % 16 == 0 && (plan->ax.m >= 64 && plan->ax.m <= 512) && (plan->ay.m >= 64 && plan->ay.m <= 512) &&
+         !(plan->ax.m & (plan->ax.m - 1)) && !(plan->ay.m & (plan->ay.m - 1));
+}
+
 ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, double* f_dev,
                         double* p_dev, void* ws, void* stream, ps_info* info_host) {
   ps_status s = check_solve_args(plan, f_dev, p_dev, ws);
@@ -1058,11 +1074,7 @@ ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, dou
   // copy of each chunk of p as soon as the first correction's x pass has written it
   // (overlapping the rest of that pass and of the loop), and p again after the loop
   // if a later correction changed it.
-  const bool pipe = plan->prec == PS_FP32_REFINE && f_dev != p_dev && plan->nz >= 2 &&
-                    plan->ax.bc != BC_FD && plan->ay.bc != BC_FD &&
-                    plan->nx % 16 == 0 && (plan->ax.m >= 64 && plan->ax.m <= 512) &&
-                    (plan->ay.m >= 64 && plan->ay.m <= 512) && !(plan->ax.m & (plan->ax.m - 1)) &&
-                    !(plan->ay.m & (plan->ay.m - 1));
+  const bool pipe = f_dev != p_dev && host_pipe_ok(plan);
   if (pipe) {
     if (!plan->copy_stream) {
       if ((e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -1126,6 +1138,129 @@ ps_status ps_solve_host(ps_plan* plan, const double* f_host, double* p_host, dou
   if (info_host && (e = cudaMemcpyAsync(info_host, info_dev, sizeof(ps_info), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(plan, e, "info copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(plan, e, "stream synchronize");
+  return PS_OK;
+}
+
+ps_status ps_solve_host_seq(ps_plan* plan, int count, const double* const* f_host, double* const* p_host,
+                            double* const* f_dev, double* const* p_dev, void* ws, void* stream,
+                            ps_info* info_host) {
+  if (!plan) return fail(nullptr, PS_INVALID_ARG, "null plan");
+  if (count < 0) return fail(plan, PS_INVALID_ARG, "negative count");
+  if (count == 0) return PS_OK;
+  if (!f_host || !p_host || !f_dev || !p_dev) return fail(plan, PS_INVALID_ARG, "null pointer array");
+  for (int s = 0; s < count; ++s)
+    if (!f_host[s] || !p_host[s]) return fail(plan, PS_INVALID_ARG, "null host pointer");
+  for (int d = 0; d < 2; ++d) {
+    ps_status st = check_solve_args(plan, f_dev[d], p_dev[d], ws);
+    if (st != PS_OK) return st;
+  }
+  const size_t bytes = plan->N * sizeof(double);
+  {  // the four device buffers must be disjoint
+    const char* b[4] = {reinterpret_cast<const char*>(f_dev[0]), reinterpret_cast<const char*>(f_dev[1]),
+                        reinterpret_cast<const char*>(p_dev[0]), reinterpret_cast<const char*>(p_dev[1])};
+    for (int u = 0; u < 4; ++u)
+      for (int v = u + 1; v < 4; ++v)
+        if (b[u] < b[v] + bytes && b[v] < b[u] + bytes)
+          return fail(plan, PS_INVALID_ARG, "the device buffers of the two slots overlap");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!host_pipe_ok(plan)) {  // no chunked pipeline for this plan: one problem after another
+    for (int s = 0; s < count; ++s) {
+      const ps_status r = ps_solve_host(plan, f_host[s], p_host[s], f_dev[0], p_dev[0], ws, stream,
+                                        info_host ? info_host + s : nullptr);
+      if (r != PS_OK) return r;
+    }
+    return PS_OK;
+  }
+  cudaError_t e;
+  if (!plan->copy_stream || !plan->out_stream) {
+    if (!plan->copy_stream) {
+      if ((e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(plan, e, "copy stream");
+      for (auto& ev : plan->pipe_ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(plan, e, "copy events");
+    }
+    if ((e = cudaStreamCreateWithFlags(&plan->out_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(plan, e, "copy-out stream");
+    for (auto& row : plan->seq_ev)
+      for (auto& ev : row)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(plan, e, "sequence events");
+  }
+  if (info_host && plan->info_cap < count) {
+    if (plan->info_pinned) cudaFreeHost(plan->info_pinned);
+    plan->info_pinned = nullptr;
+    plan->info_cap = 0;
+    if ((e = cudaHostAlloc(&plan->info_pinned, (size_t)count * sizeof(ps_info), cudaHostAllocDefault)) != cudaSuccess) {
+      plan->info_pinned = nullptr;
+      return cuda_fail(plan, e, "pinned info buffer");
+    }
+    plan->info_cap = count;
+  }
+  cudaStream_t cin = plan->copy_stream, cout = plan->out_stream;
+  ps_info* info_dev = reinterpret_cast<ps_info*>(static_cast<char*>(ws) + ws_layout(plan).info);
+  auto drain = [&]() {  // (on an error: let every enqueued copy and launch finish)
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(cin);
+    cudaStreamSynchronize(cout);
+  };
+  // the copies wait for the caller's earlier work on its stream (which may use the buffers)
+  cudaEvent_t start = plan->pipe_ev[2 * kPipeMax];
+  if ((e = cudaEventRecord(start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cin, start, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(cout, start, 0)) != cudaSuccess)
+    return cuda_fail(plan, e, "copy stream order");
+  const size_t plane = (size_t)plan->nx * plan->ny;
+  for (int s = 0; s < count; ++s) {
+    const int d = s & 1;
+    cudaEvent_t* ev = plan->seq_ev[d];
+    HostPipe hp;
+    hp.nch = plan->nz < kPipeMax ? plan->nz : kPipeMax;
+    hp.chunk_out = false;
+    for (int c = 0; c <= hp.nch; ++c) hp.z[c] = (int)((long long)plan->nz * c / hp.nch);
+    for (int c = 0; c < hp.nch; ++c) hp.in[c] = ev[c];
+    // copy in: slot d's f is free once problem s − 2's solve has ended
+    if (s >= 2 && (e = cudaStreamWaitEvent(cin, ev[kSeqComp], 0)) != cudaSuccess) {
+      drain();
+      return cuda_fail(plan, e, "copy stream order");
+    }
+    for (int c = 0; c < hp.nch; ++c) {
+      const size_t off = (size_t)hp.z[c] * plane, n = (size_t)(hp.z[c + 1] - hp.z[c]) * plane;
+      if ((e = cudaMemcpyAsync(f_dev[d] + off, f_host[s] + off, n * sizeof(double), cudaMemcpyHostToDevice, cin)) !=
+              cudaSuccess ||
+          (e = cudaEventRecord(hp.in[c], cin)) != cudaSuccess) {
+        drain();
+        return cuda_fail(plan, e, "host to device copy");
+      }
+    }
+    // solve: slot d's p is free once problem s − 2's copy out has ended
+    if (s >= 2 && (e = cudaStreamWaitEvent(st, ev[kSeqOut], 0)) != cudaSuccess) {
+      drain();
+      return cuda_fail(plan, e, "stream order");
+    }
+    const ps_status r = solve_refine(plan, f_dev[d], p_dev[d], ws, st, info_dev, &hp);
+    if (r != PS_OK) {
+      drain();
+      return r;
+    }
+    if (info_host &&
+        (e = cudaMemcpyAsync(plan->info_pinned + s, info_dev, sizeof(ps_info), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess) {
+      drain();
+      return cuda_fail(plan, e, "info copy");
+    }
+    // copy out after the solve, while the next problem's copy in and solve proceed
+    if ((e = cudaEventRecord(ev[kSeqComp], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cout, ev[kSeqComp], 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p_host[s], p_dev[d], bytes, cudaMemcpyDeviceToHost, cout)) != cudaSuccess ||
+        (e = cudaEventRecord(ev[kSeqOut], cout)) != cudaSuccess) {
+      drain();
+      return cuda_fail(plan, e, "device to host copy");
+    }
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess || (e = cudaStreamSynchronize(cin)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(cout)) != cudaSuccess)
+    return cuda_fail(plan, e, "stream synchronize");
+  if (info_host) memcpy(info_host, plan->info_pinned, (size_t)count * sizeof(ps_info));
   return PS_OK;
 }
 
@@ -1327,7 +1462,12 @@ ps_status ps_plan_destroy(ps_plan* plan) {
   for (auto& ev : plan->prof.ev) cudaEventDestroy(ev);
   for (auto& ev : plan->pipe_ev)
     if (ev) cudaEventDestroy(ev);
+  for (auto& row : plan->seq_ev)
+    for (auto& ev : row)
+      if (ev) cudaEventDestroy(ev);
   if (plan->copy_stream) cudaStreamDestroy(plan->copy_stream);
+  if (plan->out_stream) cudaStreamDestroy(plan->out_stream);
+  if (plan->info_pinned) cudaFreeHost(plan->info_pinned);
   if (plan->dev) cudaFree(plan->dev);
   delete plan;
   return PS_OK;
