@@ -362,7 +362,7 @@ ps_status ps_batch_autotune(ps_batch* batch, double* const* f_dev, double* const
                             void* stream, double* best_ms);
 
 /* Current tile scale of the batch: 2 after ps_batch_create, then whichever of
- * the autotuner's candidates 1, 2, 4, 8, 16 it picked. */
+ * the autotuner's candidates 1, 2, 4, 8, 16, 32, 64 it picked. */
 int ps_batch_tile_scale(const ps_batch* batch);
 
 /* Wait limit of the persistent kernel's dependency waits, in seconds

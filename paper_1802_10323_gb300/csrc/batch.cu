@@ -401,7 +401,7 @@ ps_status bfail(ps_batch* b, ps_status st, const char* msg) {
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Tile scales the autotuner times (and the only ones a cache entry may name).
-constexpr int kScales[] = {1, 2, 4, 8, 16};
+constexpr int kScales[] = {1, 2, 4, 8, 16, 32, 64};
 constexpr int kNumScales = (int)(sizeof(kScales) / sizeof(kScales[0]));
 bool is_candidate_scale(int sc) {
   for (int i = 0; i < kNumScales; ++i)
