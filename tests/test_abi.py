@@ -90,6 +90,12 @@ def test_ns_substep_null_plan(binding):
                                  None) == binding.PS_INVALID_ARG
 
 
+def test_host_sequence_null_plan(binding):
+    """ps_solve_host_seq checks its plan before touching any stream or buffer."""
+    assert binding.ps_solve_host_seq(None, 0, None, None, None, None, None, None, None) == binding.PS_INVALID_ARG
+    assert binding.ps_solve_host_seq(None, 3, None, None, None, None, None, None, None) == binding.PS_INVALID_ARG
+
+
 def test_injected_allocation_failure(binding):
     """A host-injected allocation failure (the stand-in for an out-of-memory device)
     makes ps_plan_create return PS_OUT_OF_MEMORY cleanly: a NULL plan and a message,
