@@ -454,6 +454,19 @@ def bench_ours(args):
             ph.copy_(p, non_blocking=True)
             torch.cuda.synchronize()
             per_copy.append(time.perf_counter() - tc)
+        # both directions at once (two streams): the link's bound for a sequence whose
+        # copies overlap across problems
+        per_both = []
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        for _ in range(k_e2e):
+            torch.cuda.synchronize()
+            tc = time.perf_counter()
+            with torch.cuda.stream(s_in):
+                f.copy_(fh, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                ph.copy_(p, non_blocking=True)
+            torch.cuda.synchronize()
+            per_both.append(time.perf_counter() - tc)
         e2e = {"value": job_rate(world, N, t_e2e * 1e3), "unit": "Mpts/s",
                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8 + 32,
                "ms_per_step": t_e2e * 1e3, "problems": k_e2e, "sequences_ms_per_problem": seq_ms,
@@ -464,7 +477,11 @@ def bench_ours(args):
                                 "ms_median": statistics.median(per_call) * 1e3},
                "copies_only": {"what": "f host->device then p device->host, pinned, no solve",
                                "ms_min": min(per_copy) * 1e3, "ms_median": statistics.median(per_copy) * 1e3,
-                               "ms_max": max(per_copy) * 1e3}}
+                               "ms_max": max(per_copy) * 1e3},
+               "copies_both_directions": {"what": "f host->device and p device->host at once, two streams",
+                                          "ms_min": min(per_both) * 1e3,
+                                          "ms_median": statistics.median(per_both) * 1e3,
+                                          "ms_max": max(per_both) * 1e3}}
         del fh, ph
 
     # ---- plain FP64 GPU solve of the same input (the comparison) ----
