@@ -43,22 +43,32 @@ constexpr int ZTAB_MAX = 4096;     // planes whose coefficient table fits in sha
 // is smooth in z with a large amplitude: exactly what an FP32 correction solve
 // removes worst (its own transform rounding, amplified by ‖A‖, scales with the
 // correction's size). Those few columns — a rectangle q_x < lowx, q_y < lowy chosen
-// at plan creation from κ — are solved here in FP64 (Thomas with c' and d' in FP64
-// scratch; the singular column (0,0) with its weighted-mean pinning), by CTAs of
-// the same launch as the FP32 columns, so they overlap them. Output rounded to FP32.
-constexpr int ZL = 4;  // rows in flight per FP64 column (keeps the kernel's registers at the FP32 path's)
+// at plan creation from κ — are solved here in double-float arithmetic, ~2^−46
+// relative per operation against ε_32 = 2^−24 (Thomas with c' and d' as float pairs in
+// the FP64-sized scratch; the singular column (0,0) with its weighted-mean pinning),
+// by CTAs of the same launch as the FP32 columns, so they overlap them. Output
+// rounded to FP32.
+constexpr int ZL = 4;  // rows in flight per rectangle column (keeps the kernel's registers at the FP32 path's)
 
-// 1/x in FP64 for those columns: the hardware approximation refined by two
-// Newton–Raphson steps r ← r + r·(1 − x·r) (each roughly doubles the correct bits),
-// well below the FP32 rounding of the result; an IEEE FP64 division costs several
-// times more on the FP64 pipe.
-__device__ __forceinline__ double rcp_newton(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+// Those columns run in double-float arithmetic (pairs of floats, ~48-bit significand)
+// rather than in FP64: on this part one FP64 warp instruction occupies its SM
+// sub-partition's FP64 pipe for ~33 ns whatever the number of active lanes (measured:
+// a dependent FP64 FMA chain 32.8 ns per step with 1, 8 or 32 lanes, 2.3 ns in FP32),
+// and a row of the FP64 elimination took about eleven of them, so the rectangle's
+// sequential sweeps were the z pass's critical path on small planes. The coefficients
+// are split on their bit patterns; no FP64 instruction remains in the row loops. The
+// result is rounded to FP32, far above the ~2^−46 relative error of these operations.
+
+// 1/x of a double-float pivot: the FP32 approximation r refined by one Newton step
+// carried in double-float, r + r·e with e = 1 − x·r (x.h·r is formed exactly with an
+// FMA; 1 − p is exact for p near 1), about 2^−46 relative.
+__device__ __forceinline__ df df_rcp(df x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x.h));
+  const float p = __fmul_rn(x.h, r);
+  const float pe = __fmaf_rn(x.h, r, -p);
+  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(x.l, r));
+  return quick_two_sum(r, __fmul_rn(r, e));
 }
 
 // Called by all 32 lanes of a warp (t = the warp's first column + lane).
@@ -88,11 +98,12 @@ __device__ void zlow_column(const ZArgs<float>& a, int t) {
   const int i = t % a.lowx, j = t / a.lowx;
   const int col = j * a.nx + i;
   float* d = a.data + col;
-  double* cs = a.scr64 + t;                       // [k][nrect]
-  double* ds = a.scr64 + (size_t)nz * nrect + t;  // [k][nrect]
+  // (c'_k, d'_k) as float pairs in the FP64 scratch: [k][nrect] each
+  float2* cs = reinterpret_cast<float2*>(a.scr64) + t;
+  float2* ds = reinterpret_cast<float2*>(a.scr64) + (size_t)nz * nrect + t;
   const bool sing = a.singular && col == 0;
-  if (!sing) mean = 0.0;  // (the warp shares column 0's mean; only its own thread uses it)
-  const double lam = a.lamx64[i] + a.lamy64[j];
+  const df mn = sing ? df_from_f64(mean) : df{0.f, 0.f};
+  const df lam = sing ? df{0.f, 0.f} : df_from_f64(a.lamx64[i] + a.lamy64[j]);
   const int kb = sing ? 1 : 0;
   // forward sweep over chunks of ZL rows, the next chunk's right-hand side in flight
   float cur[ZL], nxt[ZL];
@@ -101,53 +112,55 @@ __device__ void zlow_column(const ZArgs<float>& a, int t) {
     for (int u = 0; u < ZL; ++u) buf[u] = (k0 + u < nz) ? d[(size_t)(k0 + u) * st] : 0.f;
   };
   load(0, cur);
-  double cp = 0.0, dp = 0.0;
+  df cp = {0.f, 0.f}, dp = {0.f, 0.f};
   for (int k0 = 0; k0 < nz; k0 += ZL) {
     if (k0 + ZL < nz) load(k0 + ZL, nxt);
 #pragma unroll
     for (int u = 0; u < ZL; ++u) {
       const int k = k0 + u;
       if (k >= kb && k < nz) {
-        const double ak = (k > kb) ? __ldg(a.za64 + k) : 0.0;
-        const double ck = (k < nz - 1) ? __ldg(a.zc64 + k) : 0.0;
-        const double mk = rcp_newton(__ldg(a.zb64 + k) + (sing ? 0.0 : lam) - ak * cp);
-        cp = ck * mk;
-        dp = (((double)cur[u] - mean) - ak * dp) * mk;
-        cs[(size_t)k * nrect] = cp;
-        ds[(size_t)k * nrect] = dp;
+        const df ak = (k > kb) ? df_from_f64(__ldg(a.za64 + k)) : df{0.f, 0.f};
+        const df ck = (k < nz - 1) ? df_from_f64(__ldg(a.zc64 + k)) : df{0.f, 0.f};
+        const df bk = df_add(df_from_f64(__ldg(a.zb64 + k)), lam);
+        const df mk = df_rcp(df_sub(bk, df_mul(ak, cp)));
+        cp = df_mul(ck, mk);
+        dp = df_mul(df_sub(df_sub(df{cur[u], 0.f}, mn), df_mul(ak, dp)), mk);
+        cs[(size_t)k * nrect] = make_float2(cp.h, cp.l);
+        ds[(size_t)k * nrect] = make_float2(dp.h, dp.l);
       }
     }
 #pragma unroll
     for (int u = 0; u < ZL; ++u) cur[u] = nxt[u];
   }
   // backward sweep, chunks of (c', d') from the top with the chunk below in flight
-  double cb[ZL], db[ZL], cn[ZL], dn[ZL];
+  float2 cb[ZL], db[ZL], cn[ZL], dn[ZL];
   const int klast = ((nz - 1) / ZL) * ZL;
-  auto loadb = [&](int k0, double* c_, double* d_) {
+  auto loadb = [&](int k0, float2* c_, float2* d_) {
 #pragma unroll
     for (int u = 0; u < ZL; ++u) {
       const int k = k0 + u;
-      c_[u] = (k < nz) ? cs[(size_t)k * nrect] : 0.0;
-      d_[u] = (k < nz) ? ds[(size_t)k * nrect] : 0.0;
+      c_[u] = (k < nz) ? cs[(size_t)k * nrect] : make_float2(0.f, 0.f);
+      d_[u] = (k < nz) ? ds[(size_t)k * nrect] : make_float2(0.f, 0.f);
     }
   };
   loadb(klast, cb, db);
-  double x = 0.0, xs = 0.0;
+  df x = {0.f, 0.f}, xs = {0.f, 0.f};
   for (int k0 = klast; k0 >= 0; k0 -= ZL) {
     if (k0 > 0) loadb(k0 - ZL, cn, dn);
 #pragma unroll
     for (int u = ZL - 1; u >= 0; --u) {
       const int k = k0 + u;
       if (k >= kb && k < nz) {
-        x = db[u] - ((k < nz - 1) ? cb[u] : 0.0) * x;
-        db[u] = x;
-        if (sing) xs += a.dzf64[k] * x;
+        const df ck = (k < nz - 1) ? df{cb[u].x, cb[u].y} : df{0.f, 0.f};
+        x = df_sub(df{db[u].x, db[u].y}, df_mul(ck, x));
+        db[u] = make_float2(x.h, x.l);
+        if (sing) xs = df_add(xs, df_mul(df_from_f64(a.dzf64[k]), x));
       }
     }
     if (!sing) {
 #pragma unroll
       for (int u = 0; u < ZL; ++u)
-        if (k0 + u < nz) d[(size_t)(k0 + u) * st] = (float)db[u];
+        if (k0 + u < nz) d[(size_t)(k0 + u) * st] = __fadd_rn(db[u].x, db[u].y);
     } else {
 #pragma unroll
       for (int u = 0; u < ZL; ++u)
@@ -160,13 +173,18 @@ __device__ void zlow_column(const ZArgs<float>& a, int t) {
     }
   }
   if (sing_warp) {  // the singular column keeps zero weighted mean (its warp's live lanes)
-    const double mx = __shfl_sync(live, xs / wsum, 0);
+    const double mx = __shfl_sync(live, ((double)xs.h + (double)xs.l) / wsum, 0);
     __syncwarp(live);  // lane 0's scratch stores are visible to the lanes reading them below
     const int rank = __popc(live & ((1u << lane) - 1u)), nl = __popc(live);
     float* d0 = a.data;
-    const double* ds0 = a.scr64 + (size_t)nz * nrect;  // column t = 0 of the scratch
-    if (rank == 0) d0[0] = (float)(-mx);
-    for (int k = 1 + rank; k < nz; k += nl) d0[(size_t)k * st] = (float)(ds0[(size_t)k * nrect] - mx);
+    const float2* ds0 = reinterpret_cast<const float2*>(a.scr64) + (size_t)nz * nrect;  // column t = 0
+    const df nmx = df_from_f64(-mx);
+    if (rank == 0) d0[0] = nmx.h + nmx.l;
+    for (int k = 1 + rank; k < nz; k += nl) {
+      const float2 v = ds0[(size_t)k * nrect];
+      const df y = df_add(df{v.x, v.y}, nmx);
+      d0[(size_t)k * st] = __fadd_rn(y.h, y.l);
+    }
   }
 }
 
@@ -181,8 +199,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
 template <bool TAB>
 __global__ void __launch_bounds__(ZB) zsolve_ckpt_kernel(ZArgs<float> a, int nlowb) {
   if (a.skip && *a.skip) return;
-  if ((int)blockIdx.x < nlowb) {  // FP64 rectangle of low wavenumbers: one warp per CTA,
-    // so that the FP64 work (2 ops per clock per SM) spreads over many SMs
+  if ((int)blockIdx.x < nlowb) {  // the rectangle of low wavenumbers: one warp per CTA,
+    // so that its columns spread over many SMs
     if (threadIdx.x < 32) zlow_column(a, blockIdx.x * 32 + threadIdx.x);
     return;
   }
